@@ -1,0 +1,188 @@
+// TrioSeq oracle — TEST INFRASTRUCTURE ONLY.
+//
+// A plain, slow, obviously-correct CPU implementation of exact 3-way global alignment under
+// sum-of-pairs scoring with a linear gap, written from the paper's definitions:
+//   * the recurrence, Eq. 1 (Sec. II): each cell M[i][j][k] is the best of its 7 predecessors
+//     plus the sum-of-pairs (SOP) score of the column that the move emits;
+//   * the SOP of a column, Sec. II: sigma(x,y) + sigma(x,z) + sigma(y,z) with sigma(residue, gap)
+//     = alpha and sigma(gap, gap) = 0;
+//   * global alignment, Sec. II "Global Alignments": M[0][0][0] = 0, v = -infinity (realised here
+//     by skipping predecessors outside the cube, which reproduces the face recurrences and the
+//     axis values 2*i*alpha), score = M[a][b][c].
+// Tie-break (the paper is silent): the first maximal candidate in Eq. 1's listing order wins,
+// i.e. (1,1,1) > (1,1,0) > (1,0,1) > (0,1,1) > (1,0,0) > (0,1,0) > (0,0,1).
+//
+// Only tests/, the package smoke check and the benchmark's CPU-baseline leg may load this
+// library; the product path never does. It shares no code with the CUDA path.
+//
+// Arithmetic is int64 throughout, so it cannot overflow for any input the library accepts.
+// Residues are codes 0..K-1; in emitted alignment rows, the gap is ORACLE_GAP (255).
+
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+#include <algorithm>
+
+namespace {
+
+constexpr uint8_t ORACLE_GAP = 255;
+
+// Moves in Eq. 1's listing order: (di, dj, dk).
+constexpr int kMoves[7][3] = {
+    {1, 1, 1}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1}, {1, 0, 0}, {0, 1, 0}, {0, 0, 1}};
+
+struct Scoring {
+  int K;
+  const int32_t* sub;  // K*K row-major, symmetric
+  int64_t gap;         // alpha
+  // sigma over residues and gaps (Sec. II): residue/residue from the matrix, residue/gap = alpha,
+  // gap/gap = 0.
+  int64_t sigma(int x, int y) const {
+    if (x < 0 && y < 0) return 0;
+    if (x < 0 || y < 0) return gap;
+    return sub[x * K + y];
+  }
+  // SOP of one column (x, y, z); -1 stands for a gap.
+  int64_t sop(int x, int y, int z) const { return sigma(x, y) + sigma(x, z) + sigma(y, z); }
+};
+
+}  // namespace
+
+extern "C" {
+
+// Exact 3-way global alignment (Eq. 1, global initialisation of Sec. II).
+//   s0/s1/s2: residue codes, lengths a/b/c (any may be 0).
+//   K, sub: alphabet size and K*K symmetric substitution matrix; gap: alpha (<= 0 in practice).
+//   score_out: M[a][b][c].
+//   If rows != nullptr, the optimal alignment under the tie-break above is written to
+//   rows[0..L), rows[cap..cap+L), rows[2cap..2cap+L) (gap = 255) and L to *len_out;
+//   requires cap >= a+b+c. Returns 0 on success, -1 on bad arguments, -2 on allocation failure.
+int oracle_align(const uint8_t* s0, int a, const uint8_t* s1, int b, const uint8_t* s2, int c,
+                 int K, const int32_t* sub, int32_t gap, int64_t* score_out, uint8_t* rows,
+                 int64_t cap, int64_t* len_out) {
+  if (a < 0 || b < 0 || c < 0 || K <= 0 || !sub || !score_out) return -1;
+  if (rows && cap < (int64_t)a + b + c) return -1;
+  Scoring sc{K, sub, gap};
+  const int64_t B = b + 1, C = c + 1;
+  const int64_t plane = B * C;
+  const bool want_tb = rows != nullptr;
+  std::vector<uint8_t> code;  // full cube of winning-move indices (0..6), 7 = origin
+  try {
+    if (want_tb) code.assign((size_t)(a + 1) * (size_t)plane, 7);
+  } catch (...) {
+    return -2;
+  }
+  // Two i-slices of scores suffice for the values (each move goes back at most one slice in i).
+  std::vector<int64_t> prev(plane), cur(plane);
+  for (int i = 0; i <= a; i++) {
+    for (int j = 0; j <= b; j++) {
+      for (int k = 0; k <= c; k++) {
+        int64_t best = 0;
+        int arg = 7;
+        if (i == 0 && j == 0 && k == 0) {
+          best = 0;  // M_000 = 0
+        } else {
+          bool have = false;
+          for (int m = 0; m < 7; m++) {
+            const int di = kMoves[m][0], dj = kMoves[m][1], dk = kMoves[m][2];
+            const int pi = i - di, pj = j - dj, pk = k - dk;
+            if (pi < 0 || pj < 0 || pk < 0) continue;  // v = -infinity: predecessor outside cube
+            const int64_t pv = (di ? prev : cur)[(int64_t)pj * C + pk];
+            const int x = di ? (int)s0[i - 1] : -1;
+            const int y = dj ? (int)s1[j - 1] : -1;
+            const int z = dk ? (int)s2[k - 1] : -1;
+            const int64_t cand = pv + sc.sop(x, y, z);
+            if (!have || cand > best) {  // strict '>' keeps the first maximal move
+              best = cand;
+              arg = m;
+              have = true;
+            }
+          }
+        }
+        cur[(int64_t)j * C + k] = best;
+        if (want_tb) code[(size_t)i * plane + (size_t)j * C + k] = (uint8_t)arg;
+      }
+    }
+    std::swap(prev, cur);
+  }
+  *score_out = prev[(int64_t)b * C + c];
+  if (!want_tb) return 0;
+  // Traceback: from (a,b,c) follow the stored winning moves to the origin, emitting columns in
+  // reverse, then reverse them.
+  std::vector<uint8_t> r0, r1, r2;
+  int i = a, j = b, k = c;
+  while (i > 0 || j > 0 || k > 0) {
+    const int m = code[(size_t)i * plane + (size_t)j * C + k];
+    if (m > 6) return -1;  // cannot happen for a well-formed cube
+    const int di = kMoves[m][0], dj = kMoves[m][1], dk = kMoves[m][2];
+    r0.push_back(di ? s0[i - 1] : ORACLE_GAP);
+    r1.push_back(dj ? s1[j - 1] : ORACLE_GAP);
+    r2.push_back(dk ? s2[k - 1] : ORACLE_GAP);
+    i -= di; j -= dj; k -= dk;
+  }
+  const int64_t L = (int64_t)r0.size();
+  for (int64_t t = 0; t < L; t++) {
+    rows[t] = r0[L - 1 - t];
+    rows[cap + t] = r1[L - 1 - t];
+    rows[2 * cap + t] = r2[L - 1 - t];
+  }
+  *len_out = L;
+  return 0;
+}
+
+// Sum-of-pairs score of a given 3-row alignment (Sec. II SOP summed over columns).
+// rows: 3 rows of length L at stride cap, gap = 255. Returns 0, or -1 on a residue >= K.
+int oracle_sp_score(const uint8_t* rows, int64_t L, int64_t cap, int K, const int32_t* sub,
+                    int32_t gap, int64_t* score_out) {
+  Scoring sc{K, sub, gap};
+  int64_t s = 0;
+  for (int64_t t = 0; t < L; t++) {
+    int v[3];
+    for (int q = 0; q < 3; q++) {
+      const uint8_t r = rows[q * cap + t];
+      if (r == ORACLE_GAP) v[q] = -1;
+      else if (r < K) v[q] = r;
+      else return -1;
+    }
+    s += sc.sop(v[0], v[1], v[2]);
+  }
+  *score_out = s;
+  return 0;
+}
+
+// Textbook pairwise Needleman-Wunsch with a linear gap: one alpha per residue aligned to a gap.
+// Used by the oracle's pins (one-empty reduction, pairwise upper bound).
+int oracle_nw2(const uint8_t* x, int a, const uint8_t* y, int b, int K, const int32_t* sub,
+               int32_t gap, int64_t* score_out) {
+  if (a < 0 || b < 0) return -1;
+  std::vector<int64_t> prev(b + 1), cur(b + 1);
+  for (int j = 0; j <= b; j++) prev[j] = (int64_t)j * gap;
+  for (int i = 1; i <= a; i++) {
+    cur[0] = (int64_t)i * gap;
+    for (int j = 1; j <= b; j++) {
+      const int64_t d = prev[j - 1] + sub[x[i - 1] * K + y[j - 1]];
+      const int64_t u = prev[j] + gap;
+      const int64_t l = cur[j - 1] + gap;
+      cur[j] = std::max(d, std::max(u, l));
+    }
+    std::swap(prev, cur);
+  }
+  *score_out = prev[b];
+  return 0;
+}
+
+// Batch convenience: scores of n triplets (score only), sequences packed back to back.
+// offs[3*t+q] / lens[3*t+q] locate sequence q of triplet t in `codes`.
+int oracle_align_many(const uint8_t* codes, const int64_t* offs, const int32_t* lens, int64_t n,
+                      int K, const int32_t* sub, int32_t gap, int64_t* scores) {
+  for (int64_t t = 0; t < n; t++) {
+    const int rc = oracle_align(codes + offs[3 * t], lens[3 * t], codes + offs[3 * t + 1],
+                                lens[3 * t + 1], codes + offs[3 * t + 2], lens[3 * t + 2], K, sub,
+                                gap, &scores[t], nullptr, 0, nullptr);
+    if (rc) return rc;
+  }
+  return 0;
+}
+
+}  // extern "C"
