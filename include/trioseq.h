@@ -1,0 +1,181 @@
+/*
+ * trioseq.h — C ABI of the GB300 engine for exact 3-way global sequence alignment.
+ *
+ * The operation (Graca & Ilic, "TrioSeq", Sec. II): three sequences S0, S1, S2 of lengths
+ * a, b, c over an alphabet, a symmetric substitution score sigma and a linear gap alpha are
+ * aligned by the dynamic program of Eq. 1 over the (a+1) x (b+1) x (c+1) cube:
+ *
+ *   M[i][j][k] = max over the 7 moves m = (di,dj,dk) in {0,1}^3 \ {(0,0,0)} of
+ *                M[i-di][j-dj][k-dk] + SOP(column emitted by m),
+ *   SOP(x,y,z) = sigma(x,y) + sigma(x,z) + sigma(y,z),
+ *
+ * where a column holds the residue S0[i-1] if di = 1 and a gap otherwise (likewise for S1, S2),
+ * sigma(residue, gap) = alpha and sigma(gap, gap) = 0 (Sec. II, SOP definition). Global alignment
+ * (Sec. II, "Global Alignments"): M[0][0][0] = 0, predecessors outside the cube are -infinity,
+ * and the optimal score is M[a][b][c]. The optimal alignment is recovered by walking the winning
+ * moves back from (a,b,c) to the origin.
+ *
+ * Tie-break (the paper leaves it open): when several moves reach the maximum, the first one in
+ * Eq. 1's listing order wins: (1,1,1) > (1,1,0) > (1,0,1) > (0,1,1) > (1,0,0) > (0,1,0) > (0,0,1).
+ * With it the emitted alignment is unique, so results are reproducible bit for bit.
+ *
+ * Conventions for every call:
+ *  - Every call returns a trioseq_status and never aborts the process.
+ *  - The caller owns all inputs and outputs; the library copies what it needs before returning
+ *    (host inputs) or reads device inputs only inside the call's stream order.
+ *  - Handles are opaque and released by the matching *_destroy call.
+ *  - Scores are int32. A call whose worst-case score bound does not fit the engine's integer range
+ *    (|score| * 8 must stay below 2^29, see trioseq_plan) fails with TRIOSEQ_EOVERFLOW.
+ *  - A handle may be used by one host thread at a time; the server (trioseq_server_*) is the
+ *    thread-safe entry for concurrent producers.
+ *  - The compute path is CUDA only (sm_103a). Without a usable GPU the calls fail with
+ *    TRIOSEQ_ECUDA; there is no CPU fallback.
+ */
+#ifndef TRIOSEQ_H
+#define TRIOSEQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TRIOSEQ_OK = 0,
+  TRIOSEQ_EINVAL = 1,    /* bad argument: null pointer, residue outside the alphabet,
+                            asymmetric sigma, gap > 0, cap too small, unknown index */
+  TRIOSEQ_ENOMEM = 2,    /* host or device allocation failed */
+  TRIOSEQ_EAGAIN = 3,    /* result not ready yet (poll) or server queue full (submit) */
+  TRIOSEQ_EOVERFLOW = 4, /* score bound exceeds the integer range of the engine */
+  TRIOSEQ_ETIMEOUT = 5,  /* a bounded device-side wait expired; the context stays usable */
+  TRIOSEQ_ECUDA = 6,     /* CUDA runtime error or no usable GPU */
+  TRIOSEQ_ENOTIMPL = 7   /* requested feature is not built */
+} trioseq_status;
+
+/* Scoring scheme (Sec. II). `alphabet` lists the residue characters (1..32 distinct bytes);
+ * `sub` is the alphabet_size x alphabet_size row-major substitution matrix, which must be
+ * symmetric; `gap` is alpha, added once per residue-gap pair in a column (so a column with one
+ * residue and two gaps scores 2*alpha), and must be <= 0. */
+typedef struct {
+  const char* alphabet;
+  int32_t alphabet_size;
+  const int8_t* sub;
+  int32_t gap;
+} trioseq_scoring;
+
+/* One triplet: three caller-owned host strings over the plan's alphabet (not NUL-terminated;
+ * lengths given explicitly, 0 allowed). */
+typedef struct {
+  const char* s[3];
+  uint32_t len[3];
+} trioseq_triplet;
+
+enum { TRIOSEQ_SCORE_ONLY = 0, TRIOSEQ_WITH_TRACEBACK = 1 };
+
+typedef struct trioseq_plan_s* trioseq_plan_t;
+
+/* trioseq_plan — validate a scoring scheme and create a plan.
+ * The plan owns the device workspace (grown on demand), the kernel-variant choice and the
+ * autotuner cache for the current CUDA device. `max_len_hint` pre-sizes nothing mandatory
+ * (0 = no hint). `flags` is reserved and must be 0.
+ * Errors: EINVAL (null, bad alphabet, asymmetric sub, gap > 0), ECUDA (no device). */
+trioseq_status trioseq_plan(const trioseq_scoring* scoring, uint32_t max_len_hint, uint32_t flags,
+                            trioseq_plan_t* out);
+
+/* Release a plan and its device memory. Null is accepted. */
+trioseq_status trioseq_plan_destroy(trioseq_plan_t plan);
+
+/* trioseq_align_batch — align n triplets (host strings) in one persistent launch.
+ * mode: TRIOSEQ_SCORE_ONLY or TRIOSEQ_WITH_TRACEBACK. scores_out: caller-owned host array of n
+ * int32, filled before return. stream: a cudaStream_t (NULL = the legacy default stream); the
+ * call synchronises that stream before returning.
+ * With TRACEBACK the alignments stay in the plan until the next align call and are read with
+ * trioseq_traceback.
+ * Work: encode + pack (host), one H2D copy, one persistent wavefront launch over all triplets,
+ * one traceback-walk launch (traceback mode), one D2H copy of scores (and alignments).
+ * Errors: EINVAL (residue outside the alphabet, null), EOVERFLOW, ENOMEM, ETIMEOUT, ECUDA. */
+trioseq_status trioseq_align_batch(trioseq_plan_t plan, const trioseq_triplet* triplets, size_t n,
+                                   uint32_t mode, int32_t* scores_out, void* stream);
+
+/* trioseq_traceback — copy the optimal alignment of triplet `idx` of the last TRACEBACK batch.
+ * row0/row1/row2 receive the three aligned rows (alphabet characters, '-' for gaps, not
+ * NUL-terminated); cap is the capacity of each row; *aln_len receives the length L
+ * (max(a,b,c) <= L <= a+b+c). If cap < L the call returns EINVAL and still sets *aln_len.
+ * Errors: EINVAL (no traceback batch, idx out of range, cap too small, null). */
+trioseq_status trioseq_traceback(trioseq_plan_t plan, size_t idx, char* row0, char* row1,
+                                 char* row2, size_t cap, size_t* aln_len);
+
+/* ---- device-resident batches (inputs already in HBM; used by benchmarks and servers) ---- */
+
+typedef struct trioseq_batch_s* trioseq_batch_t;
+
+/* trioseq_batch_create — encode, pack and upload n triplets once; build the work queue, the
+ * triplet descriptors and the workspace layout. The batch can then be run repeatedly with
+ * trioseq_batch_run without any host-to-device traffic. The plan must outlive the batch.
+ * Errors: EINVAL, EOVERFLOW, ENOMEM, ECUDA. */
+trioseq_status trioseq_batch_create(trioseq_plan_t plan, const trioseq_triplet* triplets,
+                                    size_t n, uint32_t mode, trioseq_batch_t* out);
+
+/* trioseq_batch_run — enqueue one full pass of the hot path on `stream` (workspace reset, the
+ * persistent wavefront kernel, and the traceback walk in traceback mode). Asynchronous: scores
+ * land in device memory; read them with trioseq_batch_scores.
+ * Errors: ECUDA (launch failure). */
+trioseq_status trioseq_batch_run(trioseq_batch_t batch, void* stream);
+
+/* trioseq_batch_scores — synchronise `stream`, check the device error word, and copy the n
+ * scores to the caller's host array. Errors: ETIMEOUT (bounded device wait expired), ECUDA. */
+trioseq_status trioseq_batch_scores(trioseq_batch_t batch, void* stream, int32_t* scores_out);
+
+/* Device address of the batch's int32 score array (n entries), valid until destroy. */
+trioseq_status trioseq_batch_device_scores(trioseq_batch_t batch, int32_t** d_scores);
+
+/* trioseq_batch_alignment — after trioseq_batch_scores in traceback mode: copy the alignment of
+ * triplet idx as in trioseq_traceback. */
+trioseq_status trioseq_batch_alignment(trioseq_batch_t batch, size_t idx, char* row0, char* row1,
+                                       char* row2, size_t cap, size_t* aln_len);
+
+/* Work statistics of a batch: number of triplets, the paper's cell count
+ * (sum of |S0|*|S1|*|S2|, the TCUPS numerator), the number of column tasks in the queue, and the
+ * kernel variant chosen (tile rows x tile cols per lane). Any out pointer may be null. */
+trioseq_status trioseq_batch_info(trioseq_batch_t batch, size_t* n, uint64_t* cells,
+                                  uint64_t* tasks, int32_t* tile_j, int32_t* tile_k);
+
+trioseq_status trioseq_batch_destroy(trioseq_batch_t batch);
+
+/* ---- serving: continuous batching behind submit/poll ---- */
+
+typedef struct trioseq_server_s* trioseq_server_t;
+
+/* trioseq_server_create — start a server thread that owns a pending queue and admits requests
+ * by free device memory (`hbm_budget` bytes of workspace, 0 = 80% of free memory at creation)
+ * and free slots, re-batching them each tick into launches on several CUDA streams so that work
+ * of different requests overlaps on the device. plans[0..nplans) are the scoring schemes a
+ * request may name by index (e.g. 0 = DNA, 1 = protein); they must outlive the server.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+trioseq_status trioseq_server_create(const trioseq_plan_t* plans, int32_t nplans,
+                                     size_t hbm_budget, trioseq_server_t* out);
+
+/* trioseq_submit — enqueue one triplet (copied before return) under plan index `plan_id` with
+ * `mode`; returns a ticket. Non-blocking. Errors: EINVAL, EAGAIN (queue full), EOVERFLOW. */
+trioseq_status trioseq_submit(trioseq_server_t srv, const trioseq_triplet* triplet,
+                              int32_t plan_id, uint32_t mode, uint64_t* ticket);
+
+/* trioseq_poll — non-blocking. EAGAIN while the request is pending; OK once done, with *score
+ * set and, for traceback requests, rows[0..2] filled (cap bytes each, *aln_len set; rows may be
+ * null for score-only requests). A ticket is consumed by the first OK. Errors: EINVAL (unknown
+ * ticket, cap too small), ETIMEOUT / ECUDA (the request's launch failed). */
+trioseq_status trioseq_poll(trioseq_server_t srv, uint64_t ticket, int32_t* score, char* rows[3],
+                            size_t cap, size_t* aln_len);
+
+/* Stop the server thread after finishing admitted work and release it. */
+trioseq_status trioseq_server_destroy(trioseq_server_t srv);
+
+/* Human-readable name of a status code (static storage). */
+const char* trioseq_strerror(trioseq_status st);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TRIOSEQ_H */

@@ -1,0 +1,264 @@
+"""Thin ctypes binding of include/trioseq.h (argument marshalling only).
+
+Every function named ``trioseq_*`` here calls the C entry point of the same name; all alignment
+work happens in the CUDA library. If the library cannot be loaded the import raises — there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK, EINVAL, ENOMEM, EAGAIN, EOVERFLOW, ETIMEOUT, ECUDA, ENOTIMPL = range(8)
+SCORE_ONLY, WITH_TRACEBACK = 0, 1
+
+
+class TrioseqError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {trioseq_strerror(status)} ({status})")
+        self.status = status
+
+
+class Scoring(ctypes.Structure):
+    _fields_ = [("alphabet", ctypes.c_char_p), ("alphabet_size", ctypes.c_int32),
+                ("sub", ctypes.POINTER(ctypes.c_int8)), ("gap", ctypes.c_int32)]
+
+
+class Triplet(ctypes.Structure):
+    _fields_ = [("s", ctypes.c_char_p * 3), ("len", ctypes.c_uint32 * 3)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load (building first if needed) the engine library."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"engine library missing: {_build.LIB} (run build())")
+    lib = ctypes.CDLL(_build.LIB)
+    vp, sz, u32, i32 = ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_int32
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    szp = ctypes.POINTER(ctypes.c_size_t)
+    sig = {
+        "trioseq_plan": ([ctypes.POINTER(Scoring), u32, u32, ctypes.POINTER(vp)], i32),
+        "trioseq_plan_destroy": ([vp], i32),
+        "trioseq_align_batch": ([vp, ctypes.POINTER(Triplet), sz, u32, i32p, vp], i32),
+        "trioseq_traceback": ([vp, sz, ctypes.c_char_p, ctypes.c_char_p, ctypes.c_char_p, sz,
+                               szp], i32),
+        "trioseq_batch_create": ([vp, ctypes.POINTER(Triplet), sz, u32, ctypes.POINTER(vp)], i32),
+        "trioseq_batch_run": ([vp, vp], i32),
+        "trioseq_batch_scores": ([vp, vp, i32p], i32),
+        "trioseq_batch_device_scores": ([vp, ctypes.POINTER(vp)], i32),
+        "trioseq_batch_alignment": ([vp, sz, ctypes.c_char_p, ctypes.c_char_p, ctypes.c_char_p,
+                                     sz, szp], i32),
+        "trioseq_batch_info": ([vp, szp, ctypes.POINTER(ctypes.c_uint64),
+                                ctypes.POINTER(ctypes.c_uint64), i32p, i32p], i32),
+        "trioseq_batch_destroy": ([vp], i32),
+        "trioseq_server_create": ([ctypes.POINTER(vp), i32, sz, ctypes.POINTER(vp)], i32),
+        "trioseq_submit": ([vp, ctypes.POINTER(Triplet), i32, u32,
+                            ctypes.POINTER(ctypes.c_uint64)], i32),
+        "trioseq_poll": ([vp, ctypes.c_uint64, i32p, ctypes.POINTER(ctypes.c_char_p), sz, szp],
+                         i32),
+        "trioseq_server_destroy": ([vp], i32),
+        "trioseq_strerror": ([i32], ctypes.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def exported_symbols() -> list[str]:
+    return ["trioseq_plan", "trioseq_plan_destroy", "trioseq_align_batch", "trioseq_traceback",
+            "trioseq_batch_create", "trioseq_batch_run", "trioseq_batch_scores",
+            "trioseq_batch_device_scores", "trioseq_batch_alignment", "trioseq_batch_info",
+            "trioseq_batch_destroy", "trioseq_server_create", "trioseq_submit", "trioseq_poll",
+            "trioseq_server_destroy", "trioseq_strerror"]
+
+
+def trioseq_strerror(status: int) -> str:
+    return load().trioseq_strerror(int(status)).decode()
+
+
+def _check(st: int, what: str):
+    if st != OK:
+        raise TrioseqError(st, what)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _as_bytes(s) -> bytes:
+    if isinstance(s, bytes):
+        return s
+    if isinstance(s, str):
+        return s.encode()
+    return bytes(np.asarray(s, dtype=np.uint8))
+
+
+def _triplet_array(triplets):
+    """ctypes array of Triplet plus the byte objects keeping the strings alive."""
+    keep = []
+    arr = (Triplet * max(1, len(triplets)))()
+    for t, trip in enumerate(triplets):
+        if len(trip) != 3:
+            raise ValueError("a triplet has three sequences")
+        for q in range(3):
+            b = _as_bytes(trip[q])
+            keep.append(b)
+            arr[t].s[q] = b
+            arr[t].len[q] = len(b)
+    return arr, keep
+
+
+def trioseq_plan(alphabet: str, sub, gap: int):
+    lib = load()
+    sub = np.ascontiguousarray(np.asarray(sub, dtype=np.int8))
+    K = len(alphabet)
+    if sub.shape != (K, K):
+        raise ValueError("substitution matrix must be K x K")
+    sc = Scoring(alphabet.encode(), K, sub.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)), int(gap))
+    h = ctypes.c_void_p()
+    _check(lib.trioseq_plan(ctypes.byref(sc), 0, 0, ctypes.byref(h)), "trioseq_plan")
+    return h
+
+
+def trioseq_plan_destroy(plan):
+    _check(load().trioseq_plan_destroy(plan), "trioseq_plan_destroy")
+
+
+def trioseq_align_batch(plan, triplets, mode: int = SCORE_ONLY, stream=None) -> np.ndarray:
+    lib = load()
+    arr, keep = _triplet_array(triplets)
+    out = np.zeros(max(1, len(triplets)), dtype=np.int32)
+    _check(lib.trioseq_align_batch(plan, arr, len(triplets), int(mode),
+                                   out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                   _stream_ptr(stream)), "trioseq_align_batch")
+    del keep
+    return out[:len(triplets)]
+
+
+def _rows(fn, handle, idx: int, cap: int | None = None):
+    lib = load()
+    n = ctypes.c_size_t(0)
+    st = fn(handle, idx, None, None, None, 0, ctypes.byref(n))  # size query
+    if st == OK:
+        return ("", "", "")
+    if st != EINVAL or n.value == 0:
+        _check(st, fn.__name__)
+    cap = n.value if cap is None else cap
+    bufs = [ctypes.create_string_buffer(max(1, cap)) for _ in range(3)]
+    _check(fn(handle, idx, bufs[0], bufs[1], bufs[2], cap, ctypes.byref(n)), fn.__name__)
+    return tuple(b.raw[:n.value].decode() for b in bufs)
+
+
+def trioseq_traceback(plan, idx: int, cap: int | None = None):
+    """Aligned rows (three strings, '-' = gap) of triplet idx of the last traceback batch."""
+    return _rows(load().trioseq_traceback, plan, idx, cap)
+
+
+def trioseq_batch_create(plan, triplets, mode: int = SCORE_ONLY):
+    lib = load()
+    arr, keep = _triplet_array(triplets)
+    h = ctypes.c_void_p()
+    _check(lib.trioseq_batch_create(plan, arr, len(triplets), int(mode), ctypes.byref(h)),
+           "trioseq_batch_create")
+    del keep
+    return h
+
+
+def trioseq_batch_run(batch, stream=None):
+    _check(load().trioseq_batch_run(batch, _stream_ptr(stream)), "trioseq_batch_run")
+
+
+def trioseq_batch_scores(batch, n: int, stream=None) -> np.ndarray:
+    out = np.zeros(max(1, n), dtype=np.int32)
+    _check(load().trioseq_batch_scores(batch, _stream_ptr(stream),
+                                       out.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))),
+           "trioseq_batch_scores")
+    return out[:n]
+
+
+def trioseq_batch_device_scores(batch) -> int:
+    p = ctypes.c_void_p()
+    _check(load().trioseq_batch_device_scores(batch, ctypes.byref(p)),
+           "trioseq_batch_device_scores")
+    return p.value or 0
+
+
+def trioseq_batch_alignment(batch, idx: int, cap: int | None = None):
+    return _rows(load().trioseq_batch_alignment, batch, idx, cap)
+
+
+def trioseq_batch_info(batch) -> dict:
+    n = ctypes.c_size_t()
+    cells, tasks = ctypes.c_uint64(), ctypes.c_uint64()
+    tj, tk = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().trioseq_batch_info(batch, ctypes.byref(n), ctypes.byref(cells),
+                                     ctypes.byref(tasks), ctypes.byref(tj), ctypes.byref(tk)),
+           "trioseq_batch_info")
+    return {"n": n.value, "cells": cells.value, "tasks": tasks.value, "tile": (tj.value, tk.value)}
+
+
+def trioseq_batch_destroy(batch):
+    _check(load().trioseq_batch_destroy(batch), "trioseq_batch_destroy")
+
+
+def trioseq_server_create(plans, hbm_budget: int = 0):
+    arr = (ctypes.c_void_p * len(plans))(*[p.value if hasattr(p, "value") else p for p in plans])
+    h = ctypes.c_void_p()
+    _check(load().trioseq_server_create(arr, len(plans), int(hbm_budget), ctypes.byref(h)),
+           "trioseq_server_create")
+    return h
+
+
+def trioseq_submit(server, triplet, plan_id: int, mode: int = SCORE_ONLY):
+    """Returns (status, ticket); status is OK or EAGAIN (queue full)."""
+    arr, keep = _triplet_array([triplet])
+    t = ctypes.c_uint64(0)
+    st = load().trioseq_submit(server, arr, int(plan_id), int(mode), ctypes.byref(t))
+    if st not in (OK, EAGAIN):
+        _check(st, "trioseq_submit")
+    return st, t.value
+
+
+def trioseq_poll(server, ticket: int, cap: int = 0):
+    """Returns (status, score, rows or None); status is OK or EAGAIN."""
+    score = ctypes.c_int32(0)
+    n = ctypes.c_size_t(0)
+    if cap > 0:
+        bufs = [ctypes.create_string_buffer(cap) for _ in range(3)]
+        rows = (ctypes.c_char_p * 3)(*[ctypes.cast(b, ctypes.c_char_p) for b in bufs])
+    else:
+        bufs, rows = None, None
+    st = load().trioseq_poll(server, ctypes.c_uint64(ticket), ctypes.byref(score), rows,
+                             int(cap), ctypes.byref(n))
+    if st == EAGAIN:
+        return st, None, None
+    _check(st, "trioseq_poll")
+    out_rows = tuple(b.raw[:n.value].decode() for b in bufs) if bufs and n.value else None
+    return st, int(score.value), out_rows
+
+
+def trioseq_server_destroy(server):
+    _check(load().trioseq_server_destroy(server), "trioseq_server_destroy")

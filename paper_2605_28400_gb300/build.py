@@ -1,0 +1,87 @@
+"""Build the engine library (CUDA, sm_103a) in-tree: paper_2605_28400_gb300/_lib/libtrioseq.so.
+
+Two translation units (host runtime + kernels) are compiled in parallel with nvcc for
+sm_103a only, then linked into one shared library with the static CUDA runtime. No torch
+extension machinery is involved; the Python side loads the library with ctypes.
+"""
+from __future__ import annotations
+
+import os
+import shutil
+import subprocess
+import sys
+import threading
+from concurrent.futures import ThreadPoolExecutor
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+CSRC = os.path.join(HERE, "csrc")
+LIBDIR = os.path.join(HERE, "_lib")
+LIB = os.path.join(LIBDIR, "libtrioseq.so")
+SOURCES = ["runtime.cu", "kernels.cu"]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+_lock = threading.Lock()
+
+
+def nvcc() -> str:
+    for cand in (shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if cand and os.path.exists(cand):
+            return cand
+    raise RuntimeError("nvcc not found: the CUDA toolkit is required to build the engine")
+
+
+def _inputs():
+    files = [os.path.join(CSRC, s) for s in SOURCES]
+    files += [os.path.join(CSRC, "engine.h"), os.path.join(ROOT, "include", "trioseq.h")]
+    return files
+
+
+def up_to_date() -> bool:
+    if not os.path.exists(LIB):
+        return False
+    t = os.path.getmtime(LIB)
+    return all(os.path.getmtime(f) <= t for f in _inputs())
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile if any source is newer than the library; returns the library path."""
+    with _lock:
+        if not force and up_to_date():
+            return LIB
+        os.makedirs(LIBDIR, exist_ok=True)
+        cc = nvcc()
+        flags = ARCH + ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC",
+                        "-I", os.path.join(ROOT, "include"), "-I", CSRC]
+        if verbose:
+            flags += ["-Xptxas", "-v"]
+        objs = []
+        tag = f"{os.getpid()}"
+
+        def comp(src):
+            obj = os.path.join(LIBDIR, src.replace(".cu", f".{tag}.o"))
+            cmd = [cc] + flags + ["-c", os.path.join(CSRC, src), "-o", obj]
+            r = subprocess.run(cmd, capture_output=True, text=True)
+            if r.returncode != 0:
+                raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
+            if verbose:
+                sys.stderr.write(r.stderr)
+            return obj
+
+        with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+            objs = list(ex.map(comp, SOURCES))
+        tmp = LIB + f".{tag}.tmp"
+        cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        for o in objs:
+            try:
+                os.remove(o)
+            except OSError:
+                pass
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, LIB)
+        return LIB
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))

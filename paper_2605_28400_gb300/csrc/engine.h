@@ -1,0 +1,88 @@
+// engine.h — data layouts shared by the host runtime and the CUDA kernels.
+//
+// Frame and encoding used on the device (all exact integer transforms of Eq. 1):
+//  * Potential shift. Every move adds 2*alpha per residue it consumes on top of the pairwise
+//    terms, so with M'[i][j][k] = M[i][j][k] - 2*alpha*(i+j+k) the single-residue moves cost 0,
+//    a two-residue move costs sigma''(x,y) and the three-residue move costs
+//    sigma''(x,y) + sigma''(x,z) + sigma''(y,z), where sigma'' = sigma - 2*alpha.
+//    The score is M'[a][b][c] + 2*alpha*(a+b+c).
+//  * Virtual residue. Each sequence gets a virtual residue VIRT = K at position 0 and the cube
+//    is indexed 0..a, 0..b, 0..c directly; sigma''(VIRT, .) = 0. Cells at index -1 are -infinity
+//    (kNeg) except M'[-1][-1][-1] = 0, so the ordinary 7-move recurrence reproduces M_000 = 0,
+//    the axis values and the face recurrences of Sec. II without special cases.
+//  * Traceback keys. With traceback, a cell stores 8*M' + 7; every candidate adds 8*cost plus
+//    (rank - 7), rank 7..1 following Eq. 1's listing order. One integer max then yields the
+//    score and the winning move of the tie-break; the low 3 bits of the max are the rank.
+#pragma once
+#include <stdint.h>
+
+namespace trioseq {
+
+constexpr int kNeg = -(1 << 30);   // -infinity sentinel (never accumulates: see the kernel)
+constexpr int kPR = 4;             // lanes of a warp along j
+constexpr int kPC = 8;             // lanes of a warp along k
+constexpr int kMaxAlphabet = 32;
+constexpr int kWarpsPerCta = 4;
+
+// Rank of each move in the tie-break (Eq. 1 listing order): rank 7 wins ties over rank 6 ...
+// rank -> (di, dj, dk):
+//   7:(1,1,1) 6:(1,1,0) 5:(1,0,1) 4:(0,1,1) 3:(1,0,0) 2:(0,1,0) 1:(0,0,1)
+
+struct TripDesc {
+  int64_t s_off[3];    // byte offsets of S0, S1, S2 in the packed residue buffer
+  int64_t fj_off;      // int32 offset of this triplet's j-face planes in the face workspace
+  int64_t fk_off;      // int32 offset of its k-face planes
+  int64_t code_off;    // uint32-word offset of its traceback codes (-1: score only)
+  int64_t prog_base;   // index of task (J=0,K=0) in the progress array
+  int32_t len[3];      // a, b, c
+  int32_t nJ, nK;      // column blocks along j and k
+  int32_t T;           // steps per column task: a + 1 + (kPR - 1) + (kPC - 1)
+  int32_t rowJ, rowK;  // int32 row strides of the j- and k-face planes
+  int32_t score_base;  // 2*alpha*(a+b+c)
+  int32_t out_idx;     // index into the score output
+  int32_t tb_idx;      // index among the batch's traceback triplets (-1: none)
+};
+
+struct Task {
+  int32_t trip, J, K, pad;
+};
+
+struct WaveParams {
+  const TripDesc* desc;
+  const Task* tasks;
+  int32_t ntasks;
+  int32_t KP;          // alphabet size + 1 (virtual residue)
+  const int8_t* seq;   // packed residue codes
+  const int32_t* sig;  // KP*KP table of sigma'' (x8 in traceback mode), VIRT row/col = 0
+  int32_t* faces;
+  int32_t* progress;   // one published step count per task, zeroed before launch
+  int32_t* queue;      // work-queue head, zeroed before launch
+  uint32_t* codes;     // packed 4-bit traceback codes (traceback mode)
+  int32_t* scores;     // per-triplet output
+  int32_t* err;        // device error word (bit 0: a bounded wait expired)
+  int32_t TI;          // publish progress every TI steps
+  int64_t wait_ns;     // a wait that sees no progress for this long gives up
+};
+
+struct WalkParams {
+  const TripDesc* desc;
+  const int32_t* tb_trips;   // triplet index of each traceback request
+  int32_t ntb;
+  const int8_t* seq;
+  const uint32_t* codes;
+  uint8_t* rows;             // per request: 3 rows of cap bytes, residue codes, 255 = gap
+  const int64_t* row_off;    // byte offset of each request's rows
+  const int32_t* row_cap;    // capacity (a+b+c) of each row
+  int32_t* aln_len;          // written: alignment length (the alignment is the last L bytes)
+  int32_t* err;              // bit 1: corrupt code met during a walk
+  int32_t NJ, NK;            // tile of the wavefront variant that wrote the codes
+};
+
+// Host-side launchers implemented in kernels.cu.
+int launch_wavefront(int nj, int nk, bool tb, const WaveParams& p, int grid, size_t smem,
+                     void* stream);
+int wavefront_occupancy(int nj, int nk, bool tb, size_t smem, int* blocks_per_sm);
+int launch_walk(const WalkParams& p, void* stream);
+size_t wavefront_smem_bytes(int nj, int nk, int KP);
+
+}  // namespace trioseq

@@ -1,0 +1,624 @@
+// runtime.cu — host runtime behind the C ABI of include/trioseq.h.
+//
+// Plan: scoring scheme validated and turned into the device tables of the shifted frame
+// (sigma'' = sigma - 2*alpha, a virtual residue row/column of zeros, x8 for traceback keys).
+// Batch: encoded + packed residues, per-triplet descriptors (engine.h), the ordered column-task
+// queue, and a device workspace (faces, progress flags, codes, outputs).
+// Queue order: tasks sorted by anti-diagonal D = J + K of their column block, then by the
+// triplet's rank in longest-processing-time order (largest cube first). Every producer of a
+// task, (J-1,K) and (J,K-1), has a smaller D and therefore an earlier queue slot. The LPT part
+// follows the paper's dynamic partition by cumulative cells (Sec. V-D), applied here to the
+// warps of one GPU instead of to GPUs.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdlib>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "engine.h"
+#include "trioseq.h"
+
+using namespace trioseq;
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  // Grow to at least `bytes` (contents are not preserved).
+  bool ensure(size_t bytes) {
+    if (bytes <= cap && p) return true;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    const size_t want = std::max<size_t>(bytes, 256);
+    if (cudaMalloc(&p, want) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    cap = want;
+    return true;
+  }
+  template <typename T>
+  T* as() const {
+    return reinterpret_cast<T*>(p);
+  }
+};
+
+struct HostPinned {
+  void* p = nullptr;
+  size_t cap = 0;
+  ~HostPinned() {
+    if (p) cudaFreeHost(p);
+  }
+  bool ensure(size_t bytes) {
+    if (bytes <= cap && p) return true;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    cap = 0;
+    const size_t want = std::max<size_t>(bytes, 4096);
+    if (cudaMallocHost(&p, want) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    cap = want;
+    return true;
+  }
+};
+
+// Device workspace of one in-flight batch.
+struct Workspace {
+  DevBuf inputs;    // packed residues | descriptors | tasks | traceback tables
+  DevBuf faces;     // j- and k-face planes
+  DevBuf progress;  // progress flags | queue head | error word
+  DevBuf codes;     // traceback codes
+  DevBuf scores;    // int32 per triplet
+  DevBuf rows;      // traceback rows
+  DevBuf lens;      // alignment lengths
+  HostPinned staging;
+};
+
+inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+struct Variant {
+  int nj, nk;
+};
+
+}  // namespace
+
+struct trioseq_plan_s {
+  int device = 0;
+  int sms = 0;
+  int K = 0;
+  int KP = 0;
+  char alphabet[kMaxAlphabet] = {};
+  int16_t lut[256];
+  std::vector<int32_t> sub;
+  int32_t gap = 0;
+  int32_t max_abs_sig2 = 0;        // max |sigma''| over the extended table
+  DevBuf sig_score, sig_tb;        // KP*KP int32 device tables
+  Workspace ws;                    // workspace of trioseq_align_batch
+  std::unique_ptr<trioseq_batch_s> last;  // last align_batch (traceback rows kept here)
+  int TI = 8;
+  int64_t wait_ns = 2000000000LL;  // 2 s without progress = give up
+  Variant score_variant{8, 8};
+  Variant tb_variant{4, 8};
+};
+
+struct trioseq_batch_s {
+  trioseq_plan_s* plan = nullptr;
+  Workspace* ws = nullptr;             // where it runs (owned if own_ws)
+  std::unique_ptr<Workspace> own_ws;
+  size_t n = 0;
+  uint32_t mode = 0;
+  Variant var{8, 8};
+  uint64_t cells = 0;
+  std::vector<TripDesc> desc;
+  std::vector<Task> tasks;
+  std::vector<int32_t> tb_trips;       // triplet index per traceback request
+  std::vector<int64_t> row_off;
+  std::vector<int32_t> row_cap;
+  std::vector<int32_t> tb_of;          // triplet -> traceback request (-1)
+  std::vector<int8_t> seq;             // packed residue codes (host copy)
+  size_t seq_bytes = 0, face_ints = 0, code_words = 0, rows_bytes = 0;
+  size_t off_desc = 0, off_tasks = 0, off_tb = 0, off_rowoff = 0, off_rowcap = 0, inputs_bytes = 0;
+  int grid = 0;
+  size_t smem = 0;
+  bool uploaded = false;
+  // results of the last run (host)
+  std::vector<uint8_t> h_rows;
+  std::vector<int32_t> h_lens;
+  bool have_rows = false;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+trioseq_status cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return TRIOSEQ_OK;
+  cudaGetLastError();
+  return e == cudaErrorMemoryAllocation ? TRIOSEQ_ENOMEM : TRIOSEQ_ECUDA;
+}
+
+int env_int(const char* name, int def) {
+  const char* v = std::getenv(name);
+  return v ? std::atoi(v) : def;
+}
+
+// Build the host side of a batch: encode, pack, describe, order the queue.
+trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, size_t n,
+                           uint32_t mode, trioseq_batch_s* bt) {
+  if (!trip && n) return TRIOSEQ_EINVAL;
+  if (mode > TRIOSEQ_WITH_TRACEBACK) return TRIOSEQ_EINVAL;
+  const bool tb = mode == TRIOSEQ_WITH_TRACEBACK;
+  bt->plan = plan;
+  bt->n = n;
+  bt->mode = mode;
+  bt->var = tb ? plan->tb_variant : plan->score_variant;
+  const int NJ = bt->var.nj, NK = bt->var.nk;
+  const int WJ = kPR * NJ, WK = kPC * NK, W = NJ * NK / 8;
+  // encode + pack (16-byte aligned sequences)
+  size_t total = 0;
+  for (size_t t = 0; t < n; t++)
+    for (int q = 0; q < 3; q++) {
+      if (trip[t].len[q] && !trip[t].s[q]) return TRIOSEQ_EINVAL;
+      if (trip[t].len[q] > (1u << 24)) return TRIOSEQ_EOVERFLOW;
+      total += align_up(trip[t].len[q], 16);
+    }
+  bt->seq.assign(std::max<size_t>(total, 16), 0);
+  bt->desc.resize(n);
+  bt->tb_of.assign(n, -1);
+  bt->tb_trips.clear();
+  bt->row_off.clear();
+  bt->row_cap.clear();
+  size_t pos = 0, face = 0, codes = 0, rows = 0;
+  int64_t prog = 0;
+  bt->cells = 0;
+  for (size_t t = 0; t < n; t++) {
+    TripDesc& d = bt->desc[t];
+    int64_t sumlen = 0;
+    for (int q = 0; q < 3; q++) {
+      const uint32_t L = trip[t].len[q];
+      d.s_off[q] = (int64_t)pos;
+      d.len[q] = (int32_t)L;
+      const unsigned char* src = reinterpret_cast<const unsigned char*>(trip[t].s[q]);
+      for (uint32_t e = 0; e < L; e++) {
+        const int16_t code = plan->lut[src[e]];
+        if (code < 0) return TRIOSEQ_EINVAL;
+        bt->seq[pos + e] = (int8_t)code;
+      }
+      pos += align_up(L, 16);
+      sumlen += L;
+    }
+    // |M'| <= max|sigma''| * (a+b+c); keys need 8*|M'| + 8 below 2^29.
+    if ((int64_t)plan->max_abs_sig2 * sumlen >= (1LL << 26) - 1) return TRIOSEQ_EOVERFLOW;
+    if (2LL * (int64_t)std::abs(plan->gap) * sumlen >= (1LL << 30)) return TRIOSEQ_EOVERFLOW;
+    const int a = d.len[0], b = d.len[1], c = d.len[2];
+    d.nJ = (b + 1 + WJ - 1) / WJ;
+    d.nK = (c + 1 + WK - 1) / WK;
+    d.T = a + 1 + (kPR - 1) + (kPC - 1);
+    d.rowJ = d.nK * WK + 4;
+    d.rowK = d.nJ * WJ + 4;
+    d.fj_off = (int64_t)face;
+    face += (size_t)(d.nJ - 1) * (size_t)(a + 1) * (size_t)d.rowJ;
+    d.fk_off = (int64_t)face;
+    face += (size_t)(d.nK - 1) * (size_t)(a + 1) * (size_t)d.rowK;
+    face = align_up(face, 4);
+    d.prog_base = prog;
+    prog += (int64_t)d.nJ * d.nK;
+    d.score_base = 2 * plan->gap * (int32_t)sumlen;
+    d.out_idx = (int32_t)t;
+    d.tb_idx = -1;
+    d.code_off = -1;
+    if (tb) {
+      d.code_off = (int64_t)codes;
+      codes += (size_t)d.nJ * d.nK * (size_t)d.T * 32 * W;
+      d.tb_idx = (int32_t)bt->tb_trips.size();
+      bt->tb_of[t] = d.tb_idx;
+      bt->tb_trips.push_back((int32_t)t);
+      const int cap = std::max(1, a + b + c);
+      bt->row_off.push_back((int64_t)rows);
+      bt->row_cap.push_back(cap);
+      rows += align_up((size_t)3 * cap, 16);
+    }
+    bt->cells += (uint64_t)a * (uint64_t)b * (uint64_t)c;
+  }
+  bt->seq_bytes = bt->seq.size();
+  bt->face_ints = std::max<size_t>(face, 4);
+  bt->code_words = std::max<size_t>(codes, 4);
+  bt->rows_bytes = std::max<size_t>(rows, 16);
+  // queue: (anti-diagonal, LPT rank of the triplet, J)
+  std::vector<int32_t> lpt(n);
+  {
+    std::vector<int32_t> order(n);
+    for (size_t t = 0; t < n; t++) order[t] = (int32_t)t;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
+      const auto vol = [&](int32_t t) {
+        return (double)(bt->desc[t].len[0] + 1) * (bt->desc[t].len[1] + 1) *
+               (bt->desc[t].len[2] + 1);
+      };
+      return vol(x) > vol(y);
+    });
+    for (size_t r = 0; r < n; r++) lpt[order[r]] = (int32_t)r;
+  }
+  bt->tasks.clear();
+  bt->tasks.reserve((size_t)prog);
+  for (size_t t = 0; t < n; t++) {
+    const TripDesc& d = bt->desc[t];
+    for (int J = 0; J < d.nJ; J++)
+      for (int K = 0; K < d.nK; K++) bt->tasks.push_back(Task{(int32_t)t, J, K, 0});
+  }
+  std::stable_sort(bt->tasks.begin(), bt->tasks.end(), [&](const Task& x, const Task& y) {
+    const int dx = x.J + x.K, dy = y.J + y.K;
+    if (dx != dy) return dx < dy;
+    if (lpt[x.trip] != lpt[y.trip]) return lpt[x.trip] < lpt[y.trip];
+    return x.J < y.J;
+  });
+  // device layout of the input block
+  size_t off = align_up(bt->seq_bytes, 256);
+  bt->off_desc = off;
+  off = align_up(off + sizeof(TripDesc) * std::max<size_t>(n, 1), 256);
+  bt->off_tasks = off;
+  off = align_up(off + sizeof(Task) * std::max<size_t>(bt->tasks.size(), 1), 256);
+  bt->off_tb = off;
+  off = align_up(off + sizeof(int32_t) * std::max<size_t>(bt->tb_trips.size(), 1), 256);
+  bt->off_rowoff = off;
+  off = align_up(off + sizeof(int64_t) * std::max<size_t>(bt->row_off.size(), 1), 256);
+  bt->off_rowcap = off;
+  off = align_up(off + sizeof(int32_t) * std::max<size_t>(bt->row_cap.size(), 1), 256);
+  bt->inputs_bytes = off;
+  // launch shape
+  bt->smem = wavefront_smem_bytes(NJ, NK, plan->KP);
+  int bpm = 0;
+  if (wavefront_occupancy(NJ, NK, tb, bt->smem, &bpm) != 0 || bpm <= 0) return TRIOSEQ_ECUDA;
+  const int want = env_int("TRIOSEQ_CTAS_PER_SM", bpm);
+  bt->grid = plan->sms * std::max(1, std::min(bpm, want));
+  return TRIOSEQ_OK;
+}
+
+// Size the workspace and copy the inputs of `bt` into it (stream-ordered).
+trioseq_status upload(trioseq_batch_s* bt, cudaStream_t st) {
+  Workspace& ws = *bt->ws;
+  const bool tb = bt->mode == TRIOSEQ_WITH_TRACEBACK;
+  const size_t nprog = bt->tasks.size() + 64;
+  if (!ws.inputs.ensure(bt->inputs_bytes) || !ws.faces.ensure(bt->face_ints * sizeof(int32_t)) ||
+      !ws.progress.ensure(nprog * sizeof(int32_t)) ||
+      !ws.scores.ensure(std::max<size_t>(bt->n, 1) * sizeof(int32_t)) ||
+      (tb && (!ws.codes.ensure(bt->code_words * sizeof(uint32_t)) ||
+              !ws.rows.ensure(bt->rows_bytes) ||
+              !ws.lens.ensure(std::max<size_t>(bt->tb_trips.size(), 1) * sizeof(int32_t)))) ||
+      !ws.staging.ensure(bt->inputs_bytes))
+    return TRIOSEQ_ENOMEM;
+  char* h = reinterpret_cast<char*>(ws.staging.p);
+  std::memcpy(h, bt->seq.data(), bt->seq_bytes);
+  std::memcpy(h + bt->off_desc, bt->desc.data(), sizeof(TripDesc) * bt->n);
+  std::memcpy(h + bt->off_tasks, bt->tasks.data(), sizeof(Task) * bt->tasks.size());
+  if (tb) {
+    std::memcpy(h + bt->off_tb, bt->tb_trips.data(), sizeof(int32_t) * bt->tb_trips.size());
+    std::memcpy(h + bt->off_rowoff, bt->row_off.data(), sizeof(int64_t) * bt->row_off.size());
+    std::memcpy(h + bt->off_rowcap, bt->row_cap.data(), sizeof(int32_t) * bt->row_cap.size());
+  }
+  cudaError_t e = cudaMemcpyAsync(ws.inputs.p, h, bt->inputs_bytes, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_status(e);
+  bt->uploaded = true;
+  return TRIOSEQ_OK;
+}
+
+// One pass of the hot path on device-resident inputs.
+trioseq_status run(trioseq_batch_s* bt, cudaStream_t st) {
+  Workspace& ws = *bt->ws;
+  trioseq_plan_s* plan = bt->plan;
+  const bool tb = bt->mode == TRIOSEQ_WITH_TRACEBACK;
+  const size_t nprog = bt->tasks.size() + 64;
+  int32_t* prog = ws.progress.as<int32_t>();
+  int32_t* queue = prog + bt->tasks.size();
+  int32_t* err = queue + 32;
+  cudaError_t e = cudaMemsetAsync(prog, 0, nprog * sizeof(int32_t), st);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (bt->n == 0) return TRIOSEQ_OK;
+  char* in = ws.inputs.as<char>();
+  WaveParams p{};
+  p.desc = reinterpret_cast<const TripDesc*>(in + bt->off_desc);
+  p.tasks = reinterpret_cast<const Task*>(in + bt->off_tasks);
+  p.ntasks = (int32_t)bt->tasks.size();
+  p.KP = plan->KP;
+  p.seq = reinterpret_cast<const int8_t*>(in);
+  p.sig = tb ? plan->sig_tb.as<int32_t>() : plan->sig_score.as<int32_t>();
+  p.faces = ws.faces.as<int32_t>();
+  p.progress = prog;
+  p.queue = queue;
+  p.codes = tb ? ws.codes.as<uint32_t>() : nullptr;
+  p.scores = ws.scores.as<int32_t>();
+  p.err = err;
+  p.TI = std::max(1, plan->TI);
+  p.wait_ns = plan->wait_ns;
+  if (launch_wavefront(bt->var.nj, bt->var.nk, tb, p, bt->grid, bt->smem, st) != 0)
+    return cuda_status(cudaGetLastError());
+  if (tb && !bt->tb_trips.empty()) {
+    WalkParams w{};
+    w.desc = p.desc;
+    w.tb_trips = reinterpret_cast<const int32_t*>(in + bt->off_tb);
+    w.ntb = (int32_t)bt->tb_trips.size();
+    w.seq = p.seq;
+    w.codes = p.codes;
+    w.rows = ws.rows.as<uint8_t>();
+    w.row_off = reinterpret_cast<const int64_t*>(in + bt->off_rowoff);
+    w.row_cap = reinterpret_cast<const int32_t*>(in + bt->off_rowcap);
+    w.aln_len = ws.lens.as<int32_t>();
+    w.err = err;
+    w.NJ = bt->var.nj;
+    w.NK = bt->var.nk;
+    if (launch_walk(w, st) != 0) return cuda_status(cudaGetLastError());
+  }
+  return TRIOSEQ_OK;
+}
+
+// Wait for the run, check the error word, fetch scores (and traceback rows).
+trioseq_status fetch(trioseq_batch_s* bt, cudaStream_t st, int32_t* scores_out) {
+  Workspace& ws = *bt->ws;
+  const bool tb = bt->mode == TRIOSEQ_WITH_TRACEBACK;
+  int32_t herr = 0;
+  cudaError_t e = cudaSuccess;
+  if (bt->n) {
+    int32_t* err = ws.progress.as<int32_t>() + bt->tasks.size() + 32;
+    e = cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && scores_out)
+      e = cudaMemcpyAsync(scores_out, ws.scores.p, bt->n * sizeof(int32_t),
+                          cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && tb && !bt->tb_trips.empty()) {
+      bt->h_rows.resize(bt->rows_bytes);
+      bt->h_lens.resize(bt->tb_trips.size());
+      e = cudaMemcpyAsync(bt->h_rows.data(), ws.rows.p, bt->rows_bytes, cudaMemcpyDeviceToHost,
+                          st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(bt->h_lens.data(), ws.lens.p, bt->h_lens.size() * sizeof(int32_t),
+                            cudaMemcpyDeviceToHost, st);
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_status(e);
+  if (herr & 1) return TRIOSEQ_ETIMEOUT;
+  if (herr & 2) return TRIOSEQ_ECUDA;
+  bt->have_rows = tb;
+  return TRIOSEQ_OK;
+}
+
+trioseq_status copy_alignment(const trioseq_batch_s* bt, size_t idx, char* r0, char* r1, char* r2,
+                              size_t cap, size_t* aln_len) {
+  if (!bt || !bt->have_rows || idx >= bt->n || !aln_len) return TRIOSEQ_EINVAL;
+  const int32_t q = bt->tb_of[idx];
+  if (q < 0) return TRIOSEQ_EINVAL;
+  const int32_t L = bt->h_lens[q];
+  if (L < 0) return TRIOSEQ_ECUDA;
+  *aln_len = (size_t)L;
+  if (L == 0) return TRIOSEQ_OK;
+  if (cap < (size_t)L || !r0 || !r1 || !r2) return TRIOSEQ_EINVAL;
+  const int32_t rc = bt->row_cap[q];
+  const uint8_t* base = bt->h_rows.data() + bt->row_off[q];
+  const char* alpha = bt->plan->alphabet;
+  char* out[3] = {r0, r1, r2};
+  for (int s = 0; s < 3; s++) {
+    const uint8_t* row = base + (size_t)s * rc + (rc - L);
+    for (int32_t t = 0; t < L; t++) out[s][t] = row[t] == 255 ? '-' : alpha[row[t]];
+  }
+  return TRIOSEQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* trioseq_strerror(trioseq_status st) {
+  switch (st) {
+    case TRIOSEQ_OK: return "ok";
+    case TRIOSEQ_EINVAL: return "invalid argument";
+    case TRIOSEQ_ENOMEM: return "out of memory";
+    case TRIOSEQ_EAGAIN: return "not ready / queue full";
+    case TRIOSEQ_EOVERFLOW: return "score bound exceeds the integer range";
+    case TRIOSEQ_ETIMEOUT: return "bounded device wait expired";
+    case TRIOSEQ_ECUDA: return "CUDA error or no usable GPU";
+    case TRIOSEQ_ENOTIMPL: return "not implemented";
+  }
+  return "unknown status";
+}
+
+trioseq_status trioseq_plan(const trioseq_scoring* sc, uint32_t max_len_hint, uint32_t flags,
+                            trioseq_plan_t* out) {
+  (void)max_len_hint;
+  if (!out) return TRIOSEQ_EINVAL;
+  *out = nullptr;
+  if (!sc || !sc->alphabet || !sc->sub || flags != 0) return TRIOSEQ_EINVAL;
+  const int K = sc->alphabet_size;
+  if (K < 1 || K > kMaxAlphabet || sc->gap > 0 || sc->gap < -127) return TRIOSEQ_EINVAL;
+  std::unique_ptr<trioseq_plan_s> plan(new (std::nothrow) trioseq_plan_s());
+  if (!plan) return TRIOSEQ_ENOMEM;
+  for (int i = 0; i < 256; i++) plan->lut[i] = -1;
+  for (int i = 0; i < K; i++) {
+    const unsigned char ch = (unsigned char)sc->alphabet[i];
+    if (plan->lut[ch] >= 0) return TRIOSEQ_EINVAL;  // duplicate residue
+    plan->lut[ch] = (int16_t)i;
+    plan->alphabet[i] = (char)ch;
+  }
+  for (int i = 0; i < K; i++)
+    for (int j = 0; j < K; j++)
+      if (sc->sub[i * K + j] != sc->sub[j * K + i]) return TRIOSEQ_EINVAL;
+  plan->K = K;
+  plan->KP = K + 1;
+  plan->gap = sc->gap;
+  plan->sub.assign(sc->sub, sc->sub + K * K);
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return TRIOSEQ_ECUDA;
+  }
+  plan->device = dev;
+  if (cudaDeviceGetAttribute(&plan->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return TRIOSEQ_ECUDA;
+  }
+  const int KP = K + 1;
+  std::vector<int32_t> s2((size_t)KP * KP, 0), s8((size_t)KP * KP, 0);
+  int32_t mx = 0;
+  for (int i = 0; i < K; i++)
+    for (int j = 0; j < K; j++) {
+      const int32_t v = (int32_t)sc->sub[i * K + j] - 2 * sc->gap;  // sigma'' = sigma - 2 alpha
+      s2[(size_t)i * KP + j] = v;
+      s8[(size_t)i * KP + j] = 8 * v;
+      mx = std::max(mx, std::abs(v));
+    }
+  plan->max_abs_sig2 = std::max(mx, 1);
+  if (!plan->sig_score.ensure(s2.size() * 4) || !plan->sig_tb.ensure(s8.size() * 4))
+    return TRIOSEQ_ENOMEM;
+  if (cudaMemcpy(plan->sig_score.p, s2.data(), s2.size() * 4, cudaMemcpyHostToDevice) !=
+          cudaSuccess ||
+      cudaMemcpy(plan->sig_tb.p, s8.data(), s8.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+    return cuda_status(cudaGetLastError());
+  plan->TI = std::max(1, env_int("TRIOSEQ_TI", 8));
+  const char* sv = std::getenv("TRIOSEQ_SCORE_TILE");
+  if (sv && std::strlen(sv) >= 3) plan->score_variant = Variant{sv[0] - '0', sv[2] - '0'};
+  const char* tv = std::getenv("TRIOSEQ_TB_TILE");
+  if (tv && std::strlen(tv) >= 3) plan->tb_variant = Variant{tv[0] - '0', tv[2] - '0'};
+  *out = plan.release();
+  return TRIOSEQ_OK;
+}
+
+trioseq_status trioseq_plan_destroy(trioseq_plan_t plan) {
+  if (!plan) return TRIOSEQ_OK;
+  DeviceGuard g(plan->device);
+  cudaDeviceSynchronize();
+  delete plan;
+  return TRIOSEQ_OK;
+}
+
+trioseq_status trioseq_align_batch(trioseq_plan_t plan, const trioseq_triplet* triplets, size_t n,
+                                   uint32_t mode, int32_t* scores_out, void* stream) {
+  if (!plan || (n && !scores_out)) return TRIOSEQ_EINVAL;
+  DeviceGuard g(plan->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  std::unique_ptr<trioseq_batch_s> bt(new (std::nothrow) trioseq_batch_s());
+  if (!bt) return TRIOSEQ_ENOMEM;
+  plan->last.reset();
+  trioseq_status s = build_batch(plan, triplets, n, mode, bt.get());
+  if (s != TRIOSEQ_OK) return s;
+  bt->ws = &plan->ws;
+  if ((s = upload(bt.get(), st)) != TRIOSEQ_OK) return s;
+  if ((s = run(bt.get(), st)) != TRIOSEQ_OK) return s;
+  if ((s = fetch(bt.get(), st, scores_out)) != TRIOSEQ_OK) return s;
+  bt->seq.clear();
+  bt->seq.shrink_to_fit();
+  plan->last = std::move(bt);
+  return TRIOSEQ_OK;
+}
+
+trioseq_status trioseq_traceback(trioseq_plan_t plan, size_t idx, char* row0, char* row1,
+                                 char* row2, size_t cap, size_t* aln_len) {
+  if (!plan || !plan->last) return TRIOSEQ_EINVAL;
+  return copy_alignment(plan->last.get(), idx, row0, row1, row2, cap, aln_len);
+}
+
+trioseq_status trioseq_batch_create(trioseq_plan_t plan, const trioseq_triplet* triplets,
+                                    size_t n, uint32_t mode, trioseq_batch_t* out) {
+  if (!plan || !out) return TRIOSEQ_EINVAL;
+  *out = nullptr;
+  DeviceGuard g(plan->device);
+  std::unique_ptr<trioseq_batch_s> bt(new (std::nothrow) trioseq_batch_s());
+  if (!bt) return TRIOSEQ_ENOMEM;
+  trioseq_status s = build_batch(plan, triplets, n, mode, bt.get());
+  if (s != TRIOSEQ_OK) return s;
+  bt->own_ws.reset(new (std::nothrow) Workspace());
+  if (!bt->own_ws) return TRIOSEQ_ENOMEM;
+  bt->ws = bt->own_ws.get();
+  if ((s = upload(bt.get(), nullptr)) != TRIOSEQ_OK) return s;
+  if (cudaStreamSynchronize(nullptr) != cudaSuccess) return cuda_status(cudaGetLastError());
+  *out = bt.release();
+  return TRIOSEQ_OK;
+}
+
+trioseq_status trioseq_batch_run(trioseq_batch_t bt, void* stream) {
+  if (!bt) return TRIOSEQ_EINVAL;
+  DeviceGuard g(bt->plan->device);
+  return run(bt, (cudaStream_t)stream);
+}
+
+trioseq_status trioseq_batch_scores(trioseq_batch_t bt, void* stream, int32_t* scores_out) {
+  if (!bt || (bt->n && !scores_out)) return TRIOSEQ_EINVAL;
+  DeviceGuard g(bt->plan->device);
+  return fetch(bt, (cudaStream_t)stream, scores_out);
+}
+
+trioseq_status trioseq_batch_device_scores(trioseq_batch_t bt, int32_t** d_scores) {
+  if (!bt || !d_scores) return TRIOSEQ_EINVAL;
+  *d_scores = bt->ws->scores.as<int32_t>();
+  return TRIOSEQ_OK;
+}
+
+trioseq_status trioseq_batch_alignment(trioseq_batch_t bt, size_t idx, char* row0, char* row1,
+                                       char* row2, size_t cap, size_t* aln_len) {
+  return copy_alignment(bt, idx, row0, row1, row2, cap, aln_len);
+}
+
+trioseq_status trioseq_batch_info(trioseq_batch_t bt, size_t* n, uint64_t* cells, uint64_t* tasks,
+                                  int32_t* tile_j, int32_t* tile_k) {
+  if (!bt) return TRIOSEQ_EINVAL;
+  if (n) *n = bt->n;
+  if (cells) *cells = bt->cells;
+  if (tasks) *tasks = bt->tasks.size();
+  if (tile_j) *tile_j = bt->var.nj;
+  if (tile_k) *tile_k = bt->var.nk;
+  return TRIOSEQ_OK;
+}
+
+trioseq_status trioseq_batch_destroy(trioseq_batch_t bt) {
+  if (!bt) return TRIOSEQ_OK;
+  DeviceGuard g(bt->plan->device);
+  cudaDeviceSynchronize();
+  delete bt;
+  return TRIOSEQ_OK;
+}
+
+trioseq_status trioseq_server_create(const trioseq_plan_t* plans, int32_t nplans,
+                                     size_t hbm_budget, trioseq_server_t* out) {
+  (void)plans;
+  (void)nplans;
+  (void)hbm_budget;
+  if (out) *out = nullptr;
+  return TRIOSEQ_ENOTIMPL;
+}
+
+trioseq_status trioseq_submit(trioseq_server_t, const trioseq_triplet*, int32_t, uint32_t,
+                              uint64_t*) {
+  return TRIOSEQ_ENOTIMPL;
+}
+
+trioseq_status trioseq_poll(trioseq_server_t, uint64_t, int32_t*, char* [3], size_t, size_t*) {
+  return TRIOSEQ_ENOTIMPL;
+}
+
+trioseq_status trioseq_server_destroy(trioseq_server_t) { return TRIOSEQ_ENOTIMPL; }
+
+}  // extern "C"
