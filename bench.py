@@ -1,0 +1,427 @@
+#!/usr/bin/env python
+"""Benchmark of the exact 3-way global alignment engine on GB300.
+
+Metric: GCUPS = sum over triplets of |S0|*|S1|*|S2| / seconds / 1e9 (the paper's TCUPS
+numerator, Sec. V-A, scaled to giga). One step = one full pass of the hot path over the
+workload: workspace reset, the persistent wavefront kernel (all cells of Eq. 1, with the packed
+traceback-code stream in traceback mode), and the traceback walk.
+
+Default workload: one related DNA triplet, ancestor length 1000 with three descendants
+(5% substitutions, 2% indels of geometric length, mean 2), match +2 / mismatch -1 / gap -2,
+score + traceback (~1e9 cells).
+
+value : device-resident inputs (uploaded once), CUDA events on the launching stream around each
+        step, L2 flushed (256 MiB write) between timed steps outside the events.
+e2e   : the public C call trioseq_align_batch on host strings per step (encode, H2D from pinned
+        staging, kernels, D2H of scores and alignment), host wall clock.
+roofline: the wavefront kernel's int32 work (13 algorithmic ops per cell: 7 adds + 6 max) over
+        its own event-timed duration, against SMs x 128 int32 lanes x the median SM clock
+        sampled during the timed region.
+cpu_baseline / --impl reference: the C++ oracle (single core) on a bounded prefix sample.
+
+Under torchrun (N > 1) every rank aligns its own replica of the workload (triplets are
+independent; no collective on the data path) and the slowest rank's time is reported.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "GCUPS (3D cells/s) and % of INT32 roofline; batched vs per-triplet; p50/p99 lat"
+OPS_PER_CELL = 13          # 7 adds + 6 max per cell (factored Eq. 1)
+INT32_LANES_PER_SM = 128   # nominal; see the design doc for the measured VIADDMNMX/IMNMX rate
+CODE_BYTES_PER_CELL = 0.5  # packed 4-bit traceback code
+
+
+def workloads():
+    from paper_2605_28400_gb300 import synth
+    return {
+        "dna1000": (synth.config1, "one related DNA triplet, ancestor 1000, 5% subs, 2% indels "
+                                   "(geometric mean 2), +2/-1/-2, score + traceback"),
+        "protein4000": (synth.config3, "one related protein triplet, ancestor 4000, 15% subs, "
+                                       "3% indels (geometric mean 3), seeded 20x20 matrix, "
+                                       "gap -4, score only"),
+        "batch4096": (synth.config2, "4096 related DNA triplets, ancestor lengths U[100,300], "
+                                     "score only, one persistent launch"),
+        "dna128": (synth.config0, "one triplet of independent uniform DNA, 128 each, score + "
+                                  "traceback"),
+    }
+
+
+# ------------------------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons, kept if taken inside [t0, t1]."""
+
+    FIELDS = ("uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid: str | None):
+        self.uuid = uuid
+        self.samples = []
+        self.proc = None
+        self.thread = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True,
+                bufsize=1)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            if self.uuid and self.uuid not in f[0]:
+                continue
+            self.samples.append((time.time(), f))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0: float, t1: float) -> dict:
+        inside = [f for (t, f) in self.samples if t0 <= t <= t1]
+        note = "samples inside the timed region"
+        if not inside and self.samples:
+            inside = [min(self.samples, key=lambda s: abs(s[0] - 0.5 * (t0 + t1)))[1]]
+            note = "nearest sample to the timed region"
+        if not inside:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(f[1]) for f in inside if num(f[1])]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for f in inside:
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": num(inside[0][2]), "reasons": sorted(reasons),
+                "power_w_max": max((num(f[3]) or 0.0) for f in inside),
+                "samples": len(inside), "note": note}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "engine.h"):
+        with open(os.path.join(ROOT, "paper_2605_28400_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(key: str):
+    """DRAM bytes per launch of the wavefront kernel from the committed ncu summary, or None
+    when the kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "wavefront_traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        e = d.get(key)
+        if e and e.get("kernel_hash") == kernel_source_hash():
+            return e.get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        pass
+    return None
+
+
+def triplet_strings(w):
+    from paper_2605_28400_gb300 import synth
+    return [[synth.to_str(s, w.scoring.alphabet) for s in t] for t in w.triplets]
+
+
+# ------------------------------------------------------------------------------------------
+def cpu_oracle_sample(w, target_cells: float, traceback: bool):
+    """Time the oracle on prefixes of the workload's first triplet(s) (~target_cells cells)."""
+    import oracle
+    import numpy as np
+    sc = w.scoring
+    if len(w.triplets) == 1:
+        t = w.triplets[0]
+        L = int(round(target_cells ** (1.0 / 3.0)))
+        L = max(8, min(L, min(len(x) for x in t)))
+        sample = [tuple(np.ascontiguousarray(x[:L]) for x in t)]
+        desc = f"prefixes of length {L} of the workload triplet"
+    else:
+        sample, tot = [], 0
+        for t in w.triplets:
+            sample.append(t)
+            tot += len(t[0]) * len(t[1]) * len(t[2])
+            if tot >= target_cells:
+                break
+        desc = f"first {len(sample)} triplets of the workload"
+    cells = sum(len(a) * len(b) * len(c) for a, b, c in sample)
+    t0 = time.perf_counter()
+    for s in sample:
+        oracle.align(*s, sc.sub, sc.gap, traceback=traceback)
+    dt = time.perf_counter() - t0
+    mode = "score + traceback" if traceback else "score only"
+    return {"value": cells / dt / 1e9, "unit": "GCUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{desc} ({cells} cells, {mode}, {dt:.1f} s)"}, dt
+
+
+def run_reference(args, rank: int):
+    if rank != 0:
+        return
+    ws = workloads()
+    make, desc = ws[args.workload]
+    w = make()
+    tb = w.traceback
+    import oracle
+    oracle.build()
+    # each step: a bounded sample (~2.5e7 cells) of the workload on one host core
+    samples = []
+    for i in range(args.warmup + args.steps):
+        cb, dt = cpu_oracle_sample(w, 2.5e7, tb)
+        if i >= args.warmup:
+            samples.append((cb, dt))
+    v = statistics.mean(c["value"] for c, _ in samples)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GCUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.mean(dt for _, dt in samples),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic",
+            "config": {"workload": f"{w.name}: {desc}", "reference": "CPU oracle (C++, "
+                       "int64), bounded prefix sample per step"},
+            "cpu_baseline": dict(samples[-1][0], value=v),
+            "e2e": {"value": v, "unit": "GCUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
+def time_batch(B, torch, bt, steps: int, warmup: int, stream, flush, n):
+    """Run a device-resident batch; returns (per-step event ms, per-step kernel ms, scores)."""
+    B.trioseq_batch_profile(bt, True)
+    for _ in range(warmup):
+        B.trioseq_batch_run(bt, stream)
+    torch.cuda.synchronize()
+    step_ms, kern_ms, walk_ms = [], [], []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(steps):
+        if flush is not None:
+            flush.zero_()
+        e0.record(stream)
+        B.trioseq_batch_run(bt, stream)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        k, wk = B.trioseq_batch_timing(bt)
+        kern_ms.append(k)
+        walk_ms.append(wk)
+    scores = B.trioseq_batch_scores(bt, n, stream)
+    return step_ms, kern_ms, walk_ms, scores
+
+
+def aux_measurements(B, torch, stream, flush, sms, clock_mhz):
+    """Secondary lines of the metric: protein n=4000 score-only roofline, and the 4096-triplet
+    batch in one persistent launch versus one launch per triplet."""
+    from paper_2605_28400_gb300 import synth
+    out = {}
+    w = synth.config3()
+    plan = B.trioseq_plan(w.scoring.alphabet, w.scoring.sub, w.scoring.gap)
+    bt = B.trioseq_batch_create(plan, triplet_strings(w), B.SCORE_ONLY)
+    sm, km, _, sc = time_batch(B, torch, bt, 5, 2, stream, flush, 1)
+    kmean = statistics.mean(km)
+    ach = OPS_PER_CELL * w.cells / (kmean / 1e3) / 1e12
+    peak = sms * INT32_LANES_PER_SM * clock_mhz * 1e6 / 1e12
+    out["protein4000_score_only"] = {
+        "gcups": w.cells / (statistics.mean(sm) / 1e3) / 1e9, "kernel_ms": kmean,
+        "cells": w.cells, "score": int(sc[0]),
+        "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TOPS (int32)",
+                     "frac": ach / peak}}
+    B.trioseq_batch_destroy(bt)
+    B.trioseq_plan_destroy(plan)
+
+    w = synth.config2()
+    strs = triplet_strings(w)
+    plan = B.trioseq_plan(w.scoring.alphabet, w.scoring.sub, w.scoring.gap)
+    bt = B.trioseq_batch_create(plan, strs, B.SCORE_ONLY)
+    sm, km, _, sc_batched = time_batch(B, torch, bt, 5, 2, stream, flush, len(strs))
+    batched = w.cells / (statistics.mean(sm) / 1e3) / 1e9
+    B.trioseq_batch_destroy(bt)
+    singles = [B.trioseq_batch_create(plan, [s], B.SCORE_ONLY) for s in strs]
+    for b in singles[:64]:
+        B.trioseq_batch_run(b, stream)
+    torch.cuda.synchronize()
+    reps = []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(2):
+        if flush is not None:
+            flush.zero_()
+        e0.record(stream)
+        for b in singles:
+            B.trioseq_batch_run(b, stream)
+        e1.record(stream)
+        e1.synchronize()
+        reps.append(e0.elapsed_time(e1))
+    same = all(int(B.trioseq_batch_scores(b, 1, stream)[0]) == int(sc_batched[i])
+               for i, b in enumerate(singles))
+    for b in singles:
+        B.trioseq_batch_destroy(b)
+    B.trioseq_plan_destroy(plan)
+    per_triplet = w.cells / (statistics.mean(reps) / 1e3) / 1e9
+    out["batch4096_score_only"] = {
+        "batched_gcups": batched, "per_triplet_launch_gcups": per_triplet,
+        "batched_over_per_triplet": batched / per_triplet, "identical_scores": bool(same),
+        "cells": w.cells}
+    return out
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(workloads()), default="dna1000")
+    ap.add_argument("--no-aux", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_2605_28400_gb300 import binding as B
+    B.load()
+    make, desc = workloads()[args.workload]
+    w = make()
+    tb = w.traceback
+    mode = B.WITH_TRACEBACK if tb else B.SCORE_ONLY
+    strs = triplet_strings(w)
+    props = torch.cuda.get_device_properties(local)
+    sms = props.multi_processor_count
+    uuid = str(getattr(props, "uuid", "") or "")
+    uuid = uuid if uuid.startswith("GPU-") else (f"GPU-{uuid}" if uuid else None)
+
+    plan = B.trioseq_plan(w.scoring.alphabet, w.scoring.sub, w.scoring.gap)
+    bt = B.trioseq_batch_create(plan, strs, mode)
+    info = B.trioseq_batch_info(bt)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    sampler = ClockSampler(uuid)
+    time.sleep(0.2)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    step_ms, kern_ms, walk_ms, scores = time_batch(B, torch, bt, args.steps, args.warmup, stream,
+                                                   flush, len(strs))
+    torch.cuda.synchronize()
+    t1 = time.time()
+    if dist:
+        dist.barrier()
+    clocks = sampler.summary(t0, t1)
+
+    total_ms = sum(step_ms)
+    if dist:
+        tt = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    ms_step = total_ms / args.steps
+    value = world * w.cells / (ms_step / 1e3) / 1e9
+
+    # e2e through the public C call on host strings
+    e2e_ms = []
+    for i in range(max(3, min(args.steps, 20)) + 2):
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        s2 = B.trioseq_align_batch(plan, strs, mode, stream)
+        if tb:
+            B.trioseq_traceback(plan, 0)
+        e2e_ms.append((time.perf_counter() - a) * 1e3)
+    e2e_ms = e2e_ms[2:]
+    h2d, d2h = B.trioseq_plan_io_bytes(plan)
+    assert s2.tolist() == scores.tolist(), "e2e and device-resident scores differ"
+    e2e_total = sum(e2e_ms)
+    if dist:
+        tt = torch.tensor([e2e_total], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_total = float(tt.item())
+    e2e_val = world * w.cells / (e2e_total / len(e2e_ms) / 1e3) / 1e9
+
+    clock_mhz = clocks.get("sm_mhz") or 2070.0
+    kmean = statistics.mean(kern_ms)
+    achieved = OPS_PER_CELL * w.cells / (kmean / 1e3) / 1e12
+    peak = sms * INT32_LANES_PER_SM * clock_mhz * 1e6 / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOPS (int32)",
+            "frac": achieved / peak,
+            "traffic": measured_traffic(f"{args.workload}"),
+            "kernel": "wavefront_kernel", "kernel_ms": kmean,
+            "peak_basis": f"{sms} SMs x {INT32_LANES_PER_SM} int32 ops/clk x median SM clock "
+                          f"{clock_mhz:.0f} MHz sampled in the timed region"}
+    if tb:
+        roof["code_stream_gbs"] = CODE_BYTES_PER_CELL * w.cells / (kmean / 1e3) / 1e9
+
+    line = {"metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": f"{w.name}: {desc}", "cells_per_step": w.cells,
+                       "triplets": len(strs), "mode": "score+traceback" if tb else "score",
+                       "column_tasks": info["tasks"], "tile": f"{info['tile'][0]}x{info['tile'][1]}",
+                       "l2": "256 MiB flush between timed steps (outside the events)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roof,
+            "e2e": {"value": e2e_val, "unit": "GCUPS", "h2d_bytes_per_step": int(h2d),
+                    "d2h_bytes_per_step": int(d2h), "ms_per_step": statistics.mean(e2e_ms)},
+            "gpu_launches": world * args.steps * (2 if tb else 1),
+            "clocks": clocks,
+            "score": int(scores[0])}
+    B.trioseq_batch_destroy(bt)
+    B.trioseq_plan_destroy(plan)
+
+    if rank == 0 and not args.no_aux:
+        line["aux"] = aux_measurements(B, torch, stream, flush, sms, clock_mhz)
+    if rank == 0 and not args.no_cpu:
+        cb, _ = cpu_oracle_sample(w, 2.5e8, tb)
+        line["cpu_baseline"] = cb
+    sampler.stop()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

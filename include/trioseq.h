@@ -143,6 +143,18 @@ trioseq_status trioseq_batch_info(trioseq_batch_t batch, size_t* n, uint64_t* ce
 
 trioseq_status trioseq_batch_destroy(trioseq_batch_t batch);
 
+/* trioseq_batch_profile — when enable != 0, each trioseq_batch_run records CUDA events on its
+ * stream around the wavefront kernel and around the traceback walk. trioseq_batch_timing then
+ * returns, after trioseq_batch_scores (or a stream synchronisation), ms[0] = wavefront kernel
+ * time and ms[1] = walk time (0 in score-only mode) of the last run.
+ * Errors: EINVAL (null, profiling off or no run yet), ECUDA. */
+trioseq_status trioseq_batch_profile(trioseq_batch_t batch, int32_t enable);
+trioseq_status trioseq_batch_timing(trioseq_batch_t batch, float ms[2]);
+
+/* Bytes copied host->device (encoded inputs, descriptors, queue) and device->host (scores,
+ * error word, alignments) by the last trioseq_align_batch call on this plan. */
+trioseq_status trioseq_plan_io_bytes(trioseq_plan_t plan, uint64_t* h2d, uint64_t* d2h);
+
 /* ---- serving: continuous batching behind submit/poll ---- */
 
 typedef struct trioseq_server_s* trioseq_server_t;

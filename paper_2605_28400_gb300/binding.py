@@ -67,6 +67,10 @@ def load(build_if_missing: bool = True):
         "trioseq_batch_info": ([vp, szp, ctypes.POINTER(ctypes.c_uint64),
                                 ctypes.POINTER(ctypes.c_uint64), i32p, i32p], i32),
         "trioseq_batch_destroy": ([vp], i32),
+        "trioseq_batch_profile": ([vp, i32], i32),
+        "trioseq_batch_timing": ([vp, ctypes.POINTER(ctypes.c_float)], i32),
+        "trioseq_plan_io_bytes": ([vp, ctypes.POINTER(ctypes.c_uint64),
+                                   ctypes.POINTER(ctypes.c_uint64)], i32),
         "trioseq_server_create": ([ctypes.POINTER(vp), i32, sz, ctypes.POINTER(vp)], i32),
         "trioseq_submit": ([vp, ctypes.POINTER(Triplet), i32, u32,
                             ctypes.POINTER(ctypes.c_uint64)], i32),
@@ -87,7 +91,8 @@ def exported_symbols() -> list[str]:
     return ["trioseq_plan", "trioseq_plan_destroy", "trioseq_align_batch", "trioseq_traceback",
             "trioseq_batch_create", "trioseq_batch_run", "trioseq_batch_scores",
             "trioseq_batch_device_scores", "trioseq_batch_alignment", "trioseq_batch_info",
-            "trioseq_batch_destroy", "trioseq_server_create", "trioseq_submit", "trioseq_poll",
+            "trioseq_batch_destroy", "trioseq_batch_profile", "trioseq_batch_timing",
+            "trioseq_plan_io_bytes", "trioseq_server_create", "trioseq_submit", "trioseq_poll",
             "trioseq_server_destroy", "trioseq_strerror"]
 
 
@@ -222,6 +227,24 @@ def trioseq_batch_info(batch) -> dict:
 
 def trioseq_batch_destroy(batch):
     _check(load().trioseq_batch_destroy(batch), "trioseq_batch_destroy")
+
+
+def trioseq_batch_profile(batch, enable: bool = True):
+    _check(load().trioseq_batch_profile(batch, int(bool(enable))), "trioseq_batch_profile")
+
+
+def trioseq_batch_timing(batch) -> tuple[float, float]:
+    """(wavefront kernel ms, walk ms) of the last profiled run."""
+    ms = (ctypes.c_float * 2)()
+    _check(load().trioseq_batch_timing(batch, ms), "trioseq_batch_timing")
+    return float(ms[0]), float(ms[1])
+
+
+def trioseq_plan_io_bytes(plan) -> tuple[int, int]:
+    h2d, d2h = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().trioseq_plan_io_bytes(plan, ctypes.byref(h2d), ctypes.byref(d2h)),
+           "trioseq_plan_io_bytes")
+    return h2d.value, d2h.value
 
 
 def trioseq_server_create(plans, hbm_budget: int = 0):

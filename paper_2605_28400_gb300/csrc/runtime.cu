@@ -144,6 +144,15 @@ struct trioseq_batch_s {
   std::vector<uint8_t> h_rows;
   std::vector<int32_t> h_lens;
   bool have_rows = false;
+  // optional per-kernel timing (events on the launching stream)
+  bool profile = false;
+  bool timed = false;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  uint64_t h2d_bytes = 0, d2h_bytes = 0;
+  ~trioseq_batch_s() {
+    for (auto& e : ev)
+      if (e) cudaEventDestroy(e);
+  }
 };
 
 namespace {
@@ -302,7 +311,9 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
 }
 
 // Size the workspace and copy the inputs of `bt` into it (stream-ordered).
-trioseq_status upload(trioseq_batch_s* bt, cudaStream_t st) {
+// `pinned`: stage through the workspace's pinned buffer and copy asynchronously on `st` (the
+// per-call path); otherwise copy synchronously from pageable memory (one-off batch creation).
+trioseq_status upload(trioseq_batch_s* bt, cudaStream_t st, bool pinned) {
   Workspace& ws = *bt->ws;
   const bool tb = bt->mode == TRIOSEQ_WITH_TRACEBACK;
   const size_t nprog = bt->tasks.size() + 64;
@@ -312,9 +323,11 @@ trioseq_status upload(trioseq_batch_s* bt, cudaStream_t st) {
       (tb && (!ws.codes.ensure(bt->code_words * sizeof(uint32_t)) ||
               !ws.rows.ensure(bt->rows_bytes) ||
               !ws.lens.ensure(std::max<size_t>(bt->tb_trips.size(), 1) * sizeof(int32_t)))) ||
-      !ws.staging.ensure(bt->inputs_bytes))
+      (pinned && !ws.staging.ensure(bt->inputs_bytes)))
     return TRIOSEQ_ENOMEM;
-  char* h = reinterpret_cast<char*>(ws.staging.p);
+  std::vector<char> pageable;
+  if (!pinned) pageable.assign(bt->inputs_bytes, 0);
+  char* h = pinned ? reinterpret_cast<char*>(ws.staging.p) : pageable.data();
   std::memcpy(h, bt->seq.data(), bt->seq_bytes);
   std::memcpy(h + bt->off_desc, bt->desc.data(), sizeof(TripDesc) * bt->n);
   std::memcpy(h + bt->off_tasks, bt->tasks.data(), sizeof(Task) * bt->tasks.size());
@@ -323,9 +336,12 @@ trioseq_status upload(trioseq_batch_s* bt, cudaStream_t st) {
     std::memcpy(h + bt->off_rowoff, bt->row_off.data(), sizeof(int64_t) * bt->row_off.size());
     std::memcpy(h + bt->off_rowcap, bt->row_cap.data(), sizeof(int32_t) * bt->row_cap.size());
   }
-  cudaError_t e = cudaMemcpyAsync(ws.inputs.p, h, bt->inputs_bytes, cudaMemcpyHostToDevice, st);
+  cudaError_t e =
+      pinned ? cudaMemcpyAsync(ws.inputs.p, h, bt->inputs_bytes, cudaMemcpyHostToDevice, st)
+             : cudaMemcpy(ws.inputs.p, h, bt->inputs_bytes, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_status(e);
   bt->uploaded = true;
+  bt->h2d_bytes = bt->inputs_bytes;
   return TRIOSEQ_OK;
 }
 
@@ -357,7 +373,12 @@ trioseq_status run(trioseq_batch_s* bt, cudaStream_t st) {
   p.err = err;
   p.TI = std::max(1, plan->TI);
   p.wait_ns = plan->wait_ns;
+  bt->timed = false;
+  if (bt->profile && cudaEventRecord(bt->ev[0], st) != cudaSuccess)
+    return cuda_status(cudaGetLastError());
   if (launch_wavefront(bt->var.nj, bt->var.nk, tb, p, bt->grid, bt->smem, st) != 0)
+    return cuda_status(cudaGetLastError());
+  if (bt->profile && cudaEventRecord(bt->ev[1], st) != cudaSuccess)
     return cuda_status(cudaGetLastError());
   if (tb && !bt->tb_trips.empty()) {
     WalkParams w{};
@@ -374,6 +395,10 @@ trioseq_status run(trioseq_batch_s* bt, cudaStream_t st) {
     w.NJ = bt->var.nj;
     w.NK = bt->var.nk;
     if (launch_walk(w, st) != 0) return cuda_status(cudaGetLastError());
+  }
+  if (bt->profile) {
+    if (cudaEventRecord(bt->ev[2], st) != cudaSuccess) return cuda_status(cudaGetLastError());
+    bt->timed = true;
   }
   return TRIOSEQ_OK;
 }
@@ -405,6 +430,9 @@ trioseq_status fetch(trioseq_batch_s* bt, cudaStream_t st, int32_t* scores_out) 
   if (herr & 1) return TRIOSEQ_ETIMEOUT;
   if (herr & 2) return TRIOSEQ_ECUDA;
   bt->have_rows = tb;
+  bt->d2h_bytes = bt->n ? sizeof(int32_t) * (1 + bt->n) : 0;
+  if (tb && !bt->tb_trips.empty())
+    bt->d2h_bytes += bt->rows_bytes + bt->h_lens.size() * sizeof(int32_t);
   return TRIOSEQ_OK;
 }
 
@@ -526,7 +554,7 @@ trioseq_status trioseq_align_batch(trioseq_plan_t plan, const trioseq_triplet* t
   trioseq_status s = build_batch(plan, triplets, n, mode, bt.get());
   if (s != TRIOSEQ_OK) return s;
   bt->ws = &plan->ws;
-  if ((s = upload(bt.get(), st)) != TRIOSEQ_OK) return s;
+  if ((s = upload(bt.get(), st, true)) != TRIOSEQ_OK) return s;
   if ((s = run(bt.get(), st)) != TRIOSEQ_OK) return s;
   if ((s = fetch(bt.get(), st, scores_out)) != TRIOSEQ_OK) return s;
   bt->seq.clear();
@@ -553,8 +581,7 @@ trioseq_status trioseq_batch_create(trioseq_plan_t plan, const trioseq_triplet* 
   bt->own_ws.reset(new (std::nothrow) Workspace());
   if (!bt->own_ws) return TRIOSEQ_ENOMEM;
   bt->ws = bt->own_ws.get();
-  if ((s = upload(bt.get(), nullptr)) != TRIOSEQ_OK) return s;
-  if (cudaStreamSynchronize(nullptr) != cudaSuccess) return cuda_status(cudaGetLastError());
+  if ((s = upload(bt.get(), nullptr, false)) != TRIOSEQ_OK) return s;
   *out = bt.release();
   return TRIOSEQ_OK;
 }
@@ -590,6 +617,36 @@ trioseq_status trioseq_batch_info(trioseq_batch_t bt, size_t* n, uint64_t* cells
   if (tasks) *tasks = bt->tasks.size();
   if (tile_j) *tile_j = bt->var.nj;
   if (tile_k) *tile_k = bt->var.nk;
+  return TRIOSEQ_OK;
+}
+
+trioseq_status trioseq_batch_profile(trioseq_batch_t bt, int32_t enable) {
+  if (!bt) return TRIOSEQ_EINVAL;
+  DeviceGuard g(bt->plan->device);
+  if (enable)
+    for (auto& e : bt->ev)
+      if (!e && cudaEventCreate(&e) != cudaSuccess) return cuda_status(cudaGetLastError());
+  bt->profile = enable != 0;
+  bt->timed = false;
+  return TRIOSEQ_OK;
+}
+
+trioseq_status trioseq_batch_timing(trioseq_batch_t bt, float ms[2]) {
+  if (!bt || !ms || !bt->profile || !bt->timed) return TRIOSEQ_EINVAL;
+  DeviceGuard g(bt->plan->device);
+  float a = 0.f, b = 0.f;
+  if (cudaEventElapsedTime(&a, bt->ev[0], bt->ev[1]) != cudaSuccess ||
+      cudaEventElapsedTime(&b, bt->ev[1], bt->ev[2]) != cudaSuccess)
+    return cuda_status(cudaGetLastError());
+  ms[0] = a;
+  ms[1] = b;
+  return TRIOSEQ_OK;
+}
+
+trioseq_status trioseq_plan_io_bytes(trioseq_plan_t plan, uint64_t* h2d, uint64_t* d2h) {
+  if (!plan || !plan->last) return TRIOSEQ_EINVAL;
+  if (h2d) *h2d = plan->last->h2d_bytes;
+  if (d2h) *d2h = plan->last->d2h_bytes;
   return TRIOSEQ_OK;
 }
 
