@@ -56,6 +56,9 @@ def workloads():
                                      "score only, one persistent launch"),
         "dna128": (synth.config0, "one triplet of independent uniform DNA, 128 each, score + "
                                   "traceback"),
+        # reduced-size case of the protein recipe (profiling captures that must stay small)
+        "protein1000": (lambda: synth.config3(L=1000),
+                        "one related protein triplet, ancestor 1000, protein recipe, score only"),
     }
 
 

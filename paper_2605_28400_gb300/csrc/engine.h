@@ -23,21 +23,36 @@ constexpr int kPR = 4;             // lanes of a warp along j
 constexpr int kPC = 8;             // lanes of a warp along k
 constexpr int kMaxAlphabet = 32;
 constexpr int kWarpsPerCta = 4;
+constexpr int kRing = 4;           // face-staging ring slots per warp (power of two)
+constexpr int kAhead = 2;          // steps between staging a face row and using it
 
 // Rank of each move in the tie-break (Eq. 1 listing order): rank 7 wins ties over rank 6 ...
 // rank -> (di, dj, dk):
 //   7:(1,1,1) 6:(1,1,0) 5:(1,0,1) 4:(0,1,1) 3:(1,0,0) 2:(0,1,0) 1:(0,0,1)
+//
+// Traceback code layout. Lane (r, lc) of column task (J, K) writes, at step t (slice
+// i = t - r - lc), one record of NJ*NK/8 32-bit words at word offset
+//   code_off + ((task * T + t) * 32 + lane) * (NJ*NK/8),   task = J*nK + K, lane = r*8 + lc.
+// Cell (p, q) of the lane tile is e = p*NK + q; it lives in word e/8 at bit
+//   8*(e & 3) + 4*((e >> 2) & 1)   (the 3-bit rank in the low bits of that nibble).
+__host__ __device__ inline int code_bit(int e) { return 8 * (e & 3) + 4 * ((e >> 2) & 1); }
+
+// Face records. Column task (J, K) publishes, per slice s (0..a):
+//   its last j-row in the j-record  Oj[s][0 .. WK+3]: slot 3 = M'[s][J*WJ+WJ-1][K*WK-1] (the
+//     corner its consumer needs), slots 4 .. WK+3 = M'[s][J*WJ+WJ-1][K*WK + kl];
+//   its last k-column in the k-record Ok[s][0 .. WJ-1] = M'[s][J*WJ + jl][K*WK+WK-1].
+// Records of one task are contiguous: Oj at oj_off + task*(a+1)*(WK+4), Ok at
+// ok_off + task*(a+1)*WJ (int32 offsets into the face workspace).
 
 struct TripDesc {
   int64_t s_off[3];    // byte offsets of S0, S1, S2 in the packed residue buffer
-  int64_t fj_off;      // int32 offset of this triplet's j-face planes in the face workspace
-  int64_t fk_off;      // int32 offset of its k-face planes
+  int64_t oj_off;      // int32 offset of this triplet's j-records in the face workspace
+  int64_t ok_off;      // int32 offset of its k-records
   int64_t code_off;    // uint32-word offset of its traceback codes (-1: score only)
   int64_t prog_base;   // index of task (J=0,K=0) in the progress array
   int32_t len[3];      // a, b, c
   int32_t nJ, nK;      // column blocks along j and k
   int32_t T;           // steps per column task: a + 1 + (kPR - 1) + (kPC - 1)
-  int32_t rowJ, rowK;  // int32 row strides of the j- and k-face planes
   int32_t score_base;  // 2*alpha*(a+b+c)
   int32_t out_idx;     // index into the score output
   int32_t tb_idx;      // index among the batch's traceback triplets (-1: none)

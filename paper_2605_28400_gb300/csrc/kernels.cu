@@ -8,18 +8,22 @@
 //   for slice s was produced by its upper / left neighbour lane one step earlier and arrives by
 //   warp shuffle (the anti-diagonal skew of the paper's warp kernel, Sec. IV-B, rebuilt for
 //   int32 on one warp per column block).
-//   Column blocks exchange their boundary faces through global memory (L2): block (J,K) reads
-//   the j-face written by (J-1,K) and the k-face written by (J,K-1), one int32 per face cell per
-//   slice. A producer publishes how many steps it has completed every TI steps with a release
-//   store; a consumer waits (bounded, acquire) before it touches a face row. Tasks are handed
-//   out through one atomic queue in an order where every producer precedes its consumers, so
-//   the engine cannot deadlock even when not all warps are resident.
-//   TB = true additionally keeps traceback keys (8*M' + 7, see engine.h) and streams one 4-bit
-//   code per cell to HBM (rank of the winning move, 8 cells per 32-bit word, one 32-byte record
-//   per lane per step).
+//   Column blocks exchange boundary records through global memory (L2): block (J,K) reads the
+//   j-records written by (J-1,K) and the k-records written by (J,K-1) (engine.h). A producer
+//   publishes how many steps it has completed every TI steps with a release store. The
+//   consumer's edge lanes need the records of step t; every lane loads one 16-byte piece of
+//   them from L2 kAhead steps early (after lane 0 has acquired the producer's progress, bounded
+//   wait) and parks it in a small per-warp shared-memory ring one step early. All lanes then
+//   read their halo from the ring and select it against the shuffled value, so the step loop
+//   has no lane-divergent branches in steady state.
+//   Tasks come from one atomic queue in an order where every producer precedes its consumers,
+//   so the engine cannot deadlock even when not all warps are resident.
+//   TB = true additionally keeps traceback keys (8*M' + 7, engine.h) and streams one 4-bit code
+//   per cell to HBM (one record of NJ*NK/8 words per lane per step).
 //
-// walk_kernel: follows the stored codes from (a,b,c) back to the origin for each traceback
-//   request and writes the three aligned rows.
+// walk_kernel: one warp per traceback request. It stages a window of code records around the
+//   current cell in shared memory (all lanes load), then lane 0 follows the stored moves back
+//   through the window; repeated until the origin.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -29,10 +33,14 @@ namespace trioseq {
 
 namespace {
 
-__device__ __forceinline__ int ld_acquire(const int* p) {
+__device__ __forceinline__ int ld_relaxed(const int* p) {
   int v;
-  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
+}
+
+__device__ __forceinline__ void fence_acq_rel() {
+  asm volatile("fence.acq_rel.gpu;" ::: "memory");
 }
 
 __device__ __forceinline__ void st_release(int* p, int v) {
@@ -45,15 +53,25 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
-// Lane-0 wait until *flag >= need. `cached` keeps the last value seen. Gives up (returns false)
-// when the flag has not moved for wait_ns nanoseconds.
+// Lane-0 wait until *flag >= need. `cached` keeps the last value seen. Polls with relaxed loads
+// and exponential back-off (light on L2 while many warps wait); the fence after the satisfying
+// load makes it an acquire. Gives up (returns false) when the flag has not moved for wait_ns.
 __device__ __noinline__ bool wait_flag(const int* flag, int need, int* cached, int64_t wait_ns) {
-  int last = *cached;
-  if (last >= need) return true;
+  int v = ld_relaxed(flag);
+  if (v >= need) {
+    fence_acq_rel();
+    *cached = v;
+    return true;
+  }
+  int last = v;
+  unsigned ns = 32;
   uint64_t t0 = global_ns();
   for (;;) {
-    const int v = ld_acquire(flag);
+    __nanosleep(ns);
+    if (ns < 1024) ns <<= 1;
+    v = ld_relaxed(flag);
     if (v >= need) {
+      fence_acq_rel();
       *cached = v;
       return true;
     }
@@ -61,11 +79,11 @@ __device__ __noinline__ bool wait_flag(const int* flag, int need, int* cached, i
     if (v != last) {
       last = v;
       t0 = now;
+      ns = 32;
     } else if ((int64_t)(now - t0) > wait_ns) {
       *cached = v;
       return false;
     }
-    __nanosleep(128);
   }
 }
 
@@ -79,13 +97,26 @@ struct MinBlocks {
   static constexpr int value = (NJ * NK >= 64) ? 2 : ((NJ * NK >= 32) ? 3 : 4);
 };
 
+template <int NJ, int NK>
+struct Geom {
+  static constexpr int WJ = kPR * NJ, WK = kPC * NK;
+  static constexpr int RJ = WK + 4, RK = WJ;        // record strides (ints)
+  static constexpr int PJ = WJ + 4, PK = WK + 4;    // padded profile rows
+  static constexpr int SEGJ = NK + 4;               // staged j-record segment per lane column
+  static constexpr int SLOT = kPC * SEGJ + WJ;      // ints per ring slot
+  static constexpr int CBJ = NK / 4 + 1;            // 16-byte pieces per j-segment
+  static constexpr int CBK = NJ / 4;                // 16-byte pieces per k-segment
+  static constexpr int NCOPY = kPC * CBJ + kPR * CBK;
+  static constexpr int W = NJ * NK / 8;             // code words per lane per step
+};
+
 template <int NJ, int NK, bool TB>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK>::value)
     wavefront_kernel(const WaveParams p) {
+  using G = Geom<NJ, NK>;
   static_assert(NJ % 4 == 0 && NK % 4 == 0, "tile sides must be multiples of 4");
-  constexpr int WJ = kPR * NJ, WK = kPC * NK;
-  constexpr int PJ = WJ + 4, PK = WK + 4;  // padded profile rows spread lanes over banks
-  constexpr int W = NJ * NK / 8;           // code words per lane per step
+  static_assert(G::NCOPY <= 32, "one staged piece per lane per step");
+  constexpr int WJ = G::WJ, WK = G::WK, W = G::W;
   extern __shared__ int4 smem4[];
   int* smem = reinterpret_cast<int*>(smem4);
   const int KP = p.KP;
@@ -93,11 +124,29 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK>::value)
   const int sigN = (KP * KP + 3) & ~3;
   int* sig = smem;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int* profJ = smem + sigN + warp * (KP * (PJ + PK));
-  int* profK = profJ + KP * PJ;
+  int* profJ = smem + sigN + warp * (KP * (G::PJ + G::PK) + kRing * G::SLOT);
+  int* profK = profJ + KP * G::PJ;
+  int* ring = profK + KP * G::PK;
   for (int e = threadIdx.x; e < KP * KP; e += blockDim.x) sig[e] = p.sig[e];
   __syncthreads();
   const int r = lane >> 3, lc = lane & 7;
+
+  // This lane's staging piece: which record, which 16 bytes, whose slice.
+  int cp_kind = 0, cp_delta = 0, cp_col = 0, cp_dst = 0;
+  if (lane < kPC * G::CBJ) {
+    const int l = lane / G::CBJ, bb = lane % G::CBJ;
+    cp_kind = 1;
+    cp_delta = l;
+    cp_col = l * NK + 4 * bb;
+    cp_dst = l * G::SEGJ + 4 * bb;
+  } else if (lane < G::NCOPY) {
+    const int q = lane - kPC * G::CBJ;
+    const int rr = q / G::CBK, bb = q % G::CBK;
+    cp_kind = 2;
+    cp_delta = rr;
+    cp_col = rr * NJ + 4 * bb;
+    cp_dst = kPC * G::SEGJ + rr * NJ + 4 * bb;
+  }
 
   for (;;) {
     int task = 0;
@@ -113,6 +162,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK>::value)
     const int8_t* S1 = p.seq + d.s_off[1];
     const int8_t* S2 = p.seq + d.s_off[2];
     const int j0 = J * WJ + r * NJ, k0 = K * WK + lc * NK;
+    const int me = J * nK + K;
 
     // Substitution profiles of this block: profJ[x][jl] = sigma''(x, y_(J*WJ+jl)),
     // profK[x][kl] = sigma''(x, z_(K*WK+kl)); residue index 0 and beyond the end are VIRT.
@@ -120,12 +170,12 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK>::value)
     for (int e = lane; e < KP * WJ; e += 32) {
       const int x = e / WJ, jl = e - x * WJ, j = J * WJ + jl;
       const int y = (j >= 1 && j <= b) ? (int)S1[j - 1] : VIRT;
-      profJ[x * PJ + jl] = sig[x * KP + y];
+      profJ[x * G::PJ + jl] = sig[x * KP + y];
     }
     for (int e = lane; e < KP * WK; e += 32) {
       const int x = e / WK, kl = e - x * WK, k = K * WK + kl;
       const int z = (k >= 1 && k <= c) ? (int)S2[k - 1] : VIRT;
-      profK[x * PK + kl] = sig[x * KP + z];
+      profK[x * G::PK + kl] = sig[x * KP + z];
     }
     // sigma''(y_j, z_k) is the same for every i: keep this lane's tile of it in registers.
     int Cv[NJ][NK];
@@ -154,103 +204,145 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK>::value)
     const int end_p = b % NJ, end_q = c % NK;
 
     int P[NJ][NK];
-    int rowPrev[NK + 1], colPrev[NJ], rowCur[NK + 1], colCur[NJ], nxtRow[NK + 1], nxtCol[NJ];
+    int rowPrev[NK + 1], colPrev[NJ], rowCur[NK + 1], colCur[NJ];
 #pragma unroll
     for (int pp = 0; pp < NJ; ++pp) {
 #pragma unroll
       for (int qq = 0; qq < NK; ++qq) P[pp][qq] = kNeg;
       colPrev[pp] = kNeg;
       colCur[pp] = kNeg;
-      nxtCol[pp] = kNeg;
     }
 #pragma unroll
     for (int qq = 0; qq <= NK; ++qq) {
       rowPrev[qq] = kNeg;
       rowCur[qq] = kNeg;
-      nxtRow[qq] = kNeg;
     }
     // M'[-1][-1][-1] = 0 feeds the origin through the (1,1,1) move (stored as 8*0+7 with keys).
-    if (J == 0 && K == 0 && lane == 0) rowPrev[0] = TB ? 7 : 0;
+    // The halo rotation at the top of step 0 moves rowCur into rowPrev.
+    if (J == 0 && K == 0 && lane == 0) rowCur[0] = TB ? 7 : 0;
 
-    const int64_t planeJ = (int64_t)(a + 1) * d.rowJ;
-    const int64_t planeK = (int64_t)(a + 1) * d.rowK;
-    const int* fj_in = p.faces + d.fj_off + (int64_t)(J - 1) * planeJ;
-    int* fj_out = p.faces + d.fj_off + (int64_t)J * planeJ;
-    const int* fk_in = p.faces + d.fk_off + (int64_t)(K - 1) * planeK;
-    int* fk_out = p.faces + d.fk_off + (int64_t)K * planeK;
-    const bool has_fj_out = (J + 1 < nJ), has_fk_out = (K + 1 < nK);
-    const int* progJ = p.progress + d.prog_base + (int64_t)(J - 1) * nK + K;
-    const int* progK = p.progress + d.prog_base + (int64_t)J * nK + (K - 1);
-    int* progMe = p.progress + d.prog_base + (int64_t)J * nK + K;
-    int cachedJ = 0, cachedK = 0;
+    const int64_t recJ = (int64_t)(a + 1) * G::RJ, recK = (int64_t)(a + 1) * G::RK;
+    int* const faces = p.faces;
+    const int* srcJ = faces + d.oj_off + (int64_t)(me - nK) * recJ;  // producer (J-1, K)
+    const int* srcK = faces + d.ok_off + (int64_t)(me - 1) * recK;   // producer (J, K-1)
+    int* dstJ = faces + d.oj_off + (int64_t)me * recJ;
+    int* dstK = faces + d.ok_off + (int64_t)me * recK;
+    const bool has_out_j = (J + 1 < nJ), has_out_k = (K + 1 < nK);
+    const int* progJ = p.progress + d.prog_base + (me - nK);
+    const int* progK = p.progress + d.prog_base + (me - 1);
+    int* progMe = p.progress + d.prog_base + me;
+    int cachedJ = J > 0 ? 0 : 1 << 30, cachedK = K > 0 ? 0 : 1 << 30;  // warp-uniform
     uint32_t* code_base =
-        TB ? p.codes + d.code_off + (int64_t)(J * nK + K) * T * 32 * W + lane * W : nullptr;
-
+        TB ? p.codes + d.code_off + (int64_t)me * T * 32 * W + lane * W : nullptr;
     bool ok = true;
-    // Fetch the face halos of the edge lanes for step tt into nxtRow / nxtCol. The face row a
-    // lane reads was written by the producer lane at producer step tt + kPR - 1 (j-face) or
-    // tt + kPC - 1 (k-face); lane 0 first waits until the producer has published those steps.
-#define TRIOSEQ_LOAD_EDGES(tt)                                                                  \
-  {                                                                                             \
-    bool okl = true;                                                                            \
-    if (lane == 0) {                                                                            \
-      if (J > 0) okl = wait_flag(progJ, min((tt) + kPR, T), &cachedJ, p.wait_ns);               \
-      if (okl && K > 0) okl = wait_flag(progK, min((tt) + kPC, T), &cachedK, p.wait_ns);        \
-    }                                                                                           \
-    ok = __shfl_sync(kFull, okl, 0);                                                            \
-    __syncwarp();                                                                               \
-    const int ss = (tt) - r - lc;                                                               \
-    const bool sv = ok && ss >= 0 && ss <= a;                                                   \
-    if (r == 0) {                                                                               \
-      if (J > 0 && sv) {                                                                        \
-        const int* src = fj_in + (int64_t)ss * d.rowJ + k0 + 4;                                 \
-        nxtRow[0] = (K == 0 && lc == 0) ? kNeg : __ldcg(src - 1);                               \
-        _Pragma("unroll") for (int q4 = 0; q4 < NK / 4; ++q4) {                                 \
-          const int4 v = __ldcg(reinterpret_cast<const int4*>(src) + q4);                       \
-          nxtRow[1 + 4 * q4] = v.x;                                                             \
-          nxtRow[2 + 4 * q4] = v.y;                                                             \
-          nxtRow[3 + 4 * q4] = v.z;                                                             \
-          nxtRow[4 + 4 * q4] = v.w;                                                             \
-        }                                                                                       \
-      } else {                                                                                  \
-        _Pragma("unroll") for (int qq = 0; qq <= NK; ++qq) nxtRow[qq] = kNeg;                   \
-      }                                                                                         \
-    }                                                                                           \
-    if (lc == 0) {                                                                              \
-      if (K > 0 && sv) {                                                                        \
-        const int* src = fk_in + (int64_t)ss * d.rowK + j0 + 4;                                 \
-        _Pragma("unroll") for (int p4 = 0; p4 < NJ / 4; ++p4) {                                 \
-          const int4 v = __ldcg(reinterpret_cast<const int4*>(src) + p4);                       \
-          nxtCol[4 * p4] = v.x;                                                                 \
-          nxtCol[4 * p4 + 1] = v.y;                                                             \
-          nxtCol[4 * p4 + 2] = v.z;                                                             \
-          nxtCol[4 * p4 + 3] = v.w;                                                             \
-        }                                                                                       \
-      } else {                                                                                  \
-        _Pragma("unroll") for (int pp = 0; pp < NJ; ++pp) nxtCol[pp] = kNeg;                    \
-      }                                                                                         \
-    }                                                                                           \
-  }
 
-    TRIOSEQ_LOAD_EDGES(0);
-    for (int t = 0; ok && t < T; ++t) {
+    // Face pieces of step u: each lane loads its 16-byte piece from L2 into registers at step
+    // u - kAhead (after lane 0 has seen the producers publish the steps that wrote them), parks
+    // it in ring slot u % kRing at step u - 1, and the edge lanes read the slot at step u. The
+    // load's latency is covered by a whole step of compute.
+    int4 pf = make_int4(kNeg, kNeg, kNeg, kNeg);
+    int pf_u = -1;
+    bool pf_valid = false;
+    auto fetch = [&](int u) {
+      const int needJ = min(u + kPR, T), needK = min(u + kPC, T);
+      if (cachedJ < needJ || cachedK < needK) {  // warp-uniform
+        bool okl = true;
+        int cj = cachedJ, ck = cachedK;
+        if (lane == 0) {
+          if (cj < needJ) okl = wait_flag(progJ, needJ, &cj, p.wait_ns);
+          if (okl && ck < needK) okl = wait_flag(progK, needK, &ck, p.wait_ns);
+        }
+        ok = __shfl_sync(kFull, okl, 0);
+        cachedJ = __shfl_sync(kFull, cj, 0);
+        cachedK = __shfl_sync(kFull, ck, 0);
+        __syncwarp();
+      }
+      const int sl = u - cp_delta;
+      pf_u = u;
+      pf_valid = ok && cp_kind != 0 && sl >= 0 && sl <= a && (cp_kind == 1 ? J > 0 : K > 0);
+      if (pf_valid) {
+        const int* src = (cp_kind == 1) ? srcJ + (int64_t)sl * G::RJ + cp_col
+                                        : srcK + (int64_t)sl * G::RK + cp_col;
+        pf = __ldcg(reinterpret_cast<const int4*>(src));
+      }
+    };
+    auto park = [&]() {
+      if (pf_valid)
+        *reinterpret_cast<int4*>(ring + (pf_u & (kRing - 1)) * G::SLOT + cp_dst) = pf;
+    };
+
+    fetch(0);
+    park();
+    fetch(1);
+    // Residues of S0 by slice: in block B, lane q holds the residue of slice 32*B + q. Blocks are
+    // loaded one block ahead and read by shuffle, so no global load sits on the per-step path.
+    auto xblock = [&](int base) -> int {
+      const int sl = base + lane;
+      return (sl >= 1 && sl <= a) ? (int)__ldg(S0 + sl - 1) : VIRT;
+    };
+    int xprev = VIRT, xcur = xblock(0), xnext = xblock(32);
+
+    for (int t = 0; t < T; ++t) {
       const int s = t - r - lc;
-      if (r == 0) {
-#pragma unroll
-        for (int qq = 0; qq <= NK; ++qq) rowCur[qq] = nxtRow[qq];
-      }
-      if (lc == 0) {
-#pragma unroll
-        for (int pp = 0; pp < NJ; ++pp) colCur[pp] = nxtCol[pp];
-      }
-      if (t + 1 < T) TRIOSEQ_LOAD_EDGES(t + 1);
+      park();  // piece of step t + 1
+      if (t + kAhead < T) fetch(t + kAhead);
       if (!ok) break;
+      if ((t & 31) == 0 && t > 0) {
+        xprev = xcur;
+        xcur = xnext;
+        xnext = xblock(t + 32);
+      }
+      // this lane's slice s lies in [t - 10, t]: in the current or the previous block
+      const int xa = __shfl_sync(kFull, xcur, s & 31);
+      const int xb = __shfl_sync(kFull, xprev, s & 31);
+      const int x = (s >= (t & ~31)) ? xa : xb;
+      __syncwarp();
+      // Halo of slice s: shuffled from the neighbour lanes (their step t-1 results), or staged
+      // face records for the edge lanes.
+      {
+        const int* sl = ring + (t & (kRing - 1)) * G::SLOT;
+        const bool vrow = (J > 0) && s >= 0 && s <= a;
+        const bool vcol = (K > 0) && s >= 0 && s <= a;
+        const int* rs = sl + lc * G::SEGJ;
+        const int* cs = sl + kPC * G::SEGJ + r * NJ;
+        int er[NK + 1], ec[NJ];
+        er[0] = rs[3];
+#pragma unroll
+        for (int q4 = 0; q4 < NK / 4; ++q4) {
+          const int4 v = reinterpret_cast<const int4*>(rs + 4)[q4];
+          er[1 + 4 * q4] = v.x;
+          er[2 + 4 * q4] = v.y;
+          er[3 + 4 * q4] = v.z;
+          er[4 + 4 * q4] = v.w;
+        }
+#pragma unroll
+        for (int p4 = 0; p4 < NJ / 4; ++p4) {
+          const int4 v = reinterpret_cast<const int4*>(cs)[p4];
+          ec[4 * p4] = v.x;
+          ec[4 * p4 + 1] = v.y;
+          ec[4 * p4 + 2] = v.z;
+          ec[4 * p4 + 3] = v.w;
+        }
+        const int corner_send = colCur[NJ - 1];
+#pragma unroll
+        for (int qq = 0; qq <= NK; ++qq) {
+          const int send = qq == 0 ? corner_send : P[NJ - 1][qq - 1];
+          const int v = __shfl_up_sync(kFull, send, kPC);
+          rowPrev[qq] = rowCur[qq];
+          rowCur[qq] = (r == 0) ? (vrow ? er[qq] : kNeg) : v;
+        }
+#pragma unroll
+        for (int pp = 0; pp < NJ; ++pp) {
+          const int v = __shfl_up_sync(kFull, P[pp][NK - 1], 1);
+          colPrev[pp] = colCur[pp];
+          colCur[pp] = (lc == 0) ? (vcol ? ec[pp] : kNeg) : v;
+        }
+      }
 
       if (s >= 0 && s <= a) {
-        const int x = (s == 0) ? VIRT : (int)__ldg(S0 + s - 1);
         int A[NJ], B[NK];
         {
-          const int4* pa = reinterpret_cast<const int4*>(profJ + x * PJ + r * NJ);
+          const int4* pa = reinterpret_cast<const int4*>(profJ + x * G::PJ + r * NJ);
 #pragma unroll
           for (int p4 = 0; p4 < NJ / 4; ++p4) {
             const int4 v = pa[p4];
@@ -259,7 +351,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK>::value)
             A[4 * p4 + 2] = v.z;
             A[4 * p4 + 3] = v.w;
           }
-          const int4* pb = reinterpret_cast<const int4*>(profK + x * PK + lc * NK);
+          const int4* pb = reinterpret_cast<const int4*>(profK + x * G::PK + lc * NK);
 #pragma unroll
           for (int q4 = 0; q4 < NK / 4; ++q4) {
             const int4 v = pb[q4];
@@ -270,9 +362,8 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK>::value)
           }
         }
         int Q[NJ][NK];
-        uint32_t cw[W > 0 ? W : 1];
-#pragma unroll
-        for (int w = 0; w < (W > 0 ? W : 1); ++w) cw[w] = 0u;
+        uint32_t cw[W];
+        int raw[8];
 #pragma unroll
         for (int pp = 0; pp < NJ; ++pp) {
 #pragma unroll
@@ -292,7 +383,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK>::value)
               int u = max(Pxy + A[pp], Sx);
               u = max(Pxz + B[qq], u);
               const int w = max(d0, Myz);
-              int v = max(w + Cv[pp][qq], u);
+              const int v = max(w + Cv[pp][qq], u);
               Q[pp][qq] = max(v, max(Sy, Sz));
             } else {
               // Keys: rank offsets 0,-1,-2,-3,-4,-5,-6 for moves 111,110,101,011,100,010,001.
@@ -302,9 +393,16 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK>::value)
               u = max(Pxz + (B[qq] - 2), u);
               int v = max(w + Cv[pp][qq], u);
               v = max(v, max(Sy - 5, Sz - 6));
-              const int n = pp * NK + qq;
-              cw[n >> 3] |= (uint32_t)(v & 7) << (4 * (n & 7));
+              const int e = pp * NK + qq;
+              raw[e & 7] = v;
               Q[pp][qq] = v | 7;
+              if ((e & 7) == 7) {  // pack 8 ranks: bytes via PRMT, then nibbles (code_bit)
+                const uint32_t lo = __byte_perm(__byte_perm(raw[0], raw[1], 0x0040),
+                                                __byte_perm(raw[2], raw[3], 0x0040), 0x5410);
+                const uint32_t hi = __byte_perm(__byte_perm(raw[4], raw[5], 0x0040),
+                                                __byte_perm(raw[6], raw[7], 0x0040), 0x5410);
+                cw[e >> 3] = (lo & 0x07070707u) | ((hi & 0x07070707u) << 4);
+              }
             }
           }
         }
@@ -326,19 +424,21 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK>::value)
               reinterpret_cast<uint2*>(dst)[w2] = make_uint2(cw[2 * w2], cw[2 * w2 + 1]);
           }
         }
-        if (r == kPR - 1 && has_fj_out) {
-          int4* dst = reinterpret_cast<int4*>(fj_out + (int64_t)s * d.rowJ + k0 + 4);
+        if (r == kPR - 1 && has_out_j) {
+          int* dst = dstJ + (int64_t)s * G::RJ;
+          if (lc == 0) dst[3] = colCur[NJ - 1];  // corner for the consumer's lane (0,0)
+          int4* d4 = reinterpret_cast<int4*>(dst + 4 + lc * NK);
 #pragma unroll
           for (int q4 = 0; q4 < NK / 4; ++q4)
-            dst[q4] = make_int4(P[NJ - 1][4 * q4], P[NJ - 1][4 * q4 + 1], P[NJ - 1][4 * q4 + 2],
-                                P[NJ - 1][4 * q4 + 3]);
+            d4[q4] = make_int4(P[NJ - 1][4 * q4], P[NJ - 1][4 * q4 + 1], P[NJ - 1][4 * q4 + 2],
+                               P[NJ - 1][4 * q4 + 3]);
         }
-        if (lc == kPC - 1 && has_fk_out) {
-          int4* dst = reinterpret_cast<int4*>(fk_out + (int64_t)s * d.rowK + j0 + 4);
+        if (lc == kPC - 1 && has_out_k) {
+          int4* d4 = reinterpret_cast<int4*>(dstK + (int64_t)s * G::RK + r * NJ);
 #pragma unroll
           for (int p4 = 0; p4 < NJ / 4; ++p4)
-            dst[p4] = make_int4(P[4 * p4][NK - 1], P[4 * p4 + 1][NK - 1], P[4 * p4 + 2][NK - 1],
-                                P[4 * p4 + 3][NK - 1]);
+            d4[p4] = make_int4(P[4 * p4][NK - 1], P[4 * p4 + 1][NK - 1], P[4 * p4 + 2][NK - 1],
+                               P[4 * p4 + 3][NK - 1]);
         }
         if (owns_end && s == a) {
           int v = 0;
@@ -350,34 +450,12 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK>::value)
           p.scores[d.out_idx] = (TB ? (v >> 3) : v) + d.score_base;
         }
       }
-
-      // Hand this slice's boundary to the lanes below (j) and to the right (k).
-      {
-        int sendRow[NK + 1], sendCol[NJ];
-        sendRow[0] = colCur[NJ - 1];
-#pragma unroll
-        for (int qq = 0; qq < NK; ++qq) sendRow[qq + 1] = P[NJ - 1][qq];
-#pragma unroll
-        for (int pp = 0; pp < NJ; ++pp) sendCol[pp] = P[pp][NK - 1];
-#pragma unroll
-        for (int qq = 0; qq <= NK; ++qq) {
-          const int v = __shfl_up_sync(kFull, sendRow[qq], kPC);
-          rowPrev[qq] = rowCur[qq];
-          if (r > 0) rowCur[qq] = v;
-        }
-#pragma unroll
-        for (int pp = 0; pp < NJ; ++pp) {
-          const int v = __shfl_up_sync(kFull, sendCol[pp], 1);
-          colPrev[pp] = colCur[pp];
-          if (lc > 0) colCur[pp] = v;
-        }
-      }
       if ((t + 1) % p.TI == 0 || t + 1 == T) {
         __syncwarp();
         if (lane == 0) st_release(progMe, t + 1);
       }
     }
-#undef TRIOSEQ_LOAD_EDGES
+    __syncwarp();
     if (!ok) {
       if (lane == 0) atomicOr(p.err, 1);
       return;
@@ -385,12 +463,20 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK>::value)
   }
 }
 
-__global__ void walk_kernel(const WalkParams p) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= p.ntb) return;
+// ---------------------------------------------------------------------------------------------
+// Traceback walk: window of WI slices x WR lane rows x WC lane columns of code records.
+constexpr int kWalkWI = 16, kWalkWR = 4, kWalkWC = 2, kWalkWarps = 4, kWalkMaxW = 8;
+constexpr int kWalkRecs = kWalkWI * kWalkWR * kWalkWC;
+
+__global__ void __launch_bounds__(kWalkWarps * 32) walk_kernel(const WalkParams p) {
+  __shared__ uint4 wsm4[kWalkWarps * kWalkRecs * kWalkMaxW / 4];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int q = blockIdx.x * kWalkWarps + wib;
+  if (q >= p.ntb) return;  // warp-uniform
+  uint32_t* win = reinterpret_cast<uint32_t*>(wsm4) + wib * kWalkRecs * kWalkMaxW;
   const TripDesc& d = p.desc[p.tb_trips[q]];
   const int a = d.len[0], b = d.len[1], c = d.len[2];
-  const int NJ = p.NJ, NK = p.NK, WJ = kPR * NJ, WK = kPC * NK, W = NJ * NK / 8;
+  const int NJ = p.NJ, NK = p.NK, W = NJ * NK / 8;
   const int8_t* S0 = p.seq + d.s_off[0];
   const int8_t* S1 = p.seq + d.s_off[1];
   const int8_t* S2 = p.seq + d.s_off[2];
@@ -399,35 +485,71 @@ __global__ void walk_kernel(const WalkParams p) {
   uint8_t* row1 = row0 + cap;
   uint8_t* row2 = row1 + cap;
   const uint32_t* codes = p.codes + d.code_off;
-  int i = a, j = b, k = c, n = 0;
-  while (i > 0 || j > 0 || k > 0) {
-    const int J = j / WJ, K = k / WK;
-    const int jl = j - J * WJ, kl = k - K * WK;
-    const int rr = jl / NJ, cc = kl / NK;
-    const int t = i + rr + cc, ln = rr * kPC + cc;
-    const int e = (jl - rr * NJ) * NK + (kl - cc * NK);
-    const uint32_t word =
-        __ldg(codes + ((((int64_t)(J * d.nK + K) * d.T + t) * 32 + ln) * W + (e >> 3)));
-    const int rank = (word >> (4 * (e & 7))) & 7;
-    // rank -> move (Eq. 1 listing order, rank 7 first)
-    const int di = (rank == 7 || rank == 6 || rank == 5 || rank == 3) ? 1 : 0;
-    const int dj = (rank == 7 || rank == 6 || rank == 4 || rank == 2) ? 1 : 0;
-    const int dk = (rank == 7 || rank == 5 || rank == 4 || rank == 1) ? 1 : 0;
-    if (rank == 0 || n >= cap || i < di || j < dj || k < dk) {
+  int i = a, j = b, k = c, n = 0, bad = 0;
+  while ((i | j | k) != 0 && !bad) {
+    const int i0 = i, gr0 = j / NJ, gc0 = k / NK;
+    // All lanes stage the window's records (cell slices i0-WI+1..i0, lane rows gr0-WR+1..gr0,
+    // lane columns gc0-WC+1..gc0).
+    for (int e = lane; e < kWalkRecs; e += 32) {
+      const int di = e / (kWalkWR * kWalkWC), rem = e % (kWalkWR * kWalkWC);
+      const int ii = i0 - di, gr = gr0 - rem / kWalkWC, gc = gc0 - rem % kWalkWC;
+      if (ii < 0 || gr < 0 || gc < 0) continue;
+      const int task = (gr / kPR) * d.nK + (gc / kPC);
+      const int lr = gr % kPR, lcc = gc % kPC;
+      const int t = ii + lr + lcc;
+      const uint32_t* src = codes + (((int64_t)task * d.T + t) * 32 + (lr * kPC + lcc)) * W;
+      for (int w4 = 0; w4 < W; w4 += 4) {
+        if (W >= 4) {
+          *reinterpret_cast<uint4*>(win + e * kWalkMaxW + w4) =
+              __ldcg(reinterpret_cast<const uint4*>(src + w4));
+        } else {
+          *reinterpret_cast<uint2*>(win + e * kWalkMaxW + w4) =
+              __ldcg(reinterpret_cast<const uint2*>(src + w4));
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) {
+      while ((i | j | k) != 0) {
+        const int gr = j / NJ, gc = k / NK;
+        if (i0 - i >= kWalkWI || gr0 - gr >= kWalkWR || gc0 - gc >= kWalkWC) break;
+        const int e = (j - gr * NJ) * NK + (k - gc * NK);
+        const int rec = ((i0 - i) * kWalkWR + (gr0 - gr)) * kWalkWC + (gc0 - gc);
+        const uint32_t word = win[rec * kWalkMaxW + (e >> 3)];
+        const int rank = (word >> code_bit(e)) & 7;
+        // rank -> move (Eq. 1 listing order, rank 7 first)
+        const int di = (rank == 7 || rank == 6 || rank == 5 || rank == 3) ? 1 : 0;
+        const int dj = (rank == 7 || rank == 6 || rank == 4 || rank == 2) ? 1 : 0;
+        const int dk = (rank == 7 || rank == 5 || rank == 4 || rank == 1) ? 1 : 0;
+        if (rank == 0 || n >= cap || i < di || j < dj || k < dk) {
+          bad = 1;
+          break;
+        }
+        const int pos = cap - 1 - n;
+        row0[pos] = di ? (uint8_t)S0[i - 1] : (uint8_t)255;
+        row1[pos] = dj ? (uint8_t)S1[j - 1] : (uint8_t)255;
+        row2[pos] = dk ? (uint8_t)S2[k - 1] : (uint8_t)255;
+        i -= di;
+        j -= dj;
+        k -= dk;
+        ++n;
+      }
+    }
+    i = __shfl_sync(kFull, i, 0);
+    j = __shfl_sync(kFull, j, 0);
+    k = __shfl_sync(kFull, k, 0);
+    n = __shfl_sync(kFull, n, 0);
+    bad = __shfl_sync(kFull, bad, 0);
+    __syncwarp();
+  }
+  if (lane == 0) {
+    if (bad) {
       atomicOr(p.err, 2);
       p.aln_len[q] = -1;
-      return;
+    } else {
+      p.aln_len[q] = n;
     }
-    const int pos = cap - 1 - n;
-    row0[pos] = di ? (uint8_t)S0[i - 1] : (uint8_t)255;
-    row1[pos] = dj ? (uint8_t)S1[j - 1] : (uint8_t)255;
-    row2[pos] = dk ? (uint8_t)S2[k - 1] : (uint8_t)255;
-    i -= di;
-    j -= dj;
-    k -= dk;
-    ++n;
   }
-  p.aln_len[q] = n;
 }
 
 namespace {
@@ -448,8 +570,10 @@ const void* pick(int nj, int nk, bool tb) {
 
 size_t wavefront_smem_bytes(int nj, int nk, int KP) {
   const int WJ = kPR * nj, WK = kPC * nk;
+  const int slot = kPC * (nk + 4) + WJ;
   const size_t sigN = (size_t)((KP * KP + 3) & ~3);
-  return (sigN + (size_t)kWarpsPerCta * KP * ((WJ + 4) + (WK + 4))) * sizeof(int);
+  return (sigN + (size_t)kWarpsPerCta * (KP * ((WJ + 4) + (WK + 4)) + kRing * slot)) *
+         sizeof(int);
 }
 
 int wavefront_occupancy(int nj, int nk, bool tb, size_t smem, int* blocks_per_sm) {
@@ -476,8 +600,9 @@ int launch_wavefront(int nj, int nk, bool tb, const WaveParams& p, int grid, siz
 
 int launch_walk(const WalkParams& p, void* stream) {
   if (p.ntb <= 0) return 0;
-  const int bs = 64;
-  walk_kernel<<<(p.ntb + bs - 1) / bs, bs, 0, (cudaStream_t)stream>>>(p);
+  if (p.NJ * p.NK / 8 > kWalkMaxW) return -1;
+  walk_kernel<<<(p.ntb + kWalkWarps - 1) / kWalkWarps, kWalkWarps * 32, 0,
+                (cudaStream_t)stream>>>(p);
   return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 

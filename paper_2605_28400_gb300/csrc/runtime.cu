@@ -231,12 +231,12 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
     d.nJ = (b + 1 + WJ - 1) / WJ;
     d.nK = (c + 1 + WK - 1) / WK;
     d.T = a + 1 + (kPR - 1) + (kPC - 1);
-    d.rowJ = d.nK * WK + 4;
-    d.rowK = d.nJ * WJ + 4;
-    d.fj_off = (int64_t)face;
-    face += (size_t)(d.nJ - 1) * (size_t)(a + 1) * (size_t)d.rowJ;
-    d.fk_off = (int64_t)face;
-    face += (size_t)(d.nK - 1) * (size_t)(a + 1) * (size_t)d.rowK;
+    // boundary records of every column task: (a+1) x (WK+4) j-records, (a+1) x WJ k-records
+    const size_t ntask = (size_t)d.nJ * (size_t)d.nK;
+    d.oj_off = (int64_t)face;
+    face += ntask * (size_t)(a + 1) * (size_t)(WK + 4);
+    d.ok_off = (int64_t)face;
+    face += ntask * (size_t)(a + 1) * (size_t)WJ;
     face = align_up(face, 4);
     d.prog_base = prog;
     prog += (int64_t)d.nJ * d.nK;
