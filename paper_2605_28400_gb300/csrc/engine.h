@@ -24,7 +24,7 @@ constexpr int kPC = 8;             // lanes of a warp along k
 constexpr int kMaxAlphabet = 32;
 constexpr int kWarpsPerCta = 4;
 constexpr int kRing = 4;           // face-staging ring slots per warp (power of two)
-constexpr int kAhead = 2;          // steps between staging a face row and using it
+constexpr int kAhead = 2;          // steps between loading a face piece and using it
 
 // Rank of each move in the tie-break (Eq. 1 listing order): rank 7 wins ties over rank 6 ...
 // rank -> (di, dj, dk):

@@ -21,9 +21,9 @@
 //   TB = true additionally keeps traceback keys (8*M' + 7, engine.h) and streams one 4-bit code
 //   per cell to HBM (one record of NJ*NK/8 words per lane per step).
 //
-// walk_kernel: one warp per traceback request. It stages a window of code records around the
-//   current cell in shared memory (all lanes load), then lane 0 follows the stored moves back
-//   through the window; repeated until the origin.
+// walk_kernel: one warp per traceback request. Lane 0 follows the stored moves back from
+//   (a, b, c) through a tube of code records along the diagonal, staged in shared memory by the
+//   whole warp in one round trip; repeated until the origin.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -91,10 +91,13 @@ constexpr unsigned kFull = 0xffffffffu;
 
 }  // namespace
 
-// Resident CTAs per SM the register budget is sized for (4 warps each).
-template <int NJ, int NK>
+// Resident CTAs per SM the register budget is sized for (4 warps each). Traceback variants hold
+// more live state (keys, code words) and serve single large triplets that need fewer resident
+// warps, so they get the larger budget.
+template <int NJ, int NK, bool TB>
 struct MinBlocks {
-  static constexpr int value = (NJ * NK >= 64) ? 2 : ((NJ * NK >= 32) ? 3 : 4);
+  static constexpr int value = (NJ * NK >= 64 || (TB && NJ * NK >= 32)) ? 2
+                               : ((NJ * NK >= 32) ? 3 : 4);
 };
 
 template <int NJ, int NK>
@@ -111,7 +114,7 @@ struct Geom {
 };
 
 template <int NJ, int NK, bool TB>
-__global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK>::value)
+__global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::value)
     wavefront_kernel(const WaveParams p) {
   using G = Geom<NJ, NK>;
   static_assert(NJ % 4 == 0 && NK % 4 == 0, "tile sides must be multiples of 4");
@@ -464,19 +467,66 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK>::value)
 }
 
 // ---------------------------------------------------------------------------------------------
-// Traceback walk: window of WI slices x WR lane rows x WC lane columns of code records.
-constexpr int kWalkWI = 16, kWalkWR = 4, kWalkWC = 2, kWalkWarps = 4, kWalkMaxW = 8;
-constexpr int kWalkRecs = kWalkWI * kWalkWR * kWalkWC;
+// Traceback walk. Optimal paths of related sequences run close to the cube's main diagonal, so
+// the warp stages a "tube" of code records along the diagonal from the current cell: for each
+// of the next kTubeS slices, the 3 x 3 lane tiles around the diagonal cell. All lanes load the
+// tube in one round trip (independent loads, then shared-memory stores); lane 0 then follows
+// the stored moves until the path leaves the tube, and the warp stages the next tube there.
+constexpr int kTubeS = 32, kTubeR = 3, kTubeC = 3;
+constexpr int kTubeRecs = kTubeS * kTubeR * kTubeC;
+constexpr int kTubePer = (kTubeRecs + 31) / 32;
 
-__global__ void __launch_bounds__(kWalkWarps * 32) walk_kernel(const WalkParams p) {
-  __shared__ uint4 wsm4[kWalkWarps * kWalkRecs * kWalkMaxW / 4];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int q = blockIdx.x * kWalkWarps + wib;
-  if (q >= p.ntb) return;  // warp-uniform
-  uint32_t* win = reinterpret_cast<uint32_t*>(wsm4) + wib * kWalkRecs * kWalkMaxW;
+template <int W>
+__device__ __forceinline__ void tube_load(uint32_t* win, int i0, int j0, int k0, int lj, int lk,
+                                          const uint32_t* codes, const TripDesc& d, int lane) {
+  constexpr int V = (W + 3) / 4;  // 16-byte vectors per record (W = 2 uses the low half)
+  uint4 v[kTubePer][V];
+  bool valid[kTubePer];
+#pragma unroll
+  for (int u = 0; u < kTubePer; ++u) {
+    const int e = lane + 32 * u;
+    const int sx = e / (kTubeR * kTubeC), rem = e % (kTubeR * kTubeC);
+    const int ii = i0 - sx;
+    const int gr = ((j0 - sx) >> lj) + rem / kTubeC - 1;
+    const int gc = ((k0 - sx) >> lk) + rem % kTubeC - 1;
+    valid[u] = e < kTubeRecs && ii >= 0 && gr >= 0 && gc >= 0 && gr < d.nJ * kPR &&
+               gc < d.nK * kPC;
+    if (valid[u]) {
+      const int task = (gr / kPR) * d.nK + (gc / kPC);
+      const int lr = gr % kPR, lcc = gc % kPC;
+      const uint32_t* src =
+          codes + (((int64_t)task * d.T + (ii + lr + lcc)) * 32 + (lr * kPC + lcc)) * W;
+      if (W == 2) {
+        const uint2 h = __ldcg(reinterpret_cast<const uint2*>(src));
+        v[u][0] = make_uint4(h.x, h.y, 0u, 0u);
+      } else {
+#pragma unroll
+        for (int q = 0; q < V; ++q) v[u][q] = __ldcg(reinterpret_cast<const uint4*>(src) + q);
+      }
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < kTubePer; ++u) {
+    if (!valid[u]) continue;
+    uint32_t* dst = win + (lane + 32 * u) * W;
+    if (W == 2) {
+      *reinterpret_cast<uint2*>(dst) = make_uint2(v[u][0].x, v[u][0].y);
+    } else {
+#pragma unroll
+      for (int q = 0; q < V; ++q) reinterpret_cast<uint4*>(dst)[q] = v[u][q];
+    }
+  }
+}
+
+template <int W>
+__global__ void __launch_bounds__(32) walk_kernel(const WalkParams p) {
+  __shared__ uint4 win4[kTubeRecs * W / 4 + 1];
+  uint32_t* win = reinterpret_cast<uint32_t*>(win4);
+  const int lane = threadIdx.x & 31;
+  const int q = blockIdx.x;
   const TripDesc& d = p.desc[p.tb_trips[q]];
   const int a = d.len[0], b = d.len[1], c = d.len[2];
-  const int NJ = p.NJ, NK = p.NK, W = NJ * NK / 8;
+  const int lj = __ffs(p.NJ) - 1, lk = __ffs(p.NK) - 1;  // tile sides are powers of two
   const int8_t* S0 = p.seq + d.s_off[0];
   const int8_t* S1 = p.seq + d.s_off[1];
   const int8_t* S2 = p.seq + d.s_off[2];
@@ -487,40 +537,21 @@ __global__ void __launch_bounds__(kWalkWarps * 32) walk_kernel(const WalkParams 
   const uint32_t* codes = p.codes + d.code_off;
   int i = a, j = b, k = c, n = 0, bad = 0;
   while ((i | j | k) != 0 && !bad) {
-    const int i0 = i, gr0 = j / NJ, gc0 = k / NK;
-    // All lanes stage the window's records (cell slices i0-WI+1..i0, lane rows gr0-WR+1..gr0,
-    // lane columns gc0-WC+1..gc0).
-    for (int e = lane; e < kWalkRecs; e += 32) {
-      const int di = e / (kWalkWR * kWalkWC), rem = e % (kWalkWR * kWalkWC);
-      const int ii = i0 - di, gr = gr0 - rem / kWalkWC, gc = gc0 - rem % kWalkWC;
-      if (ii < 0 || gr < 0 || gc < 0) continue;
-      const int task = (gr / kPR) * d.nK + (gc / kPC);
-      const int lr = gr % kPR, lcc = gc % kPC;
-      const int t = ii + lr + lcc;
-      const uint32_t* src = codes + (((int64_t)task * d.T + t) * 32 + (lr * kPC + lcc)) * W;
-      for (int w4 = 0; w4 < W; w4 += 4) {
-        if (W >= 4) {
-          *reinterpret_cast<uint4*>(win + e * kWalkMaxW + w4) =
-              __ldcg(reinterpret_cast<const uint4*>(src + w4));
-        } else {
-          *reinterpret_cast<uint2*>(win + e * kWalkMaxW + w4) =
-              __ldcg(reinterpret_cast<const uint2*>(src + w4));
-        }
-      }
-    }
+    const int i0 = i, j0 = j, k0 = k;
+    tube_load<W>(win, i0, j0, k0, lj, lk, codes, d, lane);
     __syncwarp();
     if (lane == 0) {
       while ((i | j | k) != 0) {
-        const int gr = j / NJ, gc = k / NK;
-        if (i0 - i >= kWalkWI || gr0 - gr >= kWalkWR || gc0 - gc >= kWalkWC) break;
-        const int e = (j - gr * NJ) * NK + (k - gc * NK);
-        const int rec = ((i0 - i) * kWalkWR + (gr0 - gr)) * kWalkWC + (gc0 - gc);
-        const uint32_t word = win[rec * kWalkMaxW + (e >> 3)];
+        const int sx = i0 - i;
+        if (sx >= kTubeS) break;
+        const int dr = (j >> lj) - ((j0 - sx) >> lj) + 1;
+        const int dc = (k >> lk) - ((k0 - sx) >> lk) + 1;
+        if ((unsigned)dr >= (unsigned)kTubeR || (unsigned)dc >= (unsigned)kTubeC) break;
+        const int e = ((j & ((1 << lj) - 1)) << lk) + (k & ((1 << lk) - 1));
+        const uint32_t word = win[((sx * kTubeR + dr) * kTubeC + dc) * W + (e >> 3)];
         const int rank = (word >> code_bit(e)) & 7;
         // rank -> move (Eq. 1 listing order, rank 7 first)
-        const int di = (rank == 7 || rank == 6 || rank == 5 || rank == 3) ? 1 : 0;
-        const int dj = (rank == 7 || rank == 6 || rank == 4 || rank == 2) ? 1 : 0;
-        const int dk = (rank == 7 || rank == 5 || rank == 4 || rank == 1) ? 1 : 0;
+        const int di = (0xE8 >> rank) & 1, dj = (0xD4 >> rank) & 1, dk = (0xB2 >> rank) & 1;
         if (rank == 0 || n >= cap || i < di || j < dj || k < dk) {
           bad = 1;
           break;
@@ -535,12 +566,12 @@ __global__ void __launch_bounds__(kWalkWarps * 32) walk_kernel(const WalkParams 
         ++n;
       }
     }
+    __syncwarp();
     i = __shfl_sync(kFull, i, 0);
     j = __shfl_sync(kFull, j, 0);
     k = __shfl_sync(kFull, k, 0);
     n = __shfl_sync(kFull, n, 0);
     bad = __shfl_sync(kFull, bad, 0);
-    __syncwarp();
   }
   if (lane == 0) {
     if (bad) {
@@ -600,9 +631,12 @@ int launch_wavefront(int nj, int nk, bool tb, const WaveParams& p, int grid, siz
 
 int launch_walk(const WalkParams& p, void* stream) {
   if (p.ntb <= 0) return 0;
-  if (p.NJ * p.NK / 8 > kWalkMaxW) return -1;
-  walk_kernel<<<(p.ntb + kWalkWarps - 1) / kWalkWarps, kWalkWarps * 32, 0,
-                (cudaStream_t)stream>>>(p);
+  const int W = p.NJ * p.NK / 8;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (W == 2) walk_kernel<2><<<p.ntb, 32, 0, st>>>(p);
+  else if (W == 4) walk_kernel<4><<<p.ntb, 32, 0, st>>>(p);
+  else if (W == 8) walk_kernel<8><<<p.ntb, 32, 0, st>>>(p);
+  else return -1;
   return cudaGetLastError() == cudaSuccess ? 0 : -2;
 }
 
