@@ -40,7 +40,7 @@ if ROOT not in sys.path:
 
 METRIC = "GCUPS (3D cells/s) and % of INT32 roofline; batched vs per-triplet; p50/p99 lat"
 OPS_PER_CELL = 13          # 7 adds + 6 max per cell (factored Eq. 1)
-INT32_LANES_PER_SM = 128   # nominal; see the design doc for the measured VIADDMNMX/IMNMX rate
+INT32_LANES_PER_SM = 128   # int32 ops/clk/SM: 64 fused add+max (VIADDMNMX) issues per clock per SM
 CODE_BYTES_PER_CELL = 0.5  # packed 4-bit traceback code
 
 
