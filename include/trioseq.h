@@ -50,7 +50,8 @@ typedef enum {
   TRIOSEQ_EOVERFLOW = 4, /* score bound exceeds the integer range of the engine */
   TRIOSEQ_ETIMEOUT = 5,  /* a bounded device-side wait expired; the context stays usable */
   TRIOSEQ_ECUDA = 6,     /* CUDA runtime error or no usable GPU */
-  TRIOSEQ_ENOTIMPL = 7   /* requested feature is not built */
+  TRIOSEQ_ENOTIMPL = 7,  /* requested feature is not built */
+  TRIOSEQ_ESCRATCH = 8   /* request needs more than the fixed scratch of trioseq_align_noalloc */
 } trioseq_status;
 
 /* Scoring scheme (Sec. II). `alphabet` lists the residue characters (1..32 distinct bytes);
@@ -182,6 +183,35 @@ trioseq_status trioseq_poll(trioseq_server_t srv, uint64_t ticket, int32_t* scor
 
 /* Stop the server thread after finishing admitted work and release it. */
 trioseq_status trioseq_server_destroy(trioseq_server_t srv);
+
+/* ---- allocation-free entry point ---- */
+
+/* trioseq_align_noalloc — score one triplet without allocating any memory in the call.
+ * (The paper has no counterpart: this is an integration entry point of this library.)
+ * For callers that cannot call cudaMalloc when they align: processes whose device memory is
+ * already fully reserved by another allocator (a framework's caching pool, a serving process
+ * with a fixed memory budget) or plugin hosts that forbid allocation inside their callbacks.
+ * The call places its whole workspace (encoded residues, descriptor, work queue, progress
+ * flags, boundary records) in one 64 MiB array in device memory that the library declares at
+ * file scope; every GPU that loads the library holds that array until the process exits.
+ *   scoring   : host scoring scheme as for trioseq_plan (validated in the call).
+ *   d_s0/1/2  : caller-owned DEVICE buffers of a, b, c bytes (alphabet characters, not codes);
+ *               may be null when the length is 0.
+ *   d_score   : caller-owned DEVICE int32 that receives the optimal global score.
+ *   stream    : cudaStream_t (NULL = legacy default); the call synchronises it before
+ *               returning, so the score is ready on return.
+ * Same score as trioseq_align_batch in TRIOSEQ_SCORE_ONLY mode (score only, no traceback).
+ * The first call on a device looks up the array's device address (make it before any stream
+ * capture). All calls share the array and it keeps the last call's contents; each call clears
+ * what must start at zero, and calls that overlap on the GPU (other streams, other threads)
+ * race, so callers serialise them.
+ * Errors: ESCRATCH (the triplet's workspace exceeds the 64 MiB array: roughly a*b*c > 3e8 for
+ * DNA-sized tiles), EINVAL (null pointers, bad scoring, a byte outside the alphabet),
+ * EOVERFLOW, ETIMEOUT, ECUDA. */
+trioseq_status trioseq_align_noalloc(const trioseq_scoring* scoring, const unsigned char* d_s0,
+                                     uint32_t a, const unsigned char* d_s1, uint32_t b,
+                                     const unsigned char* d_s2, uint32_t c, int32_t* d_score,
+                                     void* stream);
 
 /* Human-readable name of a status code (static storage). */
 const char* trioseq_strerror(trioseq_status st);

@@ -13,7 +13,7 @@ import numpy as np
 
 from . import build as _build
 
-OK, EINVAL, ENOMEM, EAGAIN, EOVERFLOW, ETIMEOUT, ECUDA, ENOTIMPL = range(8)
+OK, EINVAL, ENOMEM, EAGAIN, EOVERFLOW, ETIMEOUT, ECUDA, ENOTIMPL, ESCRATCH = range(9)
 SCORE_ONLY, WITH_TRACEBACK = 0, 1
 
 
@@ -78,6 +78,8 @@ def load(build_if_missing: bool = True):
                          i32),
         "trioseq_server_destroy": ([vp], i32),
         "trioseq_strerror": ([i32], ctypes.c_char_p),
+        "trioseq_align_noalloc": ([ctypes.POINTER(Scoring), vp, u32, vp, u32, vp, u32, vp, vp],
+                                  i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -93,7 +95,7 @@ def exported_symbols() -> list[str]:
             "trioseq_batch_device_scores", "trioseq_batch_alignment", "trioseq_batch_info",
             "trioseq_batch_destroy", "trioseq_batch_profile", "trioseq_batch_timing",
             "trioseq_plan_io_bytes", "trioseq_server_create", "trioseq_submit", "trioseq_poll",
-            "trioseq_server_destroy", "trioseq_strerror"]
+            "trioseq_server_destroy", "trioseq_strerror", "trioseq_align_noalloc"]
 
 
 def trioseq_strerror(status: int) -> str:
@@ -285,3 +287,17 @@ def trioseq_poll(server, ticket: int, cap: int = 0):
 
 def trioseq_server_destroy(server):
     _check(load().trioseq_server_destroy(server), "trioseq_server_destroy")
+
+
+def trioseq_align_noalloc(alphabet: str, sub, gap: int, d_s0: int, a: int, d_s1: int, b: int,
+                          d_s2: int, c: int, d_score: int, stream=None) -> int:
+    """Allocation-free scoring of one triplet. d_s0/d_s1/d_s2 are device addresses of the raw
+    sequence bytes, d_score the device address of one int32. Returns the status code (OK on
+    success; errors are returned, not raised, so callers can test ESCRATCH)."""
+    sub = np.ascontiguousarray(np.asarray(sub, dtype=np.int8))
+    sc = Scoring(alphabet.encode(), len(alphabet),
+                 sub.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)), int(gap))
+    return int(load().trioseq_align_noalloc(ctypes.byref(sc), ctypes.c_void_p(d_s0 or None), a,
+                                            ctypes.c_void_p(d_s1 or None), b,
+                                            ctypes.c_void_p(d_s2 or None), c,
+                                            ctypes.c_void_p(d_score), _stream_ptr(stream)))

@@ -471,6 +471,7 @@ const char* trioseq_strerror(trioseq_status st) {
     case TRIOSEQ_ETIMEOUT: return "bounded device wait expired";
     case TRIOSEQ_ECUDA: return "CUDA error or no usable GPU";
     case TRIOSEQ_ENOTIMPL: return "not implemented";
+    case TRIOSEQ_ESCRATCH: return "request exceeds the fixed scratch of the allocation-free call";
   }
   return "unknown status";
 }
