@@ -241,6 +241,81 @@ def time_batch(B, torch, bt, steps: int, warmup: int, stream, flush, n):
     return step_ms, kern_ms, walk_ms, scores
 
 
+def serving_measurement(B, capacity_gcups: float, n_req: int = 2000, load: float = 0.7):
+    """Serving stream: mixed DNA/protein requests (20% traceback) submitted with Poisson gaps at
+    `load` x the measured batch capacity; latency = submit to the poll that returns the result.
+    A few served results are re-aligned alone and must match exactly."""
+    from paper_2605_28400_gb300 import synth
+    dna, prot, reqs = synth.config4(n=n_req)
+    plans = [B.trioseq_plan(dna.alphabet, dna.sub, dna.gap),
+             B.trioseq_plan(prot.alphabet, prot.sub, prot.gap)]
+    cells = [len(r["triplet"][0]) * len(r["triplet"][1]) * len(r["triplet"][2]) for r in reqs]
+    mean_cells = sum(cells) / len(cells)
+    rate = load * capacity_gcups * 1e9 / mean_cells  # requests per second
+    strs = [[synth.to_str(s, (prot if r["protein"] else dna).alphabet) for s in r["triplet"]]
+            for r in reqs]
+    cap = 3 * max(len(s) for st in strs for s in st) + 16
+    srv = B.trioseq_server_create(plans)
+    t_sub, t_done, tickets, results = {}, {}, [None] * len(reqs), {}
+    lock = threading.Lock()
+
+    def submitter():
+        t0 = time.perf_counter()
+        at = 0.0
+        for i, r in enumerate(reqs):
+            at += r["gap"] / rate
+            while time.perf_counter() - t0 < at:
+                time.sleep(min(0.0005, max(0.0, at - (time.perf_counter() - t0))))
+            mode = B.WITH_TRACEBACK if r["traceback"] else B.SCORE_ONLY
+            while True:
+                st, tk = B.trioseq_submit(srv, strs[i], 1 if r["protein"] else 0, mode)
+                if st == B.OK:
+                    break
+                time.sleep(0.001)
+            with lock:
+                t_sub[tk] = time.perf_counter()
+                tickets[i] = tk
+
+    th = threading.Thread(target=submitter)
+    th.start()
+    pending = set()
+    n_done = 0
+    while n_done < len(reqs):
+        with lock:
+            pending |= {tk for tk in tickets if tk is not None and tk not in t_done}
+        for tk in list(pending):
+            st, score, rows = B.trioseq_poll(srv, tk, cap)
+            if st == B.OK:
+                t_done[tk] = time.perf_counter()
+                results[tk] = (score, rows)
+                pending.discard(tk)
+                n_done += 1
+        time.sleep(0.0002)
+    th.join()
+    B.trioseq_server_destroy(srv)
+    lat = sorted(1e3 * (t_done[tk] - t_sub[tk]) for tk in t_done)
+    span = max(t_done.values()) - min(t_sub.values())
+    same = True
+    for i in (0, 1, 2, len(reqs) // 2, len(reqs) - 1):
+        r = reqs[i]
+        mode = B.WITH_TRACEBACK if r["traceback"] else B.SCORE_ONLY
+        pl = plans[1 if r["protein"] else 0]
+        alone = B.trioseq_align_batch(pl, [strs[i]], mode)
+        score, rows = results[tickets[i]]
+        same &= score == int(alone[0])
+        if r["traceback"]:
+            same &= rows == B.trioseq_traceback(pl, 0)
+    for p in plans:
+        B.trioseq_plan_destroy(p)
+    return {"requests": len(reqs), "arrival_rate_per_s": rate, "load_vs_batch_capacity": load,
+            "mean_cells_per_request": mean_cells, "p50_ms": lat[len(lat) // 2],
+            "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))], "max_ms": lat[-1],
+            "aggregate_gcups": sum(cells) / span / 1e9, "span_s": span,
+            "identical_to_alone_sample": bool(same),
+            "mix": "70% DNA / 30% protein, 20% traceback, ancestor lognormal(ln 300, 0.8) "
+                   "clipped to [50, 2000]"}
+
+
 def aux_measurements(B, torch, stream, flush, sms, clock_mhz):
     """Secondary lines of the metric: protein n=4000 score-only roofline, and the 4096-triplet
     batch in one persistent launch versus one launch per triplet."""
@@ -294,6 +369,7 @@ def aux_measurements(B, torch, stream, flush, sms, clock_mhz):
         "batched_gcups": batched, "per_triplet_launch_gcups": per_triplet,
         "batched_over_per_triplet": batched / per_triplet, "identical_scores": bool(same),
         "cells": w.cells}
+    out["serving_stream"] = serving_measurement(B, batched)
     return out
 
 

@@ -40,14 +40,26 @@ struct DevBuf {
   ~DevBuf() {
     if (p) cudaFree(p);
   }
-  // Grow to at least `bytes` (contents are not preserved).
-  bool ensure(size_t bytes) {
+  // Grow to at least `bytes` (contents are not preserved). With a stream, the old buffer is
+  // released and the new one taken in that stream's order (no device-wide synchronisation), so
+  // a growing workspace does not stall work running on other streams.
+  bool ensure(size_t bytes, cudaStream_t st = nullptr) {
     if (bytes <= cap && p) return true;
-    if (p) cudaFree(p);
-    p = nullptr;
-    cap = 0;
     const size_t want = std::max<size_t>(bytes, 256);
-    if (cudaMalloc(&p, want) != cudaSuccess) {
+    cudaError_t e;
+    if (st) {
+      if (p) cudaFreeAsync(p, st);
+      p = nullptr;
+      cap = 0;
+      e = cudaMallocAsync(&p, want, st);
+    } else {
+      if (p) cudaFree(p);
+      p = nullptr;
+      cap = 0;
+      e = cudaMalloc(&p, want);
+    }
+    if (e != cudaSuccess) {
+      p = nullptr;
       cudaGetLastError();
       return false;
     }
@@ -91,6 +103,7 @@ struct Workspace {
   DevBuf rows;      // traceback rows
   DevBuf lens;      // alignment lengths
   HostPinned staging;
+  cudaStream_t alloc_stream = nullptr;  // grow buffers in this stream's order (serving slots)
 };
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -317,12 +330,13 @@ trioseq_status upload(trioseq_batch_s* bt, cudaStream_t st, bool pinned) {
   Workspace& ws = *bt->ws;
   const bool tb = bt->mode == TRIOSEQ_WITH_TRACEBACK;
   const size_t nprog = bt->tasks.size() + 64;
-  if (!ws.inputs.ensure(bt->inputs_bytes) || !ws.faces.ensure(bt->face_ints * sizeof(int32_t)) ||
-      !ws.progress.ensure(nprog * sizeof(int32_t)) ||
-      !ws.scores.ensure(std::max<size_t>(bt->n, 1) * sizeof(int32_t)) ||
-      (tb && (!ws.codes.ensure(bt->code_words * sizeof(uint32_t)) ||
-              !ws.rows.ensure(bt->rows_bytes) ||
-              !ws.lens.ensure(std::max<size_t>(bt->tb_trips.size(), 1) * sizeof(int32_t)))) ||
+  cudaStream_t as = ws.alloc_stream;
+  if (!ws.inputs.ensure(bt->inputs_bytes, as) || !ws.faces.ensure(bt->face_ints * sizeof(int32_t), as) ||
+      !ws.progress.ensure(nprog * sizeof(int32_t), as) ||
+      !ws.scores.ensure(std::max<size_t>(bt->n, 1) * sizeof(int32_t), as) ||
+      (tb && (!ws.codes.ensure(bt->code_words * sizeof(uint32_t), as) ||
+              !ws.rows.ensure(bt->rows_bytes, as) ||
+              !ws.lens.ensure(std::max<size_t>(bt->tb_trips.size(), 1) * sizeof(int32_t), as))) ||
       (pinned && !ws.staging.ensure(bt->inputs_bytes)))
     return TRIOSEQ_ENOMEM;
   std::vector<char> pageable;
@@ -659,24 +673,337 @@ trioseq_status trioseq_batch_destroy(trioseq_batch_t bt) {
   return TRIOSEQ_OK;
 }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Serving: continuous batching behind submit/poll.
+//
+// A server thread owns a FIFO of requests and kSlots slots, each a CUDA stream with its own
+// reusable workspace and pinned result buffer. Every tick it (1) harvests slots whose launch has
+// completed (event query, never a blocking wait) and publishes their results, then (2) admits
+// pending requests into free slots: the oldest request fixes the (scoring, mode) group, and
+// further requests of that group join the launch in arrival order while the launch's workspace
+// estimate stays within the slot's share of the device-memory budget. Requests that arrive
+// while other launches run are therefore admitted as soon as a slot frees, and launches of
+// different slots overlap on the device. poll() only looks up the result table.
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct SrvReq {
+  uint64_t ticket = 0;
+  int32_t plan_id = 0;
+  uint32_t mode = 0;
+  std::string s[3];
+  size_t bytes = 0;
+};
+
+struct SrvRes {
+  trioseq_status st = TRIOSEQ_OK;
+  int32_t score = 0;
+  bool has_rows = false;
+  std::string rows[3];
+};
+
+struct SrvSlot {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  bool busy = false;
+  Workspace ws;
+  HostPinned out;  // scores | error word | alignment lengths | rows
+  size_t off_err = 0, off_lens = 0, off_rows = 0;
+  std::unique_ptr<trioseq_batch_s> batch;
+  std::vector<SrvReq> reqs;
+  trioseq_status launch_st = TRIOSEQ_OK;
+};
+
+// Device bytes one request adds to a launch's workspace (boundary records, flags, and in
+// traceback mode the code stream and rows).
+size_t request_bytes(const trioseq_plan_s* plan, uint32_t mode, const uint32_t len[3]) {
+  const bool tb = mode == TRIOSEQ_WITH_TRACEBACK;
+  const Variant v = tb ? plan->tb_variant : plan->score_variant;
+  const size_t WJ = (size_t)kPR * v.nj, WK = (size_t)kPC * v.nk, W = (size_t)v.nj * v.nk / 8;
+  const size_t a = len[0], b = len[1], c = len[2];
+  const size_t nJ = (b + 1 + WJ - 1) / WJ, nK = (c + 1 + WK - 1) / WK, T = a + 1 + 10;
+  size_t bytes = 4 * nJ * nK * (a + 1) * ((WK + 4) + WJ) + 4 * nJ * nK + 256 + a + b + c + 48;
+  if (tb) bytes += 4 * nJ * nK * T * 32 * W + 3 * (a + b + c) + 64;
+  return bytes;
+}
+
+}  // namespace
+
+struct trioseq_server_s {
+  static constexpr int kSlots = 4;
+  std::vector<trioseq_plan_s*> plans;
+  int device = 0;
+  size_t slot_budget = 0;
+  size_t max_pending = (size_t)1 << 20;
+  size_t max_batch = 1024;
+  std::thread th;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<SrvReq> pending;
+  std::unordered_map<uint64_t, SrvRes> done;
+  std::unordered_map<uint64_t, int> live;  // submitted and not yet consumed by poll
+  uint64_t next_ticket = 1;
+  bool stop = false;
+  SrvSlot slots[kSlots];
+};
+
+namespace {
+
+// Enqueue one launch for the requests in `sl.reqs` on the slot's stream (server thread, no lock).
+trioseq_status srv_launch(trioseq_server_s* S, SrvSlot& sl) {
+  const int32_t pid = sl.reqs.front().plan_id;
+  const uint32_t mode = sl.reqs.front().mode;
+  trioseq_plan_s* plan = S->plans[pid];
+  std::vector<trioseq_triplet> trips(sl.reqs.size());
+  for (size_t i = 0; i < sl.reqs.size(); i++)
+    for (int q = 0; q < 3; q++) {
+      trips[i].s[q] = sl.reqs[i].s[q].data();
+      trips[i].len[q] = (uint32_t)sl.reqs[i].s[q].size();
+    }
+  sl.batch.reset(new (std::nothrow) trioseq_batch_s());
+  if (!sl.batch) return TRIOSEQ_ENOMEM;
+  trioseq_batch_s* bt = sl.batch.get();
+  trioseq_status st = build_batch(plan, trips.data(), trips.size(), mode, bt);
+  if (st != TRIOSEQ_OK) return st;
+  bt->ws = &sl.ws;
+  if ((st = upload(bt, sl.stream, true)) != TRIOSEQ_OK) return st;
+  if ((st = run(bt, sl.stream)) != TRIOSEQ_OK) return st;
+  const bool tb = mode == TRIOSEQ_WITH_TRACEBACK;
+  const size_t n = bt->n, ntb = bt->tb_trips.size();
+  sl.off_err = align_up(n * 4, 64);
+  sl.off_lens = sl.off_err + 64;
+  sl.off_rows = align_up(sl.off_lens + ntb * 4, 64);
+  const size_t need = sl.off_rows + (tb ? bt->rows_bytes : 0);
+  if (!sl.out.ensure(need)) return TRIOSEQ_ENOMEM;
+  char* h = reinterpret_cast<char*>(sl.out.p);
+  int32_t* err = sl.ws.progress.as<int32_t>() + bt->tasks.size() + 32;
+  cudaError_t e = cudaMemcpyAsync(h, sl.ws.scores.p, n * 4, cudaMemcpyDeviceToHost, sl.stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(h + sl.off_err, err, 4, cudaMemcpyDeviceToHost, sl.stream);
+  if (e == cudaSuccess && tb && ntb) {
+    e = cudaMemcpyAsync(h + sl.off_lens, sl.ws.lens.p, ntb * 4, cudaMemcpyDeviceToHost,
+                        sl.stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(h + sl.off_rows, sl.ws.rows.p, bt->rows_bytes, cudaMemcpyDeviceToHost,
+                          sl.stream);
+  }
+  if (e == cudaSuccess) e = cudaEventRecord(sl.done, sl.stream);
+  return cuda_status(e);
+}
+
+// Turn a finished slot into results (server thread, lock held).
+void srv_harvest(trioseq_server_s* S, SrvSlot& sl) {
+  trioseq_batch_s* bt = sl.batch.get();
+  const char* h = reinterpret_cast<const char*>(sl.out.p);
+  trioseq_status st = sl.launch_st;
+  // A launch that failed part-way may have left work on the stream: drain it before the
+  // slot's workspace is reused.
+  if (st != TRIOSEQ_OK) cudaStreamSynchronize(sl.stream);
+  if (st == TRIOSEQ_OK && cudaEventQuery(sl.done) != cudaSuccess) st = TRIOSEQ_ECUDA;
+  int32_t herr = 0;
+  if (st == TRIOSEQ_OK) {
+    std::memcpy(&herr, h + sl.off_err, 4);
+    if (herr & 1) st = TRIOSEQ_ETIMEOUT;
+    else if (herr & 2) st = TRIOSEQ_ECUDA;
+  }
+  const char* alpha = st == TRIOSEQ_OK ? bt->plan->alphabet : nullptr;
+  for (size_t i = 0; i < sl.reqs.size(); i++) {
+    SrvRes r;
+    r.st = st;
+    if (st == TRIOSEQ_OK) {
+      std::memcpy(&r.score, h + 4 * i, 4);
+      const int32_t q = bt->tb_of[i];
+      if (q >= 0) {
+        int32_t L = 0;
+        std::memcpy(&L, h + sl.off_lens + 4 * (size_t)q, 4);
+        const int32_t rc = bt->row_cap[q];
+        const uint8_t* base =
+            reinterpret_cast<const uint8_t*>(h + sl.off_rows + (size_t)bt->row_off[q]);
+        r.has_rows = true;
+        for (int s = 0; s < 3; s++) {
+          r.rows[s].resize((size_t)L);
+          const uint8_t* row = base + (size_t)s * rc + (rc - L);
+          for (int32_t t = 0; t < L; t++) r.rows[s][t] = row[t] == 255 ? '-' : alpha[row[t]];
+        }
+      }
+    }
+    S->done[sl.reqs[i].ticket] = std::move(r);
+  }
+  sl.reqs.clear();
+  sl.batch.reset();
+  sl.busy = false;
+}
+
+void srv_loop(trioseq_server_s* S) {
+  cudaSetDevice(S->device);
+  std::unique_lock<std::mutex> lk(S->mu);
+  for (;;) {
+    bool busy_any = false, acted = false;
+    for (auto& sl : S->slots) {
+      if (!sl.busy) continue;
+      if (sl.launch_st != TRIOSEQ_OK || cudaEventQuery(sl.done) != cudaErrorNotReady) {
+        srv_harvest(S, sl);
+        acted = true;
+      } else {
+        busy_any = true;
+      }
+    }
+    for (auto& sl : S->slots) {
+      if (sl.busy || S->pending.empty()) continue;
+      // Form a launch: the oldest request fixes the group; same-group requests follow in arrival
+      // order while the workspace estimate fits the slot's share of the budget.
+      const int32_t pid = S->pending.front().plan_id;
+      const uint32_t mode = S->pending.front().mode;
+      size_t bytes = 0;
+      std::deque<SrvReq> rest;
+      while (!S->pending.empty()) {
+        SrvReq& r = S->pending.front();
+        const bool same = r.plan_id == pid && r.mode == mode;
+        if (same && sl.reqs.size() < S->max_batch &&
+            (sl.reqs.empty() || bytes + r.bytes <= S->slot_budget)) {
+          bytes += r.bytes;
+          sl.reqs.push_back(std::move(r));
+        } else {
+          rest.push_back(std::move(r));
+        }
+        S->pending.pop_front();
+        if (sl.reqs.size() >= S->max_batch || bytes >= S->slot_budget) break;
+      }
+      while (!rest.empty()) {  // keep arrival order of what was skipped
+        S->pending.push_front(std::move(rest.back()));
+        rest.pop_back();
+      }
+      sl.busy = true;
+      acted = true;
+      if (bytes > S->slot_budget) {  // a single request larger than the budget
+        sl.launch_st = TRIOSEQ_ENOMEM;
+        continue;
+      }
+      lk.unlock();
+      sl.launch_st = srv_launch(S, sl);
+      lk.lock();
+      busy_any = true;
+    }
+    if (S->stop && S->pending.empty() && !busy_any) break;
+    if (!acted) S->cv.wait_for(lk, std::chrono::microseconds(busy_any ? 20 : 2000));
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
 trioseq_status trioseq_server_create(const trioseq_plan_t* plans, int32_t nplans,
                                      size_t hbm_budget, trioseq_server_t* out) {
-  (void)plans;
-  (void)nplans;
-  (void)hbm_budget;
-  if (out) *out = nullptr;
-  return TRIOSEQ_ENOTIMPL;
+  if (!out) return TRIOSEQ_EINVAL;
+  *out = nullptr;
+  if (!plans || nplans < 1) return TRIOSEQ_EINVAL;
+  for (int32_t i = 0; i < nplans; i++)
+    if (!plans[i] || plans[i]->device != plans[0]->device) return TRIOSEQ_EINVAL;
+  std::unique_ptr<trioseq_server_s> S(new (std::nothrow) trioseq_server_s());
+  if (!S) return TRIOSEQ_ENOMEM;
+  S->plans.assign(plans, plans + nplans);
+  S->device = plans[0]->device;
+  DeviceGuard g(S->device);
+  if (hbm_budget == 0) {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return cuda_status(cudaGetLastError());
+    hbm_budget = fr / 10 * 8;
+  }
+  S->slot_budget = std::max<size_t>(hbm_budget / trioseq_server_s::kSlots, 1 << 20);
+  for (auto& sl : S->slots) {
+    if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess)
+      return cuda_status(cudaGetLastError());
+    sl.ws.alloc_stream = sl.stream;
+  }
+  try {
+    S->th = std::thread(srv_loop, S.get());
+  } catch (...) {
+    return TRIOSEQ_ENOMEM;
+  }
+  *out = S.release();
+  return TRIOSEQ_OK;
 }
 
-trioseq_status trioseq_submit(trioseq_server_t, const trioseq_triplet*, int32_t, uint32_t,
-                              uint64_t*) {
-  return TRIOSEQ_ENOTIMPL;
+trioseq_status trioseq_submit(trioseq_server_t S, const trioseq_triplet* t, int32_t plan_id,
+                              uint32_t mode, uint64_t* ticket) {
+  if (!S || !t || !ticket || plan_id < 0 || plan_id >= (int32_t)S->plans.size() ||
+      mode > TRIOSEQ_WITH_TRACEBACK)
+    return TRIOSEQ_EINVAL;
+  const trioseq_plan_s* plan = S->plans[plan_id];
+  SrvReq r;
+  r.plan_id = plan_id;
+  r.mode = mode;
+  int64_t sumlen = 0;
+  for (int q = 0; q < 3; q++) {
+    if (t->len[q] && !t->s[q]) return TRIOSEQ_EINVAL;
+    if (t->len[q] > (1u << 24)) return TRIOSEQ_EOVERFLOW;
+    const unsigned char* src = reinterpret_cast<const unsigned char*>(t->s[q]);
+    for (uint32_t e = 0; e < t->len[q]; e++)
+      if (plan->lut[src[e]] < 0) return TRIOSEQ_EINVAL;
+    r.s[q].assign(t->s[q] ? t->s[q] : "", t->len[q]);
+    sumlen += t->len[q];
+  }
+  if ((int64_t)plan->max_abs_sig2 * sumlen >= (1LL << 26) - 1) return TRIOSEQ_EOVERFLOW;
+  r.bytes = request_bytes(plan, mode, t->len);
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    if (S->stop) return TRIOSEQ_EINVAL;
+    if (S->pending.size() >= S->max_pending) return TRIOSEQ_EAGAIN;
+    r.ticket = S->next_ticket++;
+    *ticket = r.ticket;
+    S->live[r.ticket] = 0;
+    S->pending.push_back(std::move(r));
+  }
+  S->cv.notify_one();
+  return TRIOSEQ_OK;
 }
 
-trioseq_status trioseq_poll(trioseq_server_t, uint64_t, int32_t*, char* [3], size_t, size_t*) {
-  return TRIOSEQ_ENOTIMPL;
+trioseq_status trioseq_poll(trioseq_server_t S, uint64_t ticket, int32_t* score, char* rows[3],
+                            size_t cap, size_t* aln_len) {
+  if (!S) return TRIOSEQ_EINVAL;
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->done.find(ticket);
+  if (it == S->done.end()) return S->live.count(ticket) ? TRIOSEQ_EAGAIN : TRIOSEQ_EINVAL;
+  SrvRes& r = it->second;
+  if (r.st == TRIOSEQ_OK && r.has_rows) {
+    if (aln_len) *aln_len = r.rows[0].size();
+    if (rows) {
+      if (cap < r.rows[0].size() || !rows[0] || !rows[1] || !rows[2]) return TRIOSEQ_EINVAL;
+      for (int s = 0; s < 3; s++) std::memcpy(rows[s], r.rows[s].data(), r.rows[s].size());
+    }
+  } else if (aln_len) {
+    *aln_len = 0;
+  }
+  if (score) *score = r.score;
+  const trioseq_status st = r.st;
+  S->done.erase(it);
+  S->live.erase(ticket);
+  return st;
 }
 
-trioseq_status trioseq_server_destroy(trioseq_server_t) { return TRIOSEQ_ENOTIMPL; }
+trioseq_status trioseq_server_destroy(trioseq_server_t S) {
+  if (!S) return TRIOSEQ_OK;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+  }
+  S->cv.notify_all();
+  if (S->th.joinable()) S->th.join();
+  {
+    DeviceGuard g(S->device);
+    for (auto& sl : S->slots) {
+      if (sl.stream) cudaStreamSynchronize(sl.stream);
+      if (sl.done) cudaEventDestroy(sl.done);
+      if (sl.stream) cudaStreamDestroy(sl.stream);
+    }
+  }
+  delete S;
+  return TRIOSEQ_OK;
+}
 
 }  // extern "C"

@@ -1,0 +1,99 @@
+"""Serving through submit/poll: continuous batching must not change any result.
+
+A mixed stream (DNA and protein scoring, score-only and traceback requests, uneven lengths) is
+submitted while earlier requests are still on the GPU. Every result is compared with the same
+request aligned alone through trioseq_align_batch (tolerance 0: scores and rows identical), and
+a sample with the CPU oracle.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_28400_gb300 import binding as B
+from paper_2605_28400_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _poll_all(srv, tickets, cap, timeout_s=120.0):
+    out = {}
+    t0 = time.time()
+    while len(out) < len(tickets):
+        for tk in tickets:
+            if tk in out:
+                continue
+            st, score, rows = B.trioseq_poll(srv, tk, cap)
+            if st == B.OK:
+                out[tk] = (score, rows)
+        assert time.time() - t0 < timeout_s, "serving did not finish in time"
+        time.sleep(0.0005)
+    return out
+
+
+def test_mixed_stream_equals_alone():
+    dna, prot = synth.dna_scoring(), synth.protein_scoring(1004)
+    plans = [B.trioseq_plan(dna.alphabet, dna.sub, dna.gap),
+             B.trioseq_plan(prot.alphabet, prot.sub, prot.gap)]
+    rng = np.random.default_rng(7)
+    reqs = []
+    for i in range(48):
+        protein = bool(i % 3 == 2)
+        sc = prot if protein else dna
+        L = int(rng.integers(10, 220))
+        trip = synth.related_triplet(99, i, L, sc, 0.1, 0.03, 2.0)
+        reqs.append((1 if protein else 0, bool(i % 5 == 0), trip, sc))
+    srv = B.trioseq_server_create(plans)
+    try:
+        tickets = []
+        for pid, tb, trip, sc in reqs:
+            st, tk = B.trioseq_submit(srv, [synth.to_str(s, sc.alphabet) for s in trip], pid,
+                                      B.WITH_TRACEBACK if tb else B.SCORE_ONLY)
+            assert st == B.OK
+            tickets.append(tk)
+        cap = 3 * 300
+        got = _poll_all(srv, tickets, cap)
+        # a consumed ticket is unknown afterwards
+        with pytest.raises(B.TrioseqError) as e:
+            B.trioseq_poll(srv, tickets[0], cap)
+        assert e.value.status == B.EINVAL
+    finally:
+        B.trioseq_server_destroy(srv)
+    try:
+        for (pid, tb, trip, sc), tk in zip(reqs, tickets):
+            strs = [synth.to_str(s, sc.alphabet) for s in trip]
+            alone = B.trioseq_align_batch(plans[pid], [strs],
+                                          B.WITH_TRACEBACK if tb else B.SCORE_ONLY)
+            score, rows = got[tk]
+            assert score == int(alone[0])
+            if tb:
+                assert rows == B.trioseq_traceback(plans[pid], 0)
+        for (pid, tb, trip, sc), tk in list(zip(reqs, tickets))[:6]:
+            assert got[tk][0] == oracle.align(*trip, sc.sub, sc.gap)
+    finally:
+        for p in plans:
+            B.trioseq_plan_destroy(p)
+
+
+def test_server_rejects_bad_requests():
+    dna = synth.dna_scoring()
+    plan = B.trioseq_plan(dna.alphabet, dna.sub, dna.gap)
+    srv = B.trioseq_server_create([plan])
+    try:
+        with pytest.raises(B.TrioseqError) as e:
+            B.trioseq_submit(srv, ["ACGN", "A", "C"], 0)
+        assert e.value.status == B.EINVAL
+        with pytest.raises(B.TrioseqError):
+            B.trioseq_submit(srv, ["ACG", "A", "C"], 5)  # unknown plan
+        with pytest.raises(B.TrioseqError) as e:
+            B.trioseq_poll(srv, 123456789, 0)
+        assert e.value.status == B.EINVAL
+        st, tk = B.trioseq_submit(srv, ["ACGT" * 30, "ACGA" * 30, "AGGT" * 30], 0)
+        assert st == B.OK
+        got = _poll_all(srv, [tk], 0)
+        plan_alone = B.trioseq_align_batch(plan, [["ACGT" * 30, "ACGA" * 30, "AGGT" * 30]])
+        assert got[tk][0] == int(plan_alone[0])
+    finally:
+        B.trioseq_server_destroy(srv)
+        B.trioseq_plan_destroy(plan)
