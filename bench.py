@@ -6,9 +6,12 @@ numerator, Sec. V-A, scaled to giga). One step = one full pass of the hot path o
 workload: workspace reset, the persistent wavefront kernel (all cells of Eq. 1, with the packed
 traceback-code stream in traceback mode), and the traceback walk.
 
-Default workload: one related DNA triplet, ancestor length 1000 with three descendants
-(5% substitutions, 2% indels of geometric length, mean 2), match +2 / mismatch -1 / gap -2,
-score + traceback (~1e9 cells).
+Default workload: the single-triplet, score-only case the roofline fraction is quoted on: one
+related protein triplet, ancestor length 4000 with three descendants (15% substitutions, 3%
+indels of geometric length, mean 3), seeded 20 x 20 substitution matrix, gap -4 (~6.4e10 cells).
+The aux object adds the traceback workload (related DNA triplet, ancestor 1000, score + 4-bit
+codes + walk), the 4096-triplet batch against one launch per triplet, and a serving stream with
+p50/p99 latency.
 
 value : device-resident inputs (uploaded once), CUDA events on the launching stream around each
         step, L2 flushed (256 MiB write) between timed steps outside the events.
@@ -316,25 +319,37 @@ def serving_measurement(B, capacity_gcups: float, n_req: int = 2000, load: float
                    "clipped to [50, 2000]"}
 
 
-def aux_measurements(B, torch, stream, flush, sms, clock_mhz):
-    """Secondary lines of the metric: protein n=4000 score-only roofline, and the 4096-triplet
-    batch in one persistent launch versus one launch per triplet."""
+def aux_measurements(B, torch, stream, flush, sms, clock_mhz, skip: str):
+    """Secondary lines of the metric: the traceback workload (related DNA triplet n~1000, score +
+    4-bit codes + walk), the 4096-triplet batch in one persistent launch versus one launch per
+    triplet, and the serving stream (p50/p99 latency)."""
     from paper_2605_28400_gb300 import synth
     out = {}
-    w = synth.config3()
-    plan = B.trioseq_plan(w.scoring.alphabet, w.scoring.sub, w.scoring.gap)
-    bt = B.trioseq_batch_create(plan, triplet_strings(w), B.SCORE_ONLY)
-    sm, km, _, sc = time_batch(B, torch, bt, 5, 2, stream, flush, 1)
-    kmean = statistics.mean(km)
-    ach = OPS_PER_CELL * w.cells / (kmean / 1e3) / 1e12
-    peak = sms * INT32_LANES_PER_SM * clock_mhz * 1e6 / 1e12
-    out["protein4000_score_only"] = {
-        "gcups": w.cells / (statistics.mean(sm) / 1e3) / 1e9, "kernel_ms": kmean,
-        "cells": w.cells, "score": int(sc[0]),
-        "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TOPS (int32)",
-                     "frac": ach / peak}}
-    B.trioseq_batch_destroy(bt)
-    B.trioseq_plan_destroy(plan)
+    for key in ("dna1000", "protein4000"):
+        if key == skip:
+            continue
+        make, desc = workloads()[key]
+        w = make()
+        plan = B.trioseq_plan(w.scoring.alphabet, w.scoring.sub, w.scoring.gap)
+        bt = B.trioseq_batch_create(plan, triplet_strings(w),
+                                    B.WITH_TRACEBACK if w.traceback else B.SCORE_ONLY)
+        sm, km, wk, sc = time_batch(B, torch, bt, 10, 3, stream, flush, 1)
+        kmean = statistics.mean(km)
+        ach = OPS_PER_CELL * w.cells / (kmean / 1e3) / 1e12
+        peak = sms * INT32_LANES_PER_SM * clock_mhz * 1e6 / 1e12
+        entry = {"workload": f"{w.name}: {desc}",
+                 "gcups": w.cells / (statistics.mean(sm) / 1e3) / 1e9,
+                 "ms_per_step": statistics.mean(sm), "kernel_ms": kmean, "cells": w.cells,
+                 "score": int(sc[0]),
+                 "roofline": {"bound": "alu", "achieved": ach, "peak": peak,
+                              "unit": "TOPS (int32)", "frac": ach / peak,
+                              "traffic": measured_traffic(key)}}
+        if w.traceback:
+            entry["walk_ms"] = statistics.mean(wk)
+            entry["roofline"]["code_stream_gbs"] = CODE_BYTES_PER_CELL * w.cells / kmean / 1e6
+        out[key] = entry
+        B.trioseq_batch_destroy(bt)
+        B.trioseq_plan_destroy(plan)
 
     w = synth.config2()
     strs = triplet_strings(w)
@@ -376,10 +391,10 @@ def aux_measurements(B, torch, stream, flush, sms, clock_mhz):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(workloads()), default="dna1000")
+    ap.add_argument("--workload", choices=sorted(workloads()), default="protein4000")
     ap.add_argument("--no-aux", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
@@ -490,7 +505,7 @@ def main():
     B.trioseq_plan_destroy(plan)
 
     if rank == 0 and not args.no_aux:
-        line["aux"] = aux_measurements(B, torch, stream, flush, sms, clock_mhz)
+        line["aux"] = aux_measurements(B, torch, stream, flush, sms, clock_mhz, args.workload)
     if rank == 0 and not args.no_cpu:
         cb, _ = cpu_oracle_sample(w, 2.5e8, tb)
         line["cpu_baseline"] = cb
