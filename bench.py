@@ -331,8 +331,9 @@ def aux_measurements(B, torch, stream, flush, sms, clock_mhz, skip: str):
         make, desc = workloads()[key]
         w = make()
         plan = B.trioseq_plan(w.scoring.alphabet, w.scoring.sub, w.scoring.gap)
-        bt = B.trioseq_batch_create(plan, triplet_strings(w),
-                                    B.WITH_TRACEBACK if w.traceback else B.SCORE_ONLY)
+        mode = B.WITH_TRACEBACK if w.traceback else B.SCORE_ONLY
+        tuned = B.trioseq_plan_autotune(plan, triplet_strings(w), mode)
+        bt = B.trioseq_batch_create(plan, triplet_strings(w), mode)
         sm, km, wk, sc = time_batch(B, torch, bt, 10, 3, stream, flush, 1)
         kmean = statistics.mean(km)
         ach = OPS_PER_CELL * w.cells / (kmean / 1e3) / 1e12
@@ -340,7 +341,7 @@ def aux_measurements(B, torch, stream, flush, sms, clock_mhz, skip: str):
         entry = {"workload": f"{w.name}: {desc}",
                  "gcups": w.cells / (statistics.mean(sm) / 1e3) / 1e9,
                  "ms_per_step": statistics.mean(sm), "kernel_ms": kmean, "cells": w.cells,
-                 "score": int(sc[0]),
+                 "score": int(sc[0]), "tuned": tuned,
                  "roofline": {"bound": "alu", "achieved": ach, "peak": peak,
                               "unit": "TOPS (int32)", "frac": ach / peak,
                               "traffic": measured_traffic(key)}}
@@ -354,6 +355,7 @@ def aux_measurements(B, torch, stream, flush, sms, clock_mhz, skip: str):
     w = synth.config2()
     strs = triplet_strings(w)
     plan = B.trioseq_plan(w.scoring.alphabet, w.scoring.sub, w.scoring.gap)
+    tuned_batch = B.trioseq_plan_autotune(plan, strs, B.SCORE_ONLY)
     bt = B.trioseq_batch_create(plan, strs, B.SCORE_ONLY)
     sm, km, _, sc_batched = time_batch(B, torch, bt, 5, 2, stream, flush, len(strs))
     batched = w.cells / (statistics.mean(sm) / 1e3) / 1e9
@@ -383,6 +385,7 @@ def aux_measurements(B, torch, stream, flush, sms, clock_mhz, skip: str):
     out["batch4096_score_only"] = {
         "batched_gcups": batched, "per_triplet_launch_gcups": per_triplet,
         "batched_over_per_triplet": batched / per_triplet, "identical_scores": bool(same),
+        "tuned_batched": tuned_batch,
         "cells": w.cells}
     out["serving_stream"] = serving_measurement(B, batched)
     return out
@@ -427,6 +430,7 @@ def main():
     uuid = uuid if uuid.startswith("GPU-") else (f"GPU-{uuid}" if uuid else None)
 
     plan = B.trioseq_plan(w.scoring.alphabet, w.scoring.sub, w.scoring.gap)
+    tuned = B.trioseq_plan_autotune(plan, strs, mode)  # untimed: picks tile and interval
     bt = B.trioseq_batch_create(plan, strs, mode)
     info = B.trioseq_batch_info(bt)
     stream = torch.cuda.current_stream()
@@ -493,6 +497,7 @@ def main():
             "config": {"workload": f"{w.name}: {desc}", "cells_per_step": w.cells,
                        "triplets": len(strs), "mode": "score+traceback" if tb else "score",
                        "column_tasks": info["tasks"], "tile": f"{info['tile'][0]}x{info['tile'][1]}",
+                       "progress_interval": tuned["ti"], "autotuned": True,
                        "l2": "256 MiB flush between timed steps (outside the events)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roof,

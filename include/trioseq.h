@@ -152,6 +152,20 @@ trioseq_status trioseq_batch_destroy(trioseq_batch_t batch);
 trioseq_status trioseq_batch_profile(trioseq_batch_t batch, int32_t enable);
 trioseq_status trioseq_batch_timing(trioseq_batch_t batch, float ms[2]);
 
+/* trioseq_plan_autotune — pick the kernel variant for a class of work by measuring it.
+ * Runs the sample batch (host strings, n >= 1, mode as for trioseq_align_batch) once per
+ * candidate — every instantiated register tile per lane (8x8, 4x8, 4x4 cells, i.e. column blocks
+ * of 32x64, 16x64 and 16x32 cells per warp) times progress intervals of 4, 8 and 16 steps —
+ * times two passes of each with CUDA events on the legacy default stream, and remembers the
+ * fastest in the plan for batches of the same mode, the same single-or-batch kind, and the same
+ * bit length of the longest sequence. Later batches of that class use it; other classes keep
+ * the defaults (8x8 score-only, 4x8 traceback, interval 8). Outputs (any may be null) report
+ * the choice. The plan's device memory is untouched; a temporary workspace is used.
+ * Errors: EINVAL, EOVERFLOW, ENOMEM, ETIMEOUT, ECUDA. */
+trioseq_status trioseq_plan_autotune(trioseq_plan_t plan, const trioseq_triplet* sample, size_t n,
+                                     uint32_t mode, int32_t* tile_j, int32_t* tile_k,
+                                     int32_t* ti);
+
 /* Bytes copied host->device (encoded inputs, descriptors, queue) and device->host (scores,
  * error word, alignments) by the last trioseq_align_batch call on this plan. */
 trioseq_status trioseq_plan_io_bytes(trioseq_plan_t plan, uint64_t* h2d, uint64_t* d2h);

@@ -80,6 +80,7 @@ def load(build_if_missing: bool = True):
         "trioseq_strerror": ([i32], ctypes.c_char_p),
         "trioseq_align_noalloc": ([ctypes.POINTER(Scoring), vp, u32, vp, u32, vp, u32, vp, vp],
                                   i32),
+        "trioseq_plan_autotune": ([vp, ctypes.POINTER(Triplet), sz, u32, i32p, i32p, i32p], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -95,7 +96,19 @@ def exported_symbols() -> list[str]:
             "trioseq_batch_device_scores", "trioseq_batch_alignment", "trioseq_batch_info",
             "trioseq_batch_destroy", "trioseq_batch_profile", "trioseq_batch_timing",
             "trioseq_plan_io_bytes", "trioseq_server_create", "trioseq_submit", "trioseq_poll",
-            "trioseq_server_destroy", "trioseq_strerror", "trioseq_align_noalloc"]
+            "trioseq_server_destroy", "trioseq_strerror", "trioseq_align_noalloc",
+            "trioseq_plan_autotune"]
+
+
+def trioseq_plan_autotune(plan, sample, mode: int = SCORE_ONLY) -> dict:
+    """Measure the kernel variants on `sample` and remember the fastest for its class."""
+    arr, keep = _triplet_array(sample)
+    tj, tk, ti = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    _check(load().trioseq_plan_autotune(plan, arr, len(sample), int(mode), ctypes.byref(tj),
+                                        ctypes.byref(tk), ctypes.byref(ti)),
+           "trioseq_plan_autotune")
+    del keep
+    return {"tile": (tj.value, tk.value), "ti": ti.value}
 
 
 def trioseq_strerror(status: int) -> str:

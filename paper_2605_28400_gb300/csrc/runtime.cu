@@ -131,7 +131,24 @@ struct trioseq_plan_s {
   int64_t wait_ns = 2000000000LL;  // 2 s without progress = give up
   Variant score_variant{8, 8};
   Variant tb_variant{4, 8};
+  // Autotuner cache: (mode, single triplet or batch, bit length of the longest sequence) ->
+  // fastest (tile, progress interval) measured by trioseq_plan_autotune.
+  struct Tuned {
+    Variant var;
+    int TI;
+  };
+  std::map<int, Tuned> tuned;
+  bool tuning = false;     // set while the autotuner forces candidates
+  Tuned forced{{8, 8}, 8};
 };
+
+namespace {
+int tune_key(uint32_t mode, size_t n, uint32_t maxlen) {
+  int bits = 0;
+  while ((maxlen >> bits) > 0 && bits < 31) ++bits;
+  return (int)mode * 1000 + (n > 1 ? 100 : 0) + bits;
+}
+}  // namespace
 
 struct trioseq_batch_s {
   trioseq_plan_s* plan = nullptr;
@@ -152,6 +169,7 @@ struct trioseq_batch_s {
   size_t off_desc = 0, off_tasks = 0, off_tb = 0, off_rowoff = 0, off_rowcap = 0, inputs_bytes = 0;
   int grid = 0;
   size_t smem = 0;
+  int TI = 8;  // progress-publication interval of this batch's launches
   bool uploaded = false;
   // results of the last run (host)
   std::vector<uint8_t> h_rows;
@@ -202,6 +220,22 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
   bt->n = n;
   bt->mode = mode;
   bt->var = tb ? plan->tb_variant : plan->score_variant;
+  bt->TI = plan->TI;
+  {
+    uint32_t maxlen = 0;
+    for (size_t t = 0; t < n; t++)
+      for (int q = 0; q < 3; q++) maxlen = std::max(maxlen, trip[t].len[q]);
+    if (plan->tuning) {
+      bt->var = plan->forced.var;
+      bt->TI = plan->forced.TI;
+    } else {
+      auto it = plan->tuned.find(tune_key(mode, n, maxlen));
+      if (it != plan->tuned.end()) {
+        bt->var = it->second.var;
+        bt->TI = it->second.TI;
+      }
+    }
+  }
   const int NJ = bt->var.nj, NK = bt->var.nk;
   const int WJ = kPR * NJ, WK = kPC * NK, W = NJ * NK / 8;
   // encode + pack (16-byte aligned sequences)
@@ -385,7 +419,7 @@ trioseq_status run(trioseq_batch_s* bt, cudaStream_t st) {
   p.codes = tb ? ws.codes.as<uint32_t>() : nullptr;
   p.scores = ws.scores.as<int32_t>();
   p.err = err;
-  p.TI = std::max(1, plan->TI);
+  p.TI = std::max(1, bt->TI);
   p.wait_ns = plan->wait_ns;
   bt->timed = false;
   if (bt->profile && cudaEventRecord(bt->ev[0], st) != cudaSuccess)
@@ -655,6 +689,72 @@ trioseq_status trioseq_batch_timing(trioseq_batch_t bt, float ms[2]) {
     return cuda_status(cudaGetLastError());
   ms[0] = a;
   ms[1] = b;
+  return TRIOSEQ_OK;
+}
+
+trioseq_status trioseq_plan_autotune(trioseq_plan_t plan, const trioseq_triplet* sample, size_t n,
+                                     uint32_t mode, int32_t* tile_j, int32_t* tile_k,
+                                     int32_t* ti) {
+  if (!plan || !sample || n == 0 || mode > TRIOSEQ_WITH_TRACEBACK) return TRIOSEQ_EINVAL;
+  DeviceGuard g(plan->device);
+  static const Variant kTiles[] = {{8, 8}, {4, 8}, {4, 4}};
+  static const int kTI[] = {4, 8, 16};
+  uint32_t maxlen = 0;
+  for (size_t t = 0; t < n; t++)
+    for (int q = 0; q < 3; q++) maxlen = std::max(maxlen, sample[t].len[q]);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return cuda_status(cudaGetLastError());
+  trioseq_status result = TRIOSEQ_OK;
+  float best = 3.0e38f;
+  trioseq_plan_s::Tuned bestv{mode == TRIOSEQ_WITH_TRACEBACK ? plan->tb_variant
+                                                             : plan->score_variant,
+                              plan->TI};
+  {
+    Workspace ws;  // one workspace, grown to the largest candidate
+    plan->tuning = true;
+    for (const Variant& v : kTiles) {
+      for (int ti : kTI) {
+        plan->forced = trioseq_plan_s::Tuned{v, ti};
+        trioseq_batch_s bt;
+        trioseq_status s = build_batch(plan, sample, n, mode, &bt);
+        if (s == TRIOSEQ_ECUDA) continue;  // variant cannot be resident with this alphabet
+        if (s != TRIOSEQ_OK) {
+          result = s;
+          break;
+        }
+        bt.ws = &ws;
+        if ((s = upload(&bt, nullptr, false)) != TRIOSEQ_OK ||
+            (s = run(&bt, nullptr)) != TRIOSEQ_OK ||
+            (s = fetch(&bt, nullptr, nullptr)) != TRIOSEQ_OK) {
+          result = s;
+          break;
+        }
+        float ms = 0.f;
+        cudaEventRecord(e0, nullptr);
+        for (int rep = 0; rep < 2 && s == TRIOSEQ_OK; rep++) s = run(&bt, nullptr);
+        cudaEventRecord(e1, nullptr);
+        if (s == TRIOSEQ_OK) s = fetch(&bt, nullptr, nullptr);
+        if (s != TRIOSEQ_OK || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+          result = s != TRIOSEQ_OK ? s : cuda_status(cudaGetLastError());
+          break;
+        }
+        if (ms < best) {
+          best = ms;
+          bestv = trioseq_plan_s::Tuned{v, ti};
+        }
+      }
+      if (result != TRIOSEQ_OK) break;
+    }
+    plan->tuning = false;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (result != TRIOSEQ_OK) return result;
+  plan->tuned[tune_key(mode, n, maxlen)] = bestv;
+  if (tile_j) *tile_j = bestv.var.nj;
+  if (tile_k) *tile_k = bestv.var.nk;
+  if (ti) *ti = bestv.TI;
   return TRIOSEQ_OK;
 }
 

@@ -209,3 +209,29 @@ def test_config3_protein_4000_properties(prot_plan):
         check_batch(plan, sc, w2.triplets, traceback=False)
     finally:
         B.trioseq_plan_destroy(plan)
+
+
+def test_autotune_picks_a_variant_and_keeps_results(dna_plan):
+    w = synth.config2(seed=88, n=24, lo=40, hi=160)
+    strs = [strs_ for strs_ in ([synth.to_str(s, DNA.alphabet) for s in t] for t in w.triplets)]
+    plan = _plan(DNA)
+    try:
+        before = B.trioseq_align_batch(plan, strs).tolist()
+        choice = B.trioseq_plan_autotune(plan, strs, B.SCORE_ONLY)
+        assert choice["tile"] in [(8, 8), (4, 8), (4, 4)] and choice["ti"] in (4, 8, 16)
+        bt = B.trioseq_batch_create(plan, strs)
+        try:
+            assert B.trioseq_batch_info(bt)["tile"] == choice["tile"]  # the cached choice is used
+        finally:
+            B.trioseq_batch_destroy(bt)
+        assert B.trioseq_align_batch(plan, strs).tolist() == before
+        assert before == oracle.align_many(w.triplets, DNA.sub, DNA.gap).tolist()
+        choice_tb = B.trioseq_plan_autotune(plan, strs[:4], B.WITH_TRACEBACK)
+        assert choice_tb["tile"] in [(8, 8), (4, 8), (4, 4)]
+        got = B.trioseq_align_batch(plan, strs[:4], B.WITH_TRACEBACK)
+        for i in range(4):
+            want, rows = oracle.align(*w.triplets[i], DNA.sub, DNA.gap, traceback=True)
+            assert int(got[i]) == want
+            assert B.trioseq_traceback(plan, i) == oracle_rows_str(rows, DNA)
+    finally:
+        B.trioseq_plan_destroy(plan)
