@@ -220,6 +220,16 @@ def run_reference(args, rank: int):
 
 
 # ------------------------------------------------------------------------------------------
+def max_over_ranks(x: float, dist, device: str) -> float:
+    """Slowest rank's value (every rank runs its own replica; no data-path collective)."""
+    if not dist:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def time_batch(B, torch, bt, steps: int, warmup: int, stream, flush, n):
     """Run a device-resident batch; returns (per-step event ms, per-step kernel ms, scores)."""
     B.trioseq_batch_profile(bt, True)
@@ -450,11 +460,7 @@ def main():
         dist.barrier()
     clocks = sampler.summary(t0, t1)
 
-    total_ms = sum(step_ms)
-    if dist:
-        tt = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = max_over_ranks(sum(step_ms), dist, "cuda")
     ms_step = total_ms / args.steps
     value = world * w.cells / (ms_step / 1e3) / 1e9
 
@@ -470,11 +476,7 @@ def main():
     e2e_ms = e2e_ms[2:]
     h2d, d2h = B.trioseq_plan_io_bytes(plan)
     assert s2.tolist() == scores.tolist(), "e2e and device-resident scores differ"
-    e2e_total = sum(e2e_ms)
-    if dist:
-        tt = torch.tensor([e2e_total], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_total = float(tt.item())
+    e2e_total = max_over_ranks(sum(e2e_ms), dist, "cuda")
     e2e_val = world * w.cells / (e2e_total / len(e2e_ms) / 1e3) / 1e9
 
     clock_mhz = clocks.get("sm_mhz") or 2070.0
