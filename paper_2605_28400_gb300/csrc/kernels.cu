@@ -367,46 +367,61 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
         int Q[NJ][NK];
         uint32_t cw[W];
         int raw[8];
-#pragma unroll
-        for (int pp = 0; pp < NJ; ++pp) {
-#pragma unroll
-          for (int qq = 0; qq < NK; ++qq) {
-            // Predecessors of cell (s, j0+pp, k0+qq): previous slice (P, prev halos) and this
-            // slice (Q, current halos).
-            const int Pd = (pp == 0) ? rowPrev[qq] : (qq == 0 ? colPrev[pp - 1] : P[pp - 1][qq - 1]);
-            const int Pxy = (pp == 0) ? rowPrev[qq + 1] : P[pp - 1][qq];
-            const int Pxz = (qq == 0) ? colPrev[pp] : P[pp][qq - 1];
-            const int Sx = P[pp][qq];
-            const int Myz = (pp == 0) ? rowCur[qq] : (qq == 0 ? colCur[pp - 1] : Q[pp - 1][qq - 1]);
-            const int Sy = (pp == 0) ? rowCur[qq + 1] : Q[pp - 1][qq];
-            const int Sz = (qq == 0) ? colCur[pp] : Q[pp][qq - 1];
-            if (!TB) {
-              // max{ Pd+A+B+C, Pxy+A, Pxz+B, Myz+C, Sx, Sy, Sz } (shifted frame, engine.h)
-              const int d0 = Pd + A[pp] + B[qq];
-              int u = max(Pxy + A[pp], Sx);
-              u = max(Pxz + B[qq], u);
-              const int w = max(d0, Myz);
-              const int v = max(w + Cv[pp][qq], u);
-              Q[pp][qq] = max(v, max(Sy, Sz));
-            } else {
-              // Keys: rank offsets 0,-1,-2,-3,-4,-5,-6 for moves 111,110,101,011,100,010,001.
-              const int d0 = Pd + A[pp] + B[qq];
-              const int w = max(d0, Myz - 3);
-              int u = max(Pxy + (A[pp] - 1), Sx - 4);
-              u = max(Pxz + (B[qq] - 2), u);
-              int v = max(w + Cv[pp][qq], u);
-              v = max(v, max(Sy - 5, Sz - 6));
-              const int e = pp * NK + qq;
-              raw[e & 7] = v;
-              Q[pp][qq] = v | 7;
-              if ((e & 7) == 7) {  // pack 8 ranks: bytes via PRMT, then nibbles (code_bit)
-                const uint32_t lo = __byte_perm(__byte_perm(raw[0], raw[1], 0x0040),
-                                                __byte_perm(raw[2], raw[3], 0x0040), 0x5410);
-                const uint32_t hi = __byte_perm(__byte_perm(raw[4], raw[5], 0x0040),
-                                                __byte_perm(raw[6], raw[7], 0x0040), 0x5410);
-                cw[e >> 3] = (lo & 0x07070707u) | ((hi & 0x07070707u) << 4);
-              }
+        auto cell = [&](const int pp, const int qq) {
+          // Predecessors of cell (s, j0+pp, k0+qq): previous slice (P, prev halos) and this
+          // slice (Q, current halos).
+          const int Pd = (pp == 0) ? rowPrev[qq] : (qq == 0 ? colPrev[pp - 1] : P[pp - 1][qq - 1]);
+          const int Pxy = (pp == 0) ? rowPrev[qq + 1] : P[pp - 1][qq];
+          const int Pxz = (qq == 0) ? colPrev[pp] : P[pp][qq - 1];
+          const int Sx = P[pp][qq];
+          const int Myz = (pp == 0) ? rowCur[qq] : (qq == 0 ? colCur[pp - 1] : Q[pp - 1][qq - 1]);
+          const int Sy = (pp == 0) ? rowCur[qq + 1] : Q[pp - 1][qq];
+          const int Sz = (qq == 0) ? colCur[pp] : Q[pp][qq - 1];
+          if (!TB) {
+            // max{ Pd+A+B+C, Pxy+A, Pxz+B, Myz+C, Sx, Sy, Sz } (shifted frame, engine.h)
+            const int d0 = Pd + A[pp] + B[qq];
+            int u = max(Pxy + A[pp], Sx);
+            u = max(Pxz + B[qq], u);
+            const int w = max(d0, Myz);
+            const int v = max(w + Cv[pp][qq], u);
+            Q[pp][qq] = max(v, max(Sy, Sz));
+          } else {
+            // Keys: rank offsets 0,-1,-2,-3,-4,-5,-6 for moves 111,110,101,011,100,010,001.
+            const int d0 = Pd + A[pp] + B[qq];
+            const int w = max(d0, Myz - 3);
+            int u = max(Pxy + (A[pp] - 1), Sx - 4);
+            u = max(Pxz + (B[qq] - 2), u);
+            int v = max(w + Cv[pp][qq], u);
+            v = max(v, max(Sy - 5, Sz - 6));
+            const int e = pp * NK + qq;
+            raw[e & 7] = v;
+            Q[pp][qq] = v | 7;
+            if ((e & 7) == 7) {  // pack 8 ranks: bytes via PRMT, then nibbles (code_bit)
+              const uint32_t lo = __byte_perm(__byte_perm(raw[0], raw[1], 0x0040),
+                                              __byte_perm(raw[2], raw[3], 0x0040), 0x5410);
+              const uint32_t hi = __byte_perm(__byte_perm(raw[4], raw[5], 0x0040),
+                                              __byte_perm(raw[6], raw[7], 0x0040), 0x5410);
+              cw[e >> 3] = (lo & 0x07070707u) | ((hi & 0x07070707u) << 4);
             }
+          }
+        };
+        if (!TB) {
+          // Anti-diagonal order: consecutive cells are independent, which hides the latency of
+          // each cell's dependent max chain.
+#pragma unroll
+          for (int dg = 0; dg < NJ + NK - 1; ++dg) {
+#pragma unroll
+            for (int pp = 0; pp < NJ; ++pp) {
+              const int qq = dg - pp;
+              if (qq >= 0 && qq < NK) cell(pp, qq);
+            }
+          }
+        } else {
+          // Row order, so the 8 ranks of a code word are complete together.
+#pragma unroll
+          for (int pp = 0; pp < NJ; ++pp) {
+#pragma unroll
+            for (int qq = 0; qq < NK; ++qq) cell(pp, qq);
           }
         }
 #pragma unroll
