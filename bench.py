@@ -62,6 +62,8 @@ def workloads():
         # reduced-size case of the protein recipe (profiling captures that must stay small)
         "protein1000": (lambda: synth.config3(L=1000),
                         "one related protein triplet, ancestor 1000, protein recipe, score only"),
+        "protein2000": (lambda: synth.config3(L=2000),
+                        "one related protein triplet, ancestor 2000, protein recipe, score only"),
     }
 
 

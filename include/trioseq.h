@@ -120,8 +120,12 @@ trioseq_status trioseq_batch_create(trioseq_plan_t plan, const trioseq_triplet* 
 
 /* trioseq_batch_run — enqueue one full pass of the hot path on `stream` (workspace reset, the
  * persistent wavefront kernel, and the traceback walk in traceback mode). Asynchronous: scores
- * land in device memory; read them with trioseq_batch_scores.
- * Errors: ECUDA (launch failure). */
+ * land in device memory; read them with trioseq_batch_scores. The pass is captured once into a
+ * CUDA graph (on a private stream, so `stream` may be the legacy default stream) and every run
+ * replays it with one graph launch; the graph is captured again when profiling is switched or
+ * the batch's buffers moved. Setting the environment variable TRIOSEQ_GRAPHS=0 before
+ * trioseq_plan makes the runs of that plan's batches plain launches instead.
+ * Errors: ECUDA (capture, instantiation or launch failure). */
 trioseq_status trioseq_batch_run(trioseq_batch_t batch, void* stream);
 
 /* trioseq_batch_scores — synchronise `stream`, check the device error word, and copy the n

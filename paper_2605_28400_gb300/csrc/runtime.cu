@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -129,6 +130,7 @@ struct trioseq_plan_s {
   std::unique_ptr<trioseq_batch_s> last;  // last align_batch (traceback rows kept here)
   int TI = 8;
   int64_t wait_ns = 2000000000LL;  // 2 s without progress = give up
+  bool graphs = true;              // trioseq_batch_run replays a captured CUDA graph
   Variant score_variant{8, 8};
   Variant tb_variant{4, 8};
   // Autotuner cache: (mode, single triplet or batch, bit length of the longest sequence) ->
@@ -180,9 +182,16 @@ struct trioseq_batch_s {
   bool timed = false;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
   uint64_t h2d_bytes = 0, d2h_bytes = 0;
+  // trioseq_batch_run replays one captured CUDA graph (progress reset, wavefront, walk). The key
+  // holds the buffer addresses and the profiling switch the graph was captured with.
+  cudaGraphExec_t gexec = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  std::array<const void*, 8> gkey{};
   ~trioseq_batch_s() {
     for (auto& e : ev)
       if (e) cudaEventDestroy(e);
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (capture_stream) cudaStreamDestroy(capture_stream);
   }
 };
 
@@ -394,6 +403,15 @@ trioseq_status upload(trioseq_batch_s* bt, cudaStream_t st, bool pinned) {
 }
 
 // One pass of the hot path on device-resident inputs.
+// Event record that also works inside a stream capture (there it becomes an event-record node
+// instead of a capture-internal dependency).
+cudaError_t record(cudaEvent_t ev, cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (st && cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+    return cudaEventRecordWithFlags(ev, st, cudaEventRecordExternal);
+  return cudaEventRecord(ev, st);
+}
+
 trioseq_status run(trioseq_batch_s* bt, cudaStream_t st) {
   Workspace& ws = *bt->ws;
   trioseq_plan_s* plan = bt->plan;
@@ -422,11 +440,11 @@ trioseq_status run(trioseq_batch_s* bt, cudaStream_t st) {
   p.TI = std::max(1, bt->TI);
   p.wait_ns = plan->wait_ns;
   bt->timed = false;
-  if (bt->profile && cudaEventRecord(bt->ev[0], st) != cudaSuccess)
+  if (bt->profile && record(bt->ev[0], st) != cudaSuccess)
     return cuda_status(cudaGetLastError());
   if (launch_wavefront(bt->var.nj, bt->var.nk, tb, p, bt->grid, bt->smem, st) != 0)
     return cuda_status(cudaGetLastError());
-  if (bt->profile && cudaEventRecord(bt->ev[1], st) != cudaSuccess)
+  if (bt->profile && record(bt->ev[1], st) != cudaSuccess)
     return cuda_status(cudaGetLastError());
   if (tb && !bt->tb_trips.empty()) {
     WalkParams w{};
@@ -445,9 +463,47 @@ trioseq_status run(trioseq_batch_s* bt, cudaStream_t st) {
     if (launch_walk(w, st) != 0) return cuda_status(cudaGetLastError());
   }
   if (bt->profile) {
-    if (cudaEventRecord(bt->ev[2], st) != cudaSuccess) return cuda_status(cudaGetLastError());
+    if (record(bt->ev[2], st) != cudaSuccess) return cuda_status(cudaGetLastError());
     bt->timed = true;
   }
+  return TRIOSEQ_OK;
+}
+
+// trioseq_batch_run: replay the batch's graph, capturing it first (on a private stream, so the
+// caller's stream may be the legacy default stream) when there is none yet or the workspace
+// buffers or the profiling switch changed since it was captured.
+trioseq_status run_graph(trioseq_batch_s* bt, cudaStream_t st) {
+  const Workspace& ws = *bt->ws;
+  const std::array<const void*, 8> key{ws.inputs.p, ws.faces.p, ws.progress.p, ws.codes.p,
+                                       ws.scores.p, ws.rows.p, ws.lens.p,
+                                       bt->profile ? (const void*)bt->ev[0] : nullptr};
+  if (!bt->gexec || key != bt->gkey) {
+    if (bt->gexec) {
+      cudaGraphExecDestroy(bt->gexec);
+      bt->gexec = nullptr;
+    }
+    cudaError_t e = cudaSuccess;
+    if (!bt->capture_stream)
+      e = cudaStreamCreateWithFlags(&bt->capture_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+      e = cudaStreamBeginCapture(bt->capture_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_status(e);
+    const trioseq_status s = run(bt, bt->capture_stream);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(bt->capture_stream, &graph);
+    if (s == TRIOSEQ_OK && e == cudaSuccess) e = cudaGraphInstantiate(&bt->gexec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (s != TRIOSEQ_OK) return s;
+    if (e != cudaSuccess) {
+      bt->gexec = nullptr;
+      return cuda_status(e);
+    }
+    bt->gkey = key;
+  }
+  bt->timed = false;
+  const cudaError_t e = cudaGraphLaunch(bt->gexec, st);
+  if (e != cudaSuccess) return cuda_status(e);
+  bt->timed = bt->profile;
   return TRIOSEQ_OK;
 }
 
@@ -576,6 +632,7 @@ trioseq_status trioseq_plan(const trioseq_scoring* sc, uint32_t max_len_hint, ui
       cudaMemcpy(plan->sig_tb.p, s8.data(), s8.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
     return cuda_status(cudaGetLastError());
   plan->TI = std::max(1, env_int("TRIOSEQ_TI", 8));
+  plan->graphs = env_int("TRIOSEQ_GRAPHS", 1) != 0;
   const char* sv = std::getenv("TRIOSEQ_SCORE_TILE");
   if (sv && std::strlen(sv) >= 3) plan->score_variant = Variant{sv[0] - '0', sv[2] - '0'};
   const char* tv = std::getenv("TRIOSEQ_TB_TILE");
@@ -638,7 +695,7 @@ trioseq_status trioseq_batch_create(trioseq_plan_t plan, const trioseq_triplet* 
 trioseq_status trioseq_batch_run(trioseq_batch_t bt, void* stream) {
   if (!bt) return TRIOSEQ_EINVAL;
   DeviceGuard g(bt->plan->device);
-  return run(bt, (cudaStream_t)stream);
+  return bt->plan->graphs ? run_graph(bt, (cudaStream_t)stream) : run(bt, (cudaStream_t)stream);
 }
 
 trioseq_status trioseq_batch_scores(trioseq_batch_t bt, void* stream, int32_t* scores_out) {

@@ -235,3 +235,34 @@ def test_autotune_picks_a_variant_and_keeps_results(dna_plan):
             assert B.trioseq_traceback(plan, i) == oracle_rows_str(rows, DNA)
     finally:
         B.trioseq_plan_destroy(plan)
+
+
+def test_batch_run_graph_replay_matches_plain_launches():
+    w = synth.config2(seed=91, n=10, lo=30, hi=120)
+    strs_ = [strs(t, DNA) for t in w.triplets]
+    os.environ["TRIOSEQ_GRAPHS"] = "0"
+    try:
+        plain_plan = _plan(DNA)
+    finally:
+        os.environ.pop("TRIOSEQ_GRAPHS")
+    graph_plan = _plan(DNA)
+    want = oracle.align_many(w.triplets, DNA.sub, DNA.gap).tolist()
+    try:
+        for plan in (plain_plan, graph_plan):
+            bt = B.trioseq_batch_create(plan, strs_, B.WITH_TRACEBACK)
+            try:
+                for profile in (False, True, False):
+                    B.trioseq_batch_profile(bt, profile)
+                    for _ in range(2):
+                        B.trioseq_batch_run(bt)
+                        assert B.trioseq_batch_scores(bt, len(strs_)).tolist() == want
+                    if profile:
+                        ms = B.trioseq_batch_timing(bt)
+                        assert ms[0] > 0 and ms[1] > 0
+                _, rows = oracle.align(*w.triplets[3], DNA.sub, DNA.gap, traceback=True)
+                assert B.trioseq_batch_alignment(bt, 3) == oracle_rows_str(rows, DNA)
+            finally:
+                B.trioseq_batch_destroy(bt)
+    finally:
+        B.trioseq_plan_destroy(plain_plan)
+        B.trioseq_plan_destroy(graph_plan)
