@@ -1,8 +1,9 @@
 """TrioSeq oracle (TEST INFRASTRUCTURE ONLY).
 
-Python access to ``oracle.cpp``: a plain, slow CPU implementation of exact 3-way global alignment
+Python access to ``oracle.cpp``: a plain, slow CPU implementation of exact 3-way alignment
 (Eq. 1 with the sum-of-pairs column score and the global initialisation of Sec. II, int64
-arithmetic, first-maximal-move tie-break in Eq. 1's listing order).
+arithmetic, first-maximal-move tie-break in Eq. 1's listing order), plus the scores of the
+semi-global and local alignment types of Sec. II.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import
 this package. The product library never loads it, and it shares no code with the CUDA path.
@@ -58,6 +59,9 @@ def _load():
                                           ctypes.c_int64, ctypes.c_int, i32p, ctypes.c_int32,
                                           i64p]
         lib.oracle_align_many.restype = ctypes.c_int
+        lib.oracle_align_type.argtypes = [u8p, ctypes.c_int, u8p, ctypes.c_int, u8p, ctypes.c_int,
+                                          ctypes.c_int, i32p, ctypes.c_int32, ctypes.c_int, i64p]
+        lib.oracle_align_type.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -155,3 +159,22 @@ def align_many(triplets, sub, gap: int) -> np.ndarray:
     if rc:
         raise RuntimeError(f"oracle_align_many failed ({rc})")
     return out
+
+
+GLOBAL, SEMIGLOBAL, LOCAL = 0, 1, 2
+
+
+def align_type(s0, s1, s2, sub, gap: int, kind: int) -> int:
+    """Score of the alignment type ``kind`` of Sec. II: GLOBAL (M[a][b][c]), SEMIGLOBAL (zero
+    axes, best cell on a last slice) or LOCAL (zero axes, v = 0, best cell of the cube)."""
+    lib = _load()
+    n = [len(s0), len(s1), len(s2)]
+    a0, a1, a2 = _u8(s0), _u8(s1), _u8(s2)
+    sm, K = _sub(sub)
+    score = ctypes.c_int64(0)
+    rc = lib.oracle_align_type(_ptr(a0, ctypes.c_uint8), n[0], _ptr(a1, ctypes.c_uint8), n[1],
+                               _ptr(a2, ctypes.c_uint8), n[2], K, _ptr(sm, ctypes.c_int32),
+                               int(gap), int(kind), ctypes.byref(score))
+    if rc:
+        raise RuntimeError(f"oracle_align_type failed ({rc})")
+    return int(score.value)

@@ -1,6 +1,6 @@
 // TrioSeq oracle — TEST INFRASTRUCTURE ONLY.
 //
-// A plain, slow, obviously-correct CPU implementation of exact 3-way global alignment under
+// A plain, slow, obviously-correct CPU implementation of exact 3-way alignment under
 // sum-of-pairs scoring with a linear gap, written from the paper's definitions:
 //   * the recurrence, Eq. 1 (Sec. II): each cell M[i][j][k] is the best of its 7 predecessors
 //     plus the sum-of-pairs (SOP) score of the column that the move emits;
@@ -8,7 +8,9 @@
 //     = alpha and sigma(gap, gap) = 0;
 //   * global alignment, Sec. II "Global Alignments": M[0][0][0] = 0, v = -infinity (realised here
 //     by skipping predecessors outside the cube, which reproduces the face recurrences and the
-//     axis values 2*i*alpha), score = M[a][b][c].
+//     axis values 2*i*alpha), score = M[a][b][c];
+//   * semi-global and local alignment, Sec. II "Semi-Global Alignments" / "Local Alignments"
+//     (score only, oracle_align_type).
 // Tie-break (the paper is silent): the first maximal candidate in Eq. 1's listing order wins,
 // i.e. (1,1,1) > (1,1,0) > (1,0,1) > (0,1,1) > (1,0,0) > (0,1,0) > (0,0,1).
 //
@@ -128,6 +130,66 @@ int oracle_align(const uint8_t* s0, int a, const uint8_t* s1, int b, const uint8
     rows[2 * cap + t] = r2[L - 1 - t];
   }
   *len_out = L;
+  return 0;
+}
+
+// Score of the three alignment types of Sec. II (score only).
+//   type 0, "Global Alignments": as oracle_align.
+//   type 1, "Semi-Global Alignments": the axes are initialised to zero,
+//     M[i][0][0] = M[0][j][0] = M[0][0][k] = 0 (the origin included); every other cell follows
+//     Eq. 1 with v = -infinity; the score is the best cell on a last slice in any direction,
+//     max of M over the cells with i = a or j = b or k = c.
+//   type 2, "Local Alignments": the same zero axes, and v = 0 in Eq. 1 for every other cell
+//     (no cell is negative); the score is the best cell of the whole cube.
+// Returns 0, or -1 on bad arguments.
+int oracle_align_type(const uint8_t* s0, int a, const uint8_t* s1, int b, const uint8_t* s2,
+                      int c, int K, const int32_t* sub, int32_t gap, int type,
+                      int64_t* score_out) {
+  if (a < 0 || b < 0 || c < 0 || K <= 0 || !sub || !score_out || type < 0 || type > 2) return -1;
+  if (type == 0)
+    return oracle_align(s0, a, s1, b, s2, c, K, sub, gap, score_out, nullptr, 0, nullptr);
+  Scoring sc{K, sub, gap};
+  const int64_t C = c + 1;
+  const int64_t plane = (int64_t)(b + 1) * C;
+  std::vector<int64_t> prev(plane), cur(plane);
+  bool have_score = false;
+  int64_t score = 0;
+  for (int i = 0; i <= a; i++) {
+    for (int j = 0; j <= b; j++) {
+      for (int k = 0; k <= c; k++) {
+        const int zeros = (i == 0) + (j == 0) + (k == 0);
+        int64_t best = 0;
+        if (zeros >= 2) {
+          best = 0;  // zero-initialised axes (and origin)
+        } else {
+          bool have = false;
+          for (int m = 0; m < 7; m++) {
+            const int di = kMoves[m][0], dj = kMoves[m][1], dk = kMoves[m][2];
+            const int pi = i - di, pj = j - dj, pk = k - dk;
+            if (pi < 0 || pj < 0 || pk < 0) continue;
+            const int64_t pv = (di ? prev : cur)[(int64_t)pj * C + pk];
+            const int x = di ? (int)s0[i - 1] : -1;
+            const int y = dj ? (int)s1[j - 1] : -1;
+            const int z = dk ? (int)s2[k - 1] : -1;
+            const int64_t cand = pv + sc.sop(x, y, z);
+            if (!have || cand > best) {
+              best = cand;
+              have = true;
+            }
+          }
+          if (type == 2 && best < 0) best = 0;  // v = 0
+        }
+        cur[(int64_t)j * C + k] = best;
+        const bool counts = type == 2 || i == a || j == b || k == c;
+        if (counts && (!have_score || best > score)) {
+          score = best;
+          have_score = true;
+        }
+      }
+    }
+    std::swap(prev, cur);
+  }
+  *score_out = score;
   return 0;
 }
 
