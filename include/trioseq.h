@@ -74,13 +74,25 @@ typedef struct {
 
 enum { TRIOSEQ_SCORE_ONLY = 0, TRIOSEQ_WITH_TRACEBACK = 1 };
 
+/* Alignment types of Sec. II, given to trioseq_plan as `flags`:
+ *  GLOBAL      M[0][0][0] = 0, v = -infinity, score = M[a][b][c] ("Global Alignments").
+ *  SEMIGLOBAL  the axes are zero, M[i][0][0] = M[0][j][0] = M[0][0][k] = 0, v = -infinity; the
+ *              score is the best cell on a last slice, max of M over i = a or j = b or k = c
+ *              ("Semi-Global Alignments"). Only the axes are zero-initialised (the faces follow
+ *              Eq. 1), as the section writes it.
+ *  LOCAL       the same zero axes and v = 0 in Eq. 1 (no cell is negative); the score is the
+ *              best cell of the cube ("Local Alignments").
+ * SEMIGLOBAL and LOCAL are score-only: WITH_TRACEBACK under such a plan gives ENOTIMPL. */
+enum { TRIOSEQ_GLOBAL = 0, TRIOSEQ_SEMIGLOBAL = 1, TRIOSEQ_LOCAL = 2 };
+
 typedef struct trioseq_plan_s* trioseq_plan_t;
 
 /* trioseq_plan — validate a scoring scheme and create a plan.
  * The plan owns the device workspace (grown on demand), the kernel-variant choice and the
  * autotuner cache for the current CUDA device. `max_len_hint` pre-sizes nothing mandatory
- * (0 = no hint). `flags` is reserved and must be 0.
- * Errors: EINVAL (null, bad alphabet, asymmetric sub, gap > 0), ECUDA (no device). */
+ * (0 = no hint). `flags` is the alignment type: TRIOSEQ_GLOBAL (0), TRIOSEQ_SEMIGLOBAL or
+ * TRIOSEQ_LOCAL; every call on the plan (batches, autotuner, server) uses that type.
+ * Errors: EINVAL (null, bad alphabet, asymmetric sub, gap > 0, unknown flags), ECUDA. */
 trioseq_status trioseq_plan(const trioseq_scoring* scoring, uint32_t max_len_hint, uint32_t flags,
                             trioseq_plan_t* out);
 

@@ -15,6 +15,7 @@ from . import build as _build
 
 OK, EINVAL, ENOMEM, EAGAIN, EOVERFLOW, ETIMEOUT, ECUDA, ENOTIMPL, ESCRATCH = range(9)
 SCORE_ONLY, WITH_TRACEBACK = 0, 1
+GLOBAL, SEMIGLOBAL, LOCAL = 0, 1, 2  # alignment types of Sec. II (trioseq_plan flags)
 
 
 class TrioseqError(RuntimeError):
@@ -151,7 +152,8 @@ def _triplet_array(triplets):
     return arr, keep
 
 
-def trioseq_plan(alphabet: str, sub, gap: int):
+def trioseq_plan(alphabet: str, sub, gap: int, flags: int = 0):
+    """Plan for one scoring scheme; ``flags`` is the alignment type (GLOBAL, SEMIGLOBAL, LOCAL)."""
     lib = load()
     sub = np.ascontiguousarray(np.asarray(sub, dtype=np.int8))
     K = len(alphabet)
@@ -159,7 +161,7 @@ def trioseq_plan(alphabet: str, sub, gap: int):
         raise ValueError("substitution matrix must be K x K")
     sc = Scoring(alphabet.encode(), K, sub.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)), int(gap))
     h = ctypes.c_void_p()
-    _check(lib.trioseq_plan(ctypes.byref(sc), 0, 0, ctypes.byref(h)), "trioseq_plan")
+    _check(lib.trioseq_plan(ctypes.byref(sc), 0, int(flags), ctypes.byref(h)), "trioseq_plan")
     return h
 
 

@@ -26,6 +26,10 @@ constexpr int kWarpsPerCta = 4;
 constexpr int kRing = 4;           // face-staging ring slots per warp (power of two)
 constexpr int kAhead = 2;          // steps between loading a face piece and using it
 
+// Alignment types of Sec. II. Semi-global: zero axes, score = best cell on a last slice;
+// local: zero axes and v = 0 in Eq. 1, score = best cell. Both are score-only on the device.
+constexpr int kGlobal = 0, kSemiGlobal = 1, kLocal = 2;
+
 // Rank of each move in the tie-break (Eq. 1 listing order): rank 7 wins ties over rank 6 ...
 // rank -> (di, dj, dk):
 //   7:(1,1,1) 6:(1,1,0) 5:(1,0,1) 4:(0,1,1) 3:(1,0,0) 2:(0,1,0) 1:(0,0,1)
@@ -77,6 +81,7 @@ struct WaveParams {
   int32_t* err;        // device error word (bit 0: a bounded wait expired)
   int32_t TI;          // publish progress every TI steps
   int64_t wait_ns;     // a wait that sees no progress for this long gives up
+  int32_t g2;          // -2*alpha (>= 0): the potential shift per consumed residue
 };
 
 struct WalkParams {
@@ -93,10 +98,14 @@ struct WalkParams {
   int32_t NJ, NK;            // tile of the wavefront variant that wrote the codes
 };
 
-// Host-side launchers implemented in kernels.cu.
-int launch_wavefront(int nj, int nk, bool tb, const WaveParams& p, int grid, size_t smem,
+// Host-side launchers implemented in kernels.cu. `at` is the alignment type (kGlobal, ...);
+// semi-global and local exist for score mode (tb = false) only, and their scores are
+// accumulated with atomicMax, so the score array must hold INT_MIN-like values before launch.
+int launch_wavefront(int nj, int nk, bool tb, int at, const WaveParams& p, int grid, size_t smem,
                      void* stream);
-int wavefront_occupancy(int nj, int nk, bool tb, size_t smem, int* blocks_per_sm);
+int wavefront_occupancy(int nj, int nk, bool tb, int at, size_t smem, int* blocks_per_sm);
+// Kernel entry of a semi-global or local score-mode instantiation (kernels_variants.cu), or null.
+const void* wavefront_variant(int nj, int nk, int at);
 int launch_walk(const WalkParams& p, void* stream);
 size_t wavefront_smem_bytes(int nj, int nk, int KP);
 

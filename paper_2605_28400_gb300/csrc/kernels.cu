@@ -1,486 +1,12 @@
-// kernels.cu — sm_103a kernels of the 3-way alignment engine.
-//
-// wavefront_kernel<NJ, NK, TB>: persistent "column task" engine for Eq. 1.
-//   The (j,k) plane of each triplet is cut into column blocks of WJ x WK cells
-//   (WJ = 4*NJ, WK = 8*NK). One warp owns one block at a time and sweeps the whole i axis
-//   through it: lane (r, lc) of the 4 x 8 lane grid holds an NJ x NK register tile of the
-//   current i-slice and works on slice s = t - r - lc at step t, so each lane's j- and k-halo
-//   for slice s was produced by its upper / left neighbour lane one step earlier and arrives by
-//   warp shuffle (the anti-diagonal skew of the paper's warp kernel, Sec. IV-B, rebuilt for
-//   int32 on one warp per column block).
-//   Column blocks exchange boundary records through global memory (L2): block (J,K) reads the
-//   j-records written by (J-1,K) and the k-records written by (J,K-1) (engine.h). A producer
-//   publishes how many steps it has completed every TI steps with a release store. The
-//   consumer's edge lanes need the records of step t; every lane loads one 16-byte piece of
-//   them from L2 kAhead steps early (after lane 0 has acquired the producer's progress, bounded
-//   wait) and parks it in a small per-warp shared-memory ring one step early. All lanes then
-//   read their halo from the ring and select it against the shuffled value, so the step loop
-//   has no lane-divergent branches in steady state.
-//   Tasks come from one atomic queue in an order where every producer precedes its consumers,
-//   so the engine cannot deadlock even when not all warps are resident.
-//   TB = true additionally keeps traceback keys (8*M' + 7, engine.h) and streams one 4-bit code
-//   per cell to HBM (one record of NJ*NK/8 words per lane per step).
+// kernels.cu — sm_103a kernels of the 3-way alignment engine: the global-alignment
+// instantiations of the wavefront kernel (wavefront.cuh), the traceback walk, and the launchers.
 //
 // walk_kernel: one warp per traceback request. Lane 0 follows the stored moves back from
 //   (a, b, c) through a tube of code records along the diagonal, staged in shared memory by the
 //   whole warp in one round trip; repeated until the origin.
-#include <cuda_runtime.h>
-#include <stdint.h>
-
-#include "engine.h"
+#include "wavefront.cuh"
 
 namespace trioseq {
-
-namespace {
-
-__device__ __forceinline__ int ld_relaxed(const int* p) {
-  int v;
-  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void fence_acq_rel() {
-  asm volatile("fence.acq_rel.gpu;" ::: "memory");
-}
-
-__device__ __forceinline__ void st_release(int* p, int v) {
-  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Lane-0 wait until *flag >= need. `cached` keeps the last value seen. Polls with relaxed loads
-// and exponential back-off (light on L2 while many warps wait); the fence after the satisfying
-// load makes it an acquire. Gives up (returns false) when the flag has not moved for wait_ns.
-__device__ __noinline__ bool wait_flag(const int* flag, int need, int* cached, int64_t wait_ns) {
-  int v = ld_relaxed(flag);
-  if (v >= need) {
-    fence_acq_rel();
-    *cached = v;
-    return true;
-  }
-  int last = v;
-  unsigned ns = 32;
-  uint64_t t0 = global_ns();
-  for (;;) {
-    __nanosleep(ns);
-    if (ns < 1024) ns <<= 1;
-    v = ld_relaxed(flag);
-    if (v >= need) {
-      fence_acq_rel();
-      *cached = v;
-      return true;
-    }
-    const uint64_t now = global_ns();
-    if (v != last) {
-      last = v;
-      t0 = now;
-      ns = 32;
-    } else if ((int64_t)(now - t0) > wait_ns) {
-      *cached = v;
-      return false;
-    }
-  }
-}
-
-constexpr unsigned kFull = 0xffffffffu;
-
-}  // namespace
-
-// Resident CTAs per SM the register budget is sized for (4 warps each). Traceback variants hold
-// more live state (keys, code words) and serve single large triplets that need fewer resident
-// warps, so they get the larger budget.
-template <int NJ, int NK, bool TB>
-struct MinBlocks {
-  static constexpr int value = (NJ * NK >= 64 || (TB && NJ * NK >= 32)) ? 2
-                               : ((NJ * NK >= 32) ? 3 : 4);
-};
-
-template <int NJ, int NK>
-struct Geom {
-  static constexpr int WJ = kPR * NJ, WK = kPC * NK;
-  static constexpr int RJ = WK + 4, RK = WJ;        // record strides (ints)
-  static constexpr int PJ = WJ + 4, PK = WK + 4;    // padded profile rows
-  static constexpr int SEGJ = NK + 4;               // staged j-record segment per lane column
-  static constexpr int SLOT = kPC * SEGJ + WJ;      // ints per ring slot
-  static constexpr int CBJ = NK / 4 + 1;            // 16-byte pieces per j-segment
-  static constexpr int CBK = NJ / 4;                // 16-byte pieces per k-segment
-  static constexpr int NCOPY = kPC * CBJ + kPR * CBK;
-  static constexpr int W = NJ * NK / 8;             // code words per lane per step
-};
-
-template <int NJ, int NK, bool TB>
-__global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::value)
-    wavefront_kernel(const WaveParams p) {
-  using G = Geom<NJ, NK>;
-  static_assert(NJ % 4 == 0 && NK % 4 == 0, "tile sides must be multiples of 4");
-  static_assert(G::NCOPY <= 32, "one staged piece per lane per step");
-  constexpr int WJ = G::WJ, WK = G::WK, W = G::W;
-  extern __shared__ int4 smem4[];
-  int* smem = reinterpret_cast<int*>(smem4);
-  const int KP = p.KP;
-  const int VIRT = KP - 1;
-  const int sigN = (KP * KP + 3) & ~3;
-  int* sig = smem;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int* profJ = smem + sigN + warp * (KP * (G::PJ + G::PK) + kRing * G::SLOT);
-  int* profK = profJ + KP * G::PJ;
-  int* ring = profK + KP * G::PK;
-  for (int e = threadIdx.x; e < KP * KP; e += blockDim.x) sig[e] = p.sig[e];
-  __syncthreads();
-  const int r = lane >> 3, lc = lane & 7;
-
-  // This lane's staging piece: which record, which 16 bytes, whose slice.
-  int cp_kind = 0, cp_delta = 0, cp_col = 0, cp_dst = 0;
-  if (lane < kPC * G::CBJ) {
-    const int l = lane / G::CBJ, bb = lane % G::CBJ;
-    cp_kind = 1;
-    cp_delta = l;
-    cp_col = l * NK + 4 * bb;
-    cp_dst = l * G::SEGJ + 4 * bb;
-  } else if (lane < G::NCOPY) {
-    const int q = lane - kPC * G::CBJ;
-    const int rr = q / G::CBK, bb = q % G::CBK;
-    cp_kind = 2;
-    cp_delta = rr;
-    cp_col = rr * NJ + 4 * bb;
-    cp_dst = kPC * G::SEGJ + rr * NJ + 4 * bb;
-  }
-
-  for (;;) {
-    int task = 0;
-    if (lane == 0) task = atomicAdd(p.queue, 1);
-    task = __shfl_sync(kFull, task, 0);
-    if (task >= p.ntasks) return;
-    const Task tk = p.tasks[task];
-    const TripDesc& d = p.desc[tk.trip];
-    const int a = d.len[0], b = d.len[1], c = d.len[2];
-    const int nJ = d.nJ, nK = d.nK, T = d.T;
-    const int J = tk.J, K = tk.K;
-    const int8_t* S0 = p.seq + d.s_off[0];
-    const int8_t* S1 = p.seq + d.s_off[1];
-    const int8_t* S2 = p.seq + d.s_off[2];
-    const int j0 = J * WJ + r * NJ, k0 = K * WK + lc * NK;
-    const int me = J * nK + K;
-
-    // Substitution profiles of this block: profJ[x][jl] = sigma''(x, y_(J*WJ+jl)),
-    // profK[x][kl] = sigma''(x, z_(K*WK+kl)); residue index 0 and beyond the end are VIRT.
-    __syncwarp();
-    for (int e = lane; e < KP * WJ; e += 32) {
-      const int x = e / WJ, jl = e - x * WJ, j = J * WJ + jl;
-      const int y = (j >= 1 && j <= b) ? (int)S1[j - 1] : VIRT;
-      profJ[x * G::PJ + jl] = sig[x * KP + y];
-    }
-    for (int e = lane; e < KP * WK; e += 32) {
-      const int x = e / WK, kl = e - x * WK, k = K * WK + kl;
-      const int z = (k >= 1 && k <= c) ? (int)S2[k - 1] : VIRT;
-      profK[x * G::PK + kl] = sig[x * KP + z];
-    }
-    // sigma''(y_j, z_k) is the same for every i: keep this lane's tile of it in registers.
-    int Cv[NJ][NK];
-    {
-      int yo[NJ], zv[NK];
-#pragma unroll
-      for (int pp = 0; pp < NJ; ++pp) {
-        const int j = j0 + pp;
-        yo[pp] = ((j >= 1 && j <= b) ? (int)S1[j - 1] : VIRT) * KP;
-      }
-#pragma unroll
-      for (int qq = 0; qq < NK; ++qq) {
-        const int k = k0 + qq;
-        zv[qq] = (k >= 1 && k <= c) ? (int)S2[k - 1] : VIRT;
-      }
-#pragma unroll
-      for (int pp = 0; pp < NJ; ++pp)
-#pragma unroll
-        for (int qq = 0; qq < NK; ++qq) Cv[pp][qq] = sig[yo[pp] + zv[qq]];
-    }
-    __syncwarp();
-
-    // Owner of the final cell (a, b, c).
-    const bool owns_end = (J == b / WJ) && (K == c / WK) && (r == (b % WJ) / NJ) &&
-                          (lc == (c % WK) / NK);
-    const int end_p = b % NJ, end_q = c % NK;
-
-    int P[NJ][NK];
-    int rowPrev[NK + 1], colPrev[NJ], rowCur[NK + 1], colCur[NJ];
-#pragma unroll
-    for (int pp = 0; pp < NJ; ++pp) {
-#pragma unroll
-      for (int qq = 0; qq < NK; ++qq) P[pp][qq] = kNeg;
-      colPrev[pp] = kNeg;
-      colCur[pp] = kNeg;
-    }
-#pragma unroll
-    for (int qq = 0; qq <= NK; ++qq) {
-      rowPrev[qq] = kNeg;
-      rowCur[qq] = kNeg;
-    }
-    // M'[-1][-1][-1] = 0 feeds the origin through the (1,1,1) move (stored as 8*0+7 with keys).
-    // The halo rotation at the top of step 0 moves rowCur into rowPrev.
-    if (J == 0 && K == 0 && lane == 0) rowCur[0] = TB ? 7 : 0;
-
-    const int64_t recJ = (int64_t)(a + 1) * G::RJ, recK = (int64_t)(a + 1) * G::RK;
-    int* const faces = p.faces;
-    const int* srcJ = faces + d.oj_off + (int64_t)(me - nK) * recJ;  // producer (J-1, K)
-    const int* srcK = faces + d.ok_off + (int64_t)(me - 1) * recK;   // producer (J, K-1)
-    int* dstJ = faces + d.oj_off + (int64_t)me * recJ;
-    int* dstK = faces + d.ok_off + (int64_t)me * recK;
-    const bool has_out_j = (J + 1 < nJ), has_out_k = (K + 1 < nK);
-    const int* progJ = p.progress + d.prog_base + (me - nK);
-    const int* progK = p.progress + d.prog_base + (me - 1);
-    int* progMe = p.progress + d.prog_base + me;
-    int cachedJ = J > 0 ? 0 : 1 << 30, cachedK = K > 0 ? 0 : 1 << 30;  // warp-uniform
-    uint32_t* code_base =
-        TB ? p.codes + d.code_off + (int64_t)me * T * 32 * W + lane * W : nullptr;
-    bool ok = true;
-
-    // Face pieces of step u: each lane loads its 16-byte piece from L2 into registers at step
-    // u - kAhead (after lane 0 has seen the producers publish the steps that wrote them), parks
-    // it in ring slot u % kRing at step u - 1, and the edge lanes read the slot at step u. The
-    // load's latency is covered by a whole step of compute.
-    int4 pf = make_int4(kNeg, kNeg, kNeg, kNeg);
-    int pf_u = -1;
-    bool pf_valid = false;
-    auto fetch = [&](int u) {
-      const int needJ = min(u + kPR, T), needK = min(u + kPC, T);
-      if (cachedJ < needJ || cachedK < needK) {  // warp-uniform
-        bool okl = true;
-        int cj = cachedJ, ck = cachedK;
-        if (lane == 0) {
-          if (cj < needJ) okl = wait_flag(progJ, needJ, &cj, p.wait_ns);
-          if (okl && ck < needK) okl = wait_flag(progK, needK, &ck, p.wait_ns);
-        }
-        ok = __shfl_sync(kFull, okl, 0);
-        cachedJ = __shfl_sync(kFull, cj, 0);
-        cachedK = __shfl_sync(kFull, ck, 0);
-        __syncwarp();
-      }
-      const int sl = u - cp_delta;
-      pf_u = u;
-      pf_valid = ok && cp_kind != 0 && sl >= 0 && sl <= a && (cp_kind == 1 ? J > 0 : K > 0);
-      if (pf_valid) {
-        const int* src = (cp_kind == 1) ? srcJ + (int64_t)sl * G::RJ + cp_col
-                                        : srcK + (int64_t)sl * G::RK + cp_col;
-        pf = __ldcg(reinterpret_cast<const int4*>(src));
-      }
-    };
-    auto park = [&]() {
-      if (pf_valid)
-        *reinterpret_cast<int4*>(ring + (pf_u & (kRing - 1)) * G::SLOT + cp_dst) = pf;
-    };
-
-    fetch(0);
-    park();
-    fetch(1);
-    // Residues of S0 by slice: in block B, lane q holds the residue of slice 32*B + q. Blocks are
-    // loaded one block ahead and read by shuffle, so no global load sits on the per-step path.
-    auto xblock = [&](int base) -> int {
-      const int sl = base + lane;
-      return (sl >= 1 && sl <= a) ? (int)__ldg(S0 + sl - 1) : VIRT;
-    };
-    int xprev = VIRT, xcur = xblock(0), xnext = xblock(32);
-
-    for (int t = 0; t < T; ++t) {
-      const int s = t - r - lc;
-      park();  // piece of step t + 1
-      if (t + kAhead < T) fetch(t + kAhead);
-      if (!ok) break;
-      if ((t & 31) == 0 && t > 0) {
-        xprev = xcur;
-        xcur = xnext;
-        xnext = xblock(t + 32);
-      }
-      // this lane's slice s lies in [t - 10, t]: in the current or the previous block
-      const int xa = __shfl_sync(kFull, xcur, s & 31);
-      const int xb = __shfl_sync(kFull, xprev, s & 31);
-      const int x = (s >= (t & ~31)) ? xa : xb;
-      __syncwarp();
-      // Halo of slice s: shuffled from the neighbour lanes (their step t-1 results), or staged
-      // face records for the edge lanes.
-      {
-        const int* sl = ring + (t & (kRing - 1)) * G::SLOT;
-        const bool vrow = (J > 0) && s >= 0 && s <= a;
-        const bool vcol = (K > 0) && s >= 0 && s <= a;
-        const int* rs = sl + lc * G::SEGJ;
-        const int* cs = sl + kPC * G::SEGJ + r * NJ;
-        int er[NK + 1], ec[NJ];
-        er[0] = rs[3];
-#pragma unroll
-        for (int q4 = 0; q4 < NK / 4; ++q4) {
-          const int4 v = reinterpret_cast<const int4*>(rs + 4)[q4];
-          er[1 + 4 * q4] = v.x;
-          er[2 + 4 * q4] = v.y;
-          er[3 + 4 * q4] = v.z;
-          er[4 + 4 * q4] = v.w;
-        }
-#pragma unroll
-        for (int p4 = 0; p4 < NJ / 4; ++p4) {
-          const int4 v = reinterpret_cast<const int4*>(cs)[p4];
-          ec[4 * p4] = v.x;
-          ec[4 * p4 + 1] = v.y;
-          ec[4 * p4 + 2] = v.z;
-          ec[4 * p4 + 3] = v.w;
-        }
-        const int corner_send = colCur[NJ - 1];
-#pragma unroll
-        for (int qq = 0; qq <= NK; ++qq) {
-          const int send = qq == 0 ? corner_send : P[NJ - 1][qq - 1];
-          const int v = __shfl_up_sync(kFull, send, kPC);
-          rowPrev[qq] = rowCur[qq];
-          rowCur[qq] = (r == 0) ? (vrow ? er[qq] : kNeg) : v;
-        }
-#pragma unroll
-        for (int pp = 0; pp < NJ; ++pp) {
-          const int v = __shfl_up_sync(kFull, P[pp][NK - 1], 1);
-          colPrev[pp] = colCur[pp];
-          colCur[pp] = (lc == 0) ? (vcol ? ec[pp] : kNeg) : v;
-        }
-      }
-
-      if (s >= 0 && s <= a) {
-        int A[NJ], B[NK];
-        {
-          const int4* pa = reinterpret_cast<const int4*>(profJ + x * G::PJ + r * NJ);
-#pragma unroll
-          for (int p4 = 0; p4 < NJ / 4; ++p4) {
-            const int4 v = pa[p4];
-            A[4 * p4] = v.x;
-            A[4 * p4 + 1] = v.y;
-            A[4 * p4 + 2] = v.z;
-            A[4 * p4 + 3] = v.w;
-          }
-          const int4* pb = reinterpret_cast<const int4*>(profK + x * G::PK + lc * NK);
-#pragma unroll
-          for (int q4 = 0; q4 < NK / 4; ++q4) {
-            const int4 v = pb[q4];
-            B[4 * q4] = v.x;
-            B[4 * q4 + 1] = v.y;
-            B[4 * q4 + 2] = v.z;
-            B[4 * q4 + 3] = v.w;
-          }
-        }
-        int Q[NJ][NK];
-        uint32_t cw[W];
-        int raw[8];
-        auto cell = [&](const int pp, const int qq) {
-          // Predecessors of cell (s, j0+pp, k0+qq): previous slice (P, prev halos) and this
-          // slice (Q, current halos).
-          const int Pd = (pp == 0) ? rowPrev[qq] : (qq == 0 ? colPrev[pp - 1] : P[pp - 1][qq - 1]);
-          const int Pxy = (pp == 0) ? rowPrev[qq + 1] : P[pp - 1][qq];
-          const int Pxz = (qq == 0) ? colPrev[pp] : P[pp][qq - 1];
-          const int Sx = P[pp][qq];
-          const int Myz = (pp == 0) ? rowCur[qq] : (qq == 0 ? colCur[pp - 1] : Q[pp - 1][qq - 1]);
-          const int Sy = (pp == 0) ? rowCur[qq + 1] : Q[pp - 1][qq];
-          const int Sz = (qq == 0) ? colCur[pp] : Q[pp][qq - 1];
-          if (!TB) {
-            // max{ Pd+A+B+C, Pxy+A, Pxz+B, Myz+C, Sx, Sy, Sz } (shifted frame, engine.h)
-            const int d0 = Pd + A[pp] + B[qq];
-            int u = max(Pxy + A[pp], Sx);
-            u = max(Pxz + B[qq], u);
-            const int w = max(d0, Myz);
-            const int v = max(w + Cv[pp][qq], u);
-            Q[pp][qq] = max(v, max(Sy, Sz));
-          } else {
-            // Keys: rank offsets 0,-1,-2,-3,-4,-5,-6 for moves 111,110,101,011,100,010,001.
-            const int d0 = Pd + A[pp] + B[qq];
-            const int w = max(d0, Myz - 3);
-            int u = max(Pxy + (A[pp] - 1), Sx - 4);
-            u = max(Pxz + (B[qq] - 2), u);
-            int v = max(w + Cv[pp][qq], u);
-            v = max(v, max(Sy - 5, Sz - 6));
-            const int e = pp * NK + qq;
-            raw[e & 7] = v;
-            Q[pp][qq] = v | 7;
-            if ((e & 7) == 7) {  // pack 8 ranks: bytes via PRMT, then nibbles (code_bit)
-              const uint32_t lo = __byte_perm(__byte_perm(raw[0], raw[1], 0x0040),
-                                              __byte_perm(raw[2], raw[3], 0x0040), 0x5410);
-              const uint32_t hi = __byte_perm(__byte_perm(raw[4], raw[5], 0x0040),
-                                              __byte_perm(raw[6], raw[7], 0x0040), 0x5410);
-              cw[e >> 3] = (lo & 0x07070707u) | ((hi & 0x07070707u) << 4);
-            }
-          }
-        };
-        if (!TB) {
-          // Anti-diagonal order: consecutive cells are independent, which hides the latency of
-          // each cell's dependent max chain.
-#pragma unroll
-          for (int dg = 0; dg < NJ + NK - 1; ++dg) {
-#pragma unroll
-            for (int pp = 0; pp < NJ; ++pp) {
-              const int qq = dg - pp;
-              if (qq >= 0 && qq < NK) cell(pp, qq);
-            }
-          }
-        } else {
-          // Row order, so the 8 ranks of a code word are complete together.
-#pragma unroll
-          for (int pp = 0; pp < NJ; ++pp) {
-#pragma unroll
-            for (int qq = 0; qq < NK; ++qq) cell(pp, qq);
-          }
-        }
-#pragma unroll
-        for (int pp = 0; pp < NJ; ++pp)
-#pragma unroll
-          for (int qq = 0; qq < NK; ++qq) P[pp][qq] = Q[pp][qq];
-
-        if (TB) {
-          uint32_t* dst = code_base + (int64_t)t * 32 * W;
-          if (W % 4 == 0) {
-#pragma unroll
-            for (int w4 = 0; w4 < W / 4; ++w4)
-              reinterpret_cast<uint4*>(dst)[w4] =
-                  make_uint4(cw[4 * w4], cw[4 * w4 + 1], cw[4 * w4 + 2], cw[4 * w4 + 3]);
-          } else {
-#pragma unroll
-            for (int w2 = 0; w2 < W / 2; ++w2)
-              reinterpret_cast<uint2*>(dst)[w2] = make_uint2(cw[2 * w2], cw[2 * w2 + 1]);
-          }
-        }
-        if (r == kPR - 1 && has_out_j) {
-          int* dst = dstJ + (int64_t)s * G::RJ;
-          if (lc == 0) dst[3] = colCur[NJ - 1];  // corner for the consumer's lane (0,0)
-          int4* d4 = reinterpret_cast<int4*>(dst + 4 + lc * NK);
-#pragma unroll
-          for (int q4 = 0; q4 < NK / 4; ++q4)
-            d4[q4] = make_int4(P[NJ - 1][4 * q4], P[NJ - 1][4 * q4 + 1], P[NJ - 1][4 * q4 + 2],
-                               P[NJ - 1][4 * q4 + 3]);
-        }
-        if (lc == kPC - 1 && has_out_k) {
-          int4* d4 = reinterpret_cast<int4*>(dstK + (int64_t)s * G::RK + r * NJ);
-#pragma unroll
-          for (int p4 = 0; p4 < NJ / 4; ++p4)
-            d4[p4] = make_int4(P[4 * p4][NK - 1], P[4 * p4 + 1][NK - 1], P[4 * p4 + 2][NK - 1],
-                               P[4 * p4 + 3][NK - 1]);
-        }
-        if (owns_end && s == a) {
-          int v = 0;
-#pragma unroll
-          for (int pp = 0; pp < NJ; ++pp)
-#pragma unroll
-            for (int qq = 0; qq < NK; ++qq)
-              if (pp == end_p && qq == end_q) v = P[pp][qq];
-          p.scores[d.out_idx] = (TB ? (v >> 3) : v) + d.score_base;
-        }
-      }
-      if ((t + 1) % p.TI == 0 || t + 1 == T) {
-        __syncwarp();
-        if (lane == 0) st_release(progMe, t + 1);
-      }
-    }
-    __syncwarp();
-    if (!ok) {
-      if (lane == 0) atomicOr(p.err, 1);
-      return;
-    }
-  }
-}
-
 // ---------------------------------------------------------------------------------------------
 // Traceback walk. Optimal paths of related sequences run close to the cube's main diagonal, so
 // the warp stages a "tube" of code records along the diagonal from the current cell: for each
@@ -602,10 +128,11 @@ namespace {
 
 template <int NJ, int NK, bool TB>
 const void* kptr() {
-  return reinterpret_cast<const void*>(&wavefront_kernel<NJ, NK, TB>);
+  return reinterpret_cast<const void*>(&wavefront_kernel<NJ, NK, TB, kGlobal>);
 }
 
-const void* pick(int nj, int nk, bool tb) {
+const void* pick(int nj, int nk, bool tb, int at) {
+  if (at != kGlobal) return tb ? nullptr : wavefront_variant(nj, nk, at);
   if (nj == 8 && nk == 8) return tb ? kptr<8, 8, true>() : kptr<8, 8, false>();
   if (nj == 4 && nk == 8) return tb ? kptr<4, 8, true>() : kptr<4, 8, false>();
   if (nj == 4 && nk == 4) return tb ? kptr<4, 4, true>() : kptr<4, 4, false>();
@@ -622,8 +149,8 @@ size_t wavefront_smem_bytes(int nj, int nk, int KP) {
          sizeof(int);
 }
 
-int wavefront_occupancy(int nj, int nk, bool tb, size_t smem, int* blocks_per_sm) {
-  const void* k = pick(nj, nk, tb);
+int wavefront_occupancy(int nj, int nk, bool tb, int at, size_t smem, int* blocks_per_sm) {
+  const void* k = pick(nj, nk, tb, at);
   if (!k) return -1;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
@@ -634,9 +161,9 @@ int wavefront_occupancy(int nj, int nk, bool tb, size_t smem, int* blocks_per_sm
   return 0;
 }
 
-int launch_wavefront(int nj, int nk, bool tb, const WaveParams& p, int grid, size_t smem,
+int launch_wavefront(int nj, int nk, bool tb, int at, const WaveParams& p, int grid, size_t smem,
                      void* stream) {
-  const void* k = pick(nj, nk, tb);
+  const void* k = pick(nj, nk, tb, at);
   if (!k) return -1;
   void* args[] = {const_cast<WaveParams*>(&p)};
   const cudaError_t e = cudaLaunchKernel(k, dim3(grid), dim3(kWarpsPerCta * 32), args, smem,

@@ -200,7 +200,7 @@ extern "C" trioseq_status trioseq_align_noalloc(const trioseq_scoring* sc,
     return TRIOSEQ_ECUDA;
   }
   const size_t smem = wavefront_smem_bytes(kNoallocNJ, kNoallocNK, KP);
-  if (wavefront_occupancy(kNoallocNJ, kNoallocNK, false, smem, &bpm) != 0 || bpm <= 0)
+  if (wavefront_occupancy(kNoallocNJ, kNoallocNK, false, kGlobal, smem, &bpm) != 0 || bpm <= 0)
     return TRIOSEQ_ECUDA;
   int32_t* prog = reinterpret_cast<int32_t*>(scratch + L.off_prog);
   WaveParams p{};
@@ -217,8 +217,9 @@ extern "C" trioseq_status trioseq_align_noalloc(const trioseq_scoring* sc,
   p.scores = d_score;
   p.err = prog + L.ntasks + 32;
   p.TI = 8;
+  p.g2 = -2 * sc->gap;
   p.wait_ns = 2000000000LL;
-  if (launch_wavefront(kNoallocNJ, kNoallocNK, false, p, sms * bpm, smem, st) != 0) {
+  if (launch_wavefront(kNoallocNJ, kNoallocNK, false, kGlobal, p, sms * bpm, smem, st) != 0) {
     cudaGetLastError();
     return TRIOSEQ_ECUDA;
   }

@@ -124,6 +124,7 @@ struct trioseq_plan_s {
   int16_t lut[256];
   std::vector<int32_t> sub;
   int32_t gap = 0;
+  int atype = kGlobal;             // alignment type of Sec. II (plan flags)
   int32_t max_abs_sig2 = 0;        // max |sigma''| over the extended table
   DevBuf sig_score, sig_tb;        // KP*KP int32 device tables
   Workspace ws;                    // workspace of trioseq_align_batch
@@ -225,6 +226,7 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
   if (!trip && n) return TRIOSEQ_EINVAL;
   if (mode > TRIOSEQ_WITH_TRACEBACK) return TRIOSEQ_EINVAL;
   const bool tb = mode == TRIOSEQ_WITH_TRACEBACK;
+  if (tb && plan->atype != kGlobal) return TRIOSEQ_ENOTIMPL;  // variants are score-only
   bt->plan = plan;
   bt->n = n;
   bt->mode = mode;
@@ -280,8 +282,11 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
       pos += align_up(L, 16);
       sumlen += L;
     }
-    // |M'| <= max|sigma''| * (a+b+c); keys need 8*|M'| + 8 below 2^29.
-    if ((int64_t)plan->max_abs_sig2 * sumlen >= (1LL << 26) - 1) return TRIOSEQ_EOVERFLOW;
+    // |M'| <= max|sigma''| * (a+b+c) (and, with zero axes or v = 0, <= 2|alpha| * (a+b+c));
+    // keys need 8*|M'| + 8 below 2^29.
+    if ((int64_t)std::max(plan->max_abs_sig2, plan->atype != kGlobal ? -2 * plan->gap : 0) *
+            sumlen >= (1LL << 26) - 1)
+      return TRIOSEQ_EOVERFLOW;
     if (2LL * (int64_t)std::abs(plan->gap) * sumlen >= (1LL << 30)) return TRIOSEQ_EOVERFLOW;
     const int a = d.len[0], b = d.len[1], c = d.len[2];
     d.nJ = (b + 1 + WJ - 1) / WJ;
@@ -360,7 +365,8 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
   // launch shape
   bt->smem = wavefront_smem_bytes(NJ, NK, plan->KP);
   int bpm = 0;
-  if (wavefront_occupancy(NJ, NK, tb, bt->smem, &bpm) != 0 || bpm <= 0) return TRIOSEQ_ECUDA;
+  if (wavefront_occupancy(NJ, NK, tb, plan->atype, bt->smem, &bpm) != 0 || bpm <= 0)
+    return TRIOSEQ_ECUDA;
   const int want = env_int("TRIOSEQ_CTAS_PER_SM", bpm);
   bt->grid = plan->sms * std::max(1, std::min(bpm, want));
   return TRIOSEQ_OK;
@@ -402,7 +408,6 @@ trioseq_status upload(trioseq_batch_s* bt, cudaStream_t st, bool pinned) {
   return TRIOSEQ_OK;
 }
 
-// One pass of the hot path on device-resident inputs.
 // Event record that also works inside a stream capture (there it becomes an event-record node
 // instead of a capture-internal dependency).
 cudaError_t record(cudaEvent_t ev, cudaStream_t st) {
@@ -412,6 +417,7 @@ cudaError_t record(cudaEvent_t ev, cudaStream_t st) {
   return cudaEventRecord(ev, st);
 }
 
+// One pass of the hot path on device-resident inputs.
 trioseq_status run(trioseq_batch_s* bt, cudaStream_t st) {
   Workspace& ws = *bt->ws;
   trioseq_plan_s* plan = bt->plan;
@@ -439,10 +445,15 @@ trioseq_status run(trioseq_batch_s* bt, cudaStream_t st) {
   p.err = err;
   p.TI = std::max(1, bt->TI);
   p.wait_ns = plan->wait_ns;
+  p.g2 = -2 * plan->gap;
+  // Semi-global and local scores are maxima accumulated with atomicMax: start from 0x80808080.
+  if (plan->atype != kGlobal &&
+      (e = cudaMemsetAsync(p.scores, 0x80, bt->n * sizeof(int32_t), st)) != cudaSuccess)
+    return cuda_status(e);
   bt->timed = false;
   if (bt->profile && record(bt->ev[0], st) != cudaSuccess)
     return cuda_status(cudaGetLastError());
-  if (launch_wavefront(bt->var.nj, bt->var.nk, tb, p, bt->grid, bt->smem, st) != 0)
+  if (launch_wavefront(bt->var.nj, bt->var.nk, tb, plan->atype, p, bt->grid, bt->smem, st) != 0)
     return cuda_status(cudaGetLastError());
   if (bt->profile && record(bt->ev[1], st) != cudaSuccess)
     return cuda_status(cudaGetLastError());
@@ -585,7 +596,7 @@ trioseq_status trioseq_plan(const trioseq_scoring* sc, uint32_t max_len_hint, ui
   (void)max_len_hint;
   if (!out) return TRIOSEQ_EINVAL;
   *out = nullptr;
-  if (!sc || !sc->alphabet || !sc->sub || flags != 0) return TRIOSEQ_EINVAL;
+  if (!sc || !sc->alphabet || !sc->sub || flags > TRIOSEQ_LOCAL) return TRIOSEQ_EINVAL;
   const int K = sc->alphabet_size;
   if (K < 1 || K > kMaxAlphabet || sc->gap > 0 || sc->gap < -127) return TRIOSEQ_EINVAL;
   std::unique_ptr<trioseq_plan_s> plan(new (std::nothrow) trioseq_plan_s());
@@ -603,6 +614,7 @@ trioseq_status trioseq_plan(const trioseq_scoring* sc, uint32_t max_len_hint, ui
   plan->K = K;
   plan->KP = K + 1;
   plan->gap = sc->gap;
+  plan->atype = (int)flags;
   plan->sub.assign(sc->sub, sc->sub + K * K);
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) {
@@ -1105,7 +1117,10 @@ trioseq_status trioseq_submit(trioseq_server_t S, const trioseq_triplet* t, int3
     r.s[q].assign(t->s[q] ? t->s[q] : "", t->len[q]);
     sumlen += t->len[q];
   }
-  if ((int64_t)plan->max_abs_sig2 * sumlen >= (1LL << 26) - 1) return TRIOSEQ_EOVERFLOW;
+  if ((int64_t)std::max(plan->max_abs_sig2, plan->atype != kGlobal ? -2 * plan->gap : 0) *
+          sumlen >= (1LL << 26) - 1)
+    return TRIOSEQ_EOVERFLOW;
+  if (mode == TRIOSEQ_WITH_TRACEBACK && plan->atype != kGlobal) return TRIOSEQ_ENOTIMPL;
   r.bytes = request_bytes(plan, mode, t->len);
   {
     std::lock_guard<std::mutex> lk(S->mu);
