@@ -268,10 +268,12 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
     // Face pieces of step u: each lane loads its 16-byte piece from L2 into registers at step
     // u - kAhead (after lane 0 has seen the producers publish the steps that wrote them), parks
     // it in ring slot u % kRing at step u - 1, and the edge lanes read the slot at step u. The
-    // load's latency is covered by a whole step of compute.
+    // load's latency is covered by a whole step of compute. A piece whose slice is outside
+    // 0..a, or whose producer does not exist, is parked as -infinity: the piece of lane column
+    // l covers exactly the slice s = u - l that edge lane (0, l) (or row l, for k-pieces) works
+    // on at step u, so the edge lanes take the ring value as is.
     int4 pf = make_int4(kNeg, kNeg, kNeg, kNeg);
     int pf_u = -1;
-    bool pf_valid = false;
     auto fetch = [&](int u) {
       const int needJ = min(u + kPR, T), needK = min(u + kPC, T);
       if (cachedJ < needJ || cachedK < needK) {  // warp-uniform
@@ -288,15 +290,16 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
       }
       const int sl = u - cp_delta;
       pf_u = u;
-      pf_valid = ok && cp_kind != 0 && sl >= 0 && sl <= a && (cp_kind == 1 ? J > 0 : K > 0);
-      if (pf_valid) {
+      if (ok && cp_kind != 0 && sl >= 0 && sl <= a && (cp_kind == 1 ? J > 0 : K > 0)) {
         const int* src = (cp_kind == 1) ? srcJ + (int64_t)sl * G::RJ + cp_col
                                         : srcK + (int64_t)sl * G::RK + cp_col;
         pf = __ldcg(reinterpret_cast<const int4*>(src));
+      } else {
+        pf = make_int4(kNeg, kNeg, kNeg, kNeg);
       }
     };
     auto park = [&]() {
-      if (pf_valid)
+      if (cp_kind != 0)
         *reinterpret_cast<int4*>(ring + (pf_u & (kRing - 1)) * G::SLOT + cp_dst) = pf;
     };
 
@@ -311,6 +314,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
     };
     int xprev = VIRT, xcur = xblock(0), xnext = xblock(32);
 
+    int pub_in = p.TI;  // steps until the next progress publication
     for (int t = 0; t < T; ++t) {
       const int s = t - r - lc;
       park();  // piece of step t + 1
@@ -330,8 +334,6 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
       // face records for the edge lanes.
       {
         const int* sl = ring + (t & (kRing - 1)) * G::SLOT;
-        const bool vrow = (J > 0) && s >= 0 && s <= a;
-        const bool vcol = (K > 0) && s >= 0 && s <= a;
         const int* rs = sl + lc * G::SEGJ;
         const int* cs = sl + kPC * G::SEGJ + r * NJ;
         int er[NK + 1], ec[NJ];
@@ -358,13 +360,13 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
           const int send = qq == 0 ? corner_send : P[NJ - 1][qq - 1];
           const int v = __shfl_up_sync(kFull, send, kPC);
           rowPrev[qq] = rowCur[qq];
-          rowCur[qq] = (r == 0) ? (vrow ? er[qq] : kNeg) : v;
+          rowCur[qq] = (r == 0) ? er[qq] : v;
         }
 #pragma unroll
         for (int pp = 0; pp < NJ; ++pp) {
           const int v = __shfl_up_sync(kFull, P[pp][NK - 1], 1);
           colPrev[pp] = colCur[pp];
-          colCur[pp] = (lc == 0) ? (vcol ? ec[pp] : kNeg) : v;
+          colCur[pp] = (lc == 0) ? ec[pp] : v;
         }
         if (AT == kSemiGlobal && (J == 0 || K == 0)) {  // axis feeds (warp-uniform branch)
           if (J == 0 && r == 0) {
@@ -533,7 +535,8 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
           p.scores[d.out_idx] = (TB ? (v >> 3) : v) + d.score_base;
         }
       }
-      if ((t + 1) % p.TI == 0 || t + 1 == T) {
+      if (--pub_in == 0 || t + 1 == T) {
+        pub_in = p.TI;
         __syncwarp();
         if (lane == 0) st_release(progMe, t + 1);
       }
