@@ -114,6 +114,9 @@ struct Geom {
   static constexpr int W = NJ * NK / 8;             // code words per lane per step
 };
 
+// The cell passes read tile values that earlier cells of the same pass wrote; the front end
+// cannot see that order and may warn (#549) without cause.
+#pragma nv_diag_suppress 549
 // AT selects the alignment type of Sec. II (kGlobal, kSemiGlobal, kLocal; engine.h); the
 // semi-global and local types are built for score mode only.
 template <int NJ, int NK, bool TB, int AT>
@@ -211,22 +214,25 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
     const int end_p = b % NJ, end_q = c % NK;
 
     int P[NJ][NK];
-    int rowPrev[NK + 1], colPrev[NJ], rowCur[NK + 1], colCur[NJ];
+    // Halo rows / columns of two consecutive slices. Step t writes the halo of its slice into
+    // the pair that held slice s-2 and reads slice s-1 from the other; the loop runs two steps
+    // per iteration with the roles swapped, so the rotation costs no moves. B holds "slice -1"
+    // (the state before step 0).
+    int rowA[NK + 1], colA[NJ], rowB[NK + 1], colB[NJ];
 #pragma unroll
     for (int pp = 0; pp < NJ; ++pp) {
 #pragma unroll
       for (int qq = 0; qq < NK; ++qq) P[pp][qq] = kNeg;
-      colPrev[pp] = kNeg;
-      colCur[pp] = kNeg;
+      colA[pp] = kNeg;
+      colB[pp] = kNeg;
     }
 #pragma unroll
     for (int qq = 0; qq <= NK; ++qq) {
-      rowPrev[qq] = kNeg;
-      rowCur[qq] = kNeg;
+      rowA[qq] = kNeg;
+      rowB[qq] = kNeg;
     }
     // M'[-1][-1][-1] = 0 feeds the origin through the (1,1,1) move (stored as 8*0+7 with keys).
-    // The halo rotation at the top of step 0 moves rowCur into rowPrev.
-    if (J == 0 && K == 0 && lane == 0) rowCur[0] = TB ? 7 : 0;
+    if (J == 0 && K == 0 && lane == 0) rowB[0] = TB ? 7 : 0;
     // Semi-global (Sec. II): the axes are zero in the original frame, i.e. M'[i][0][0] = g2*i,
     // M'[0][j][0] = g2*j, M'[0][0][k] = g2*k with g2 = -2*alpha. They enter through the halo
     // cells that feed each axis through a move whose cost is 0 there (all involve the virtual
@@ -237,11 +243,11 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
     if (AT == kSemiGlobal && lane == 0) {
       if (J == 0) {
 #pragma unroll
-        for (int qq = 0; qq <= NK; ++qq) rowCur[qq] = g2 * max(k0 + qq - 1, 0);
+        for (int qq = 0; qq <= NK; ++qq) rowB[qq] = g2 * max(k0 + qq - 1, 0);
       }
       if (K == 0) {
 #pragma unroll
-        for (int pp = 0; pp < NJ; ++pp) colCur[pp] = g2 * (j0 + pp);
+        for (int pp = 0; pp < NJ; ++pp) colB[pp] = g2 * (j0 + pp);
       }
     }
     int best = kNeg;  // semi-global / local: best original-frame score seen by this lane
@@ -315,11 +321,14 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
     int xprev = VIRT, xcur = xblock(0), xnext = xblock(32);
 
     int pub_in = p.TI;  // steps until the next progress publication
-    for (int t = 0; t < T; ++t) {
+    // One step: the halo of slice s goes into rowCur / colCur, slice s-1 is in rowPrev /
+    // colPrev. Returns false when a bounded wait gave up.
+    auto step = [&](const int t, int (&rowCur)[NK + 1], const int (&rowPrev)[NK + 1],
+                    int (&colCur)[NJ], const int (&colPrev)[NJ]) -> bool {
       const int s = t - r - lc;
       park();  // piece of step t + 1
       if (t + kAhead < T) fetch(t + kAhead);
-      if (!ok) break;
+      if (!ok) return false;
       if ((t & 31) == 0 && t > 0) {
         xprev = xcur;
         xcur = xnext;
@@ -354,18 +363,16 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
           ec[4 * p4 + 2] = v.z;
           ec[4 * p4 + 3] = v.w;
         }
-        const int corner_send = colCur[NJ - 1];
+        const int corner_send = colPrev[NJ - 1];
 #pragma unroll
         for (int qq = 0; qq <= NK; ++qq) {
           const int send = qq == 0 ? corner_send : P[NJ - 1][qq - 1];
           const int v = __shfl_up_sync(kFull, send, kPC);
-          rowPrev[qq] = rowCur[qq];
           rowCur[qq] = (r == 0) ? er[qq] : v;
         }
 #pragma unroll
         for (int pp = 0; pp < NJ; ++pp) {
           const int v = __shfl_up_sync(kFull, P[pp][NK - 1], 1);
-          colPrev[pp] = colCur[pp];
           colCur[pp] = (lc == 0) ? ec[pp] : v;
         }
         if (AT == kSemiGlobal && (J == 0 || K == 0)) {  // axis feeds (warp-uniform branch)
@@ -405,85 +412,136 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
             B[4 * q4 + 3] = v.w;
           }
         }
-        int Q[NJ][NK];
+        // Global and semi-global score kernels: two passes (below); the local type and the
+        // traceback keys: one pass over the cells with a second tile Q.
         uint32_t cw[W];
-        int raw[8];
-        // Local (Sec. II, v = 0): M >= 0, i.e. M' >= g2*(s+j+k) = fl on the anti-diagonal pp+qq
-        // of the tile being computed; nfl = -fl converts that diagonal's best M' to M.
-        int fl = g2 * (s + j0 + k0), nfl = -fl;
-        auto cell = [&](const int pp, const int qq) {
-          // Predecessors of cell (s, j0+pp, k0+qq): previous slice (P, prev halos) and this
-          // slice (Q, current halos).
-          const int Pd = (pp == 0) ? rowPrev[qq] : (qq == 0 ? colPrev[pp - 1] : P[pp - 1][qq - 1]);
-          const int Pxy = (pp == 0) ? rowPrev[qq + 1] : P[pp - 1][qq];
-          const int Pxz = (qq == 0) ? colPrev[pp] : P[pp][qq - 1];
-          const int Sx = P[pp][qq];
-          const int Myz = (pp == 0) ? rowCur[qq] : (qq == 0 ? colCur[pp - 1] : Q[pp - 1][qq - 1]);
-          const int Sy = (pp == 0) ? rowCur[qq + 1] : Q[pp - 1][qq];
-          const int Sz = (qq == 0) ? colCur[pp] : Q[pp][qq - 1];
-          if (!TB) {
-            // max{ Pd+A+B+C, Pxy+A, Pxz+B, Myz+C, Sx, Sy, Sz } (shifted frame, engine.h)
-            const int d0 = Pd + A[pp] + B[qq];
-            int u = max(Pxy + A[pp], Sx);
-            u = max(Pxz + B[qq], u);
-            if (AT == kLocal) u = max(u, fl);  // the v = 0 candidate
-            const int w = max(d0, Myz);
-            const int v = max(w + Cv[pp][qq], u);
-            Q[pp][qq] = max(v, max(Sy, Sz));
-          } else {
-            // Keys: rank offsets 0,-1,-2,-3,-4,-5,-6 for moves 111,110,101,011,100,010,001.
-            const int d0 = Pd + A[pp] + B[qq];
-            const int w = max(d0, Myz - 3);
-            int u = max(Pxy + (A[pp] - 1), Sx - 4);
-            u = max(Pxz + (B[qq] - 2), u);
-            int v = max(w + Cv[pp][qq], u);
-            v = max(v, max(Sy - 5, Sz - 6));
-            const int e = pp * NK + qq;
-            raw[e & 7] = v;
-            Q[pp][qq] = v | 7;
-            if ((e & 7) == 7) {  // pack 8 ranks: bytes via PRMT, then nibbles (code_bit)
-              const uint32_t lo = __byte_perm(__byte_perm(raw[0], raw[1], 0x0040),
-                                              __byte_perm(raw[2], raw[3], 0x0040), 0x5410);
-              const uint32_t hi = __byte_perm(__byte_perm(raw[4], raw[5], 0x0040),
-                                              __byte_perm(raw[6], raw[7], 0x0040), 0x5410);
-              cw[e >> 3] = (lo & 0x07070707u) | ((hi & 0x07070707u) << 4);
+        if constexpr (!TB && AT != kLocal) {
+          // Two passes, both in place in P, so no second tile and no copy-back:
+          //  pass 1 (anti-diagonals in decreasing order) replaces P (slice s-1) by
+          //    E = max{ Pd+A+B+C, Pxy+A, Pxz+B, Sx }, the moves from the previous slice; a cell's
+          //    old value is last read by its own E, since the cells that read it lie on later
+          //    anti-diagonals and are done first;
+          //  pass 2 (forward order) turns E into Q = max{ E, Myz+C, Sy, Sz }, the moves within
+          //    the slice, reading Q of earlier cells.
+          // Shifted frame (engine.h). Used for the global and semi-global score kernels; the
+          // local floor and the traceback keys lengthen pass 2's dependent chain (it can only
+          // start once pass 1 reaches cell (0,0)), and there the one-pass form below is faster.
+          auto pass1 = [&](const int pp, const int qq) {
+            const int Pd =
+                (pp == 0) ? rowPrev[qq] : (qq == 0 ? colPrev[pp - 1] : P[pp - 1][qq - 1]);
+            const int Pxy = (pp == 0) ? rowPrev[qq + 1] : P[pp - 1][qq];
+            const int Pxz = (qq == 0) ? colPrev[pp] : P[pp][qq - 1];
+            const int Sx = P[pp][qq];
+            int e = max(Pd + A[pp] + B[qq] + Cv[pp][qq], Sx);
+            e = max(Pxy + A[pp], e);
+            e = max(Pxz + B[qq], e);
+            P[pp][qq] = e;
+          };
+          auto pass2 = [&](const int pp, const int qq) {
+            const int Myz =
+                (pp == 0) ? rowCur[qq] : (qq == 0 ? colCur[pp - 1] : P[pp - 1][qq - 1]);
+            const int Sy = (pp == 0) ? rowCur[qq + 1] : P[pp - 1][qq];
+            const int Sz = (qq == 0) ? colCur[pp] : P[pp][qq - 1];
+            P[pp][qq] = max(max(Myz + Cv[pp][qq], P[pp][qq]), max(Sy, Sz));
+          };
+#pragma unroll
+          for (int dg = NJ + NK - 2; dg >= 0; --dg) {
+#pragma unroll
+            for (int pp = NJ - 1; pp >= 0; --pp) {
+              const int qq = dg - pp;
+              if (qq >= 0 && qq < NK) pass1(pp, qq);
             }
           }
-        };
-        if (!TB) {
-          // Anti-diagonal order: consecutive cells are independent, which hides the latency of
-          // each cell's dependent max chain.
 #pragma unroll
           for (int dg = 0; dg < NJ + NK - 1; ++dg) {
 #pragma unroll
             for (int pp = 0; pp < NJ; ++pp) {
               const int qq = dg - pp;
-              if (qq >= 0 && qq < NK) cell(pp, qq);
-            }
-            if (AT == kLocal) {  // best M = M' - g2*(s+j+k) on this anti-diagonal
-              int mq = kNeg;
-#pragma unroll
-              for (int pp = 0; pp < NJ; ++pp) {
-                const int qq = dg - pp;
-                if (qq >= 0 && qq < NK) mq = max(mq, Q[pp][qq]);
-              }
-              best = max(mq + nfl, best);
-              fl += g2;
-              nfl -= g2;
+              if (qq >= 0 && qq < NK) pass2(pp, qq);
             }
           }
         } else {
-          // Row order, so the 8 ranks of a code word are complete together.
+          int Q[NJ][NK];
+          int raw[8];
+          // Local (Sec. II, v = 0): M >= 0, i.e. M' >= g2*(s+j+k) = fl on the anti-diagonal pp+qq
+          // of the tile being computed; nfl = -fl converts that diagonal's best M' to M.
+          int fl = g2 * (s + j0 + k0), nfl = -fl;
+          auto cell = [&](const int pp, const int qq) {
+            // Predecessors of cell (s, j0+pp, k0+qq): previous slice (P, prev halos) and this
+            // slice (Q, current halos).
+            const int Pd =
+                (pp == 0) ? rowPrev[qq] : (qq == 0 ? colPrev[pp - 1] : P[pp - 1][qq - 1]);
+            const int Pxy = (pp == 0) ? rowPrev[qq + 1] : P[pp - 1][qq];
+            const int Pxz = (qq == 0) ? colPrev[pp] : P[pp][qq - 1];
+            const int Sx = P[pp][qq];
+            const int Myz =
+                (pp == 0) ? rowCur[qq] : (qq == 0 ? colCur[pp - 1] : Q[pp - 1][qq - 1]);
+            const int Sy = (pp == 0) ? rowCur[qq + 1] : Q[pp - 1][qq];
+            const int Sz = (qq == 0) ? colCur[pp] : Q[pp][qq - 1];
+            if (!TB) {
+              // max{ Pd+A+B+C, Pxy+A, Pxz+B, Myz+C, Sx, Sy, Sz } (shifted frame, engine.h)
+              const int d0 = Pd + A[pp] + B[qq];
+              int u = max(Pxy + A[pp], Sx);
+              u = max(Pxz + B[qq], u);
+              if (AT == kLocal) u = max(u, fl);  // the v = 0 candidate
+              const int w = max(d0, Myz);
+              const int v = max(w + Cv[pp][qq], u);
+              Q[pp][qq] = max(v, max(Sy, Sz));
+            } else {
+              // Keys: rank offsets 0,-1,-2,-3,-4,-5,-6 for moves 111,110,101,011,100,010,001.
+              const int d0 = Pd + A[pp] + B[qq];
+              const int w = max(d0, Myz - 3);
+              int u = max(Pxy + (A[pp] - 1), Sx - 4);
+              u = max(Pxz + (B[qq] - 2), u);
+              int v = max(w + Cv[pp][qq], u);
+              v = max(v, max(Sy - 5, Sz - 6));
+              const int e = pp * NK + qq;
+              raw[e & 7] = v;
+              Q[pp][qq] = v | 7;
+              if ((e & 7) == 7) {  // pack 8 ranks: bytes via PRMT, then nibbles (code_bit)
+                const uint32_t lo = __byte_perm(__byte_perm(raw[0], raw[1], 0x0040),
+                                                __byte_perm(raw[2], raw[3], 0x0040), 0x5410);
+                const uint32_t hi = __byte_perm(__byte_perm(raw[4], raw[5], 0x0040),
+                                                __byte_perm(raw[6], raw[7], 0x0040), 0x5410);
+                cw[e >> 3] = (lo & 0x07070707u) | ((hi & 0x07070707u) << 4);
+              }
+            }
+          };
+          if (!TB) {
+            // Anti-diagonal order: consecutive cells are independent, which hides the latency of
+            // each cell's dependent max chain.
 #pragma unroll
-          for (int pp = 0; pp < NJ; ++pp) {
+            for (int dg = 0; dg < NJ + NK - 1; ++dg) {
 #pragma unroll
-            for (int qq = 0; qq < NK; ++qq) cell(pp, qq);
+              for (int pp = 0; pp < NJ; ++pp) {
+                const int qq = dg - pp;
+                if (qq >= 0 && qq < NK) cell(pp, qq);
+              }
+              if (AT == kLocal) {  // best M = M' - g2*(s+j+k) on this anti-diagonal
+                int mq = kNeg;
+#pragma unroll
+                for (int pp = 0; pp < NJ; ++pp) {
+                  const int qq = dg - pp;
+                  if (qq >= 0 && qq < NK) mq = max(mq, Q[pp][qq]);
+                }
+                best = max(mq + nfl, best);
+                fl += g2;
+                nfl -= g2;
+              }
+            }
+          } else {
+            // Row order, so the 8 ranks of a code word are complete together.
+#pragma unroll
+            for (int pp = 0; pp < NJ; ++pp) {
+#pragma unroll
+              for (int qq = 0; qq < NK; ++qq) cell(pp, qq);
+            }
           }
+#pragma unroll
+          for (int pp = 0; pp < NJ; ++pp)
+#pragma unroll
+            for (int qq = 0; qq < NK; ++qq) P[pp][qq] = Q[pp][qq];
         }
-#pragma unroll
-        for (int pp = 0; pp < NJ; ++pp)
-#pragma unroll
-          for (int qq = 0; qq < NK; ++qq) P[pp][qq] = Q[pp][qq];
 
         if (TB) {
           uint32_t* dst = code_base + (int64_t)t * 32 * W;
@@ -540,6 +598,11 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
         __syncwarp();
         if (lane == 0) st_release(progMe, t + 1);
       }
+      return true;
+    };
+    for (int t = 0; t < T; t += 2) {
+      if (!step(t, rowA, rowB, colA, colB)) break;
+      if (t + 1 < T && !step(t + 1, rowB, rowA, colB, colA)) break;
     }
     __syncwarp();
     if (!ok) {
