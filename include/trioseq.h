@@ -158,6 +158,15 @@ trioseq_status trioseq_batch_alignment(trioseq_batch_t batch, size_t idx, char* 
 trioseq_status trioseq_batch_info(trioseq_batch_t batch, size_t* n, uint64_t* cells,
                                   uint64_t* tasks, int32_t* tile_j, int32_t* tile_k);
 
+/* trioseq_batch_packing — *per_word = how many triplets share each register of the batch's
+ * kernel: 2 in the packed int16x2 mode, else 1. The packed mode is the integer counterpart of
+ * the paper's FP16x2 arithmetic (Sec. IV-B). A score-only global batch of two or more triplets
+ * is packed when every pair fits: the batch pairs triplets of the same column-task grid class,
+ * and each pair's grid needs max|sigma''| * (a+b+c+3) < 2^14 on its maximal lengths. Otherwise,
+ * or with TRIOSEQ_PACKED=0 set before trioseq_plan, every triplet gets its own int32 tasks.
+ * Results are identical either way. Errors: EINVAL (null). */
+trioseq_status trioseq_batch_packing(trioseq_batch_t batch, int32_t* per_word);
+
 trioseq_status trioseq_batch_destroy(trioseq_batch_t batch);
 
 /* trioseq_batch_profile — when enable != 0, each trioseq_batch_run records CUDA events on its

@@ -82,6 +82,7 @@ def load(build_if_missing: bool = True):
         "trioseq_align_noalloc": ([ctypes.POINTER(Scoring), vp, u32, vp, u32, vp, u32, vp, vp],
                                   i32),
         "trioseq_plan_autotune": ([vp, ctypes.POINTER(Triplet), sz, u32, i32p, i32p, i32p], i32),
+        "trioseq_batch_packing": ([vp, i32p], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -98,7 +99,7 @@ def exported_symbols() -> list[str]:
             "trioseq_batch_destroy", "trioseq_batch_profile", "trioseq_batch_timing",
             "trioseq_plan_io_bytes", "trioseq_server_create", "trioseq_submit", "trioseq_poll",
             "trioseq_server_destroy", "trioseq_strerror", "trioseq_align_noalloc",
-            "trioseq_plan_autotune"]
+            "trioseq_plan_autotune", "trioseq_batch_packing"]
 
 
 def trioseq_plan_autotune(plan, sample, mode: int = SCORE_ONLY) -> dict:
@@ -239,7 +240,10 @@ def trioseq_batch_info(batch) -> dict:
     _check(load().trioseq_batch_info(batch, ctypes.byref(n), ctypes.byref(cells),
                                      ctypes.byref(tasks), ctypes.byref(tj), ctypes.byref(tk)),
            "trioseq_batch_info")
-    return {"n": n.value, "cells": cells.value, "tasks": tasks.value, "tile": (tj.value, tk.value)}
+    per = ctypes.c_int32()
+    _check(load().trioseq_batch_packing(batch, ctypes.byref(per)), "trioseq_batch_packing")
+    return {"n": n.value, "cells": cells.value, "tasks": tasks.value, "tile": (tj.value, tk.value),
+            "packing": per.value}
 
 
 def trioseq_batch_destroy(batch):

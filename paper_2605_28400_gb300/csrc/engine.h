@@ -30,6 +30,13 @@ constexpr int kAhead = 2;          // steps between loading a face piece and usi
 // local: zero axes and v = 0 in Eq. 1, score = best cell. Both are score-only on the device.
 constexpr int kGlobal = 0, kSemiGlobal = 1, kLocal = 2;
 
+// Packed int16x2 mode (global score only): two triplets share a column task, one per 16-bit half
+// of every register, record word and halo. -infinity is kNeg16 in each half. A batch is packed
+// only if every cell value of both halves stays within +-(2^14 - 3*max|sigma''|), so no add wraps
+// and the sentinel never wins against a finite candidate.
+constexpr int kNeg16 = -(1 << 14);
+constexpr int kNeg16x2 = (int)0xC000C000u;  // kNeg16 in both halves
+
 // Rank of each move in the tie-break (Eq. 1 listing order): rank 7 wins ties over rank 6 ...
 // rank -> (di, dj, dk):
 //   7:(1,1,1) 6:(1,1,0) 5:(1,0,1) 4:(0,1,1) 3:(1,0,0) 2:(0,1,0) 1:(0,0,1)
@@ -55,6 +62,8 @@ struct TripDesc {
   int64_t code_off;    // uint32-word offset of its traceback codes (-1: score only)
   int64_t prog_base;   // index of task (J=0,K=0) in the progress array
   int32_t len[3];      // a, b, c
+  int32_t glen[3];     // lengths of the task grid: len, or in packed mode the pair's maxima
+  int32_t pair;        // packed mode: descriptor of the triplet in the high halves; else -1
   int32_t nJ, nK;      // column blocks along j and k
   int32_t T;           // steps per column task: a + 1 + (kPR - 1) + (kPC - 1)
   int32_t score_base;  // 2*alpha*(a+b+c)
@@ -101,12 +110,15 @@ struct WalkParams {
 // Host-side launchers implemented in kernels.cu. `at` is the alignment type (kGlobal, ...);
 // semi-global and local exist for score mode (tb = false) only, and their scores are
 // accumulated with atomicMax, so the score array must hold INT_MIN-like values before launch.
-int launch_wavefront(int nj, int nk, bool tb, int at, const WaveParams& p, int grid, size_t smem,
-                     void* stream);
-int wavefront_occupancy(int nj, int nk, bool tb, int at, size_t smem, int* blocks_per_sm);
+int launch_wavefront(int nj, int nk, bool tb, int at, bool pk, const WaveParams& p, int grid,
+                     size_t smem, void* stream);
+int wavefront_occupancy(int nj, int nk, bool tb, int at, bool pk, size_t smem,
+                        int* blocks_per_sm);
 // Kernel entry of a semi-global or local score-mode instantiation (kernels_variants.cu), or null.
 const void* wavefront_variant(int nj, int nk, int at);
+// Kernel entry of a packed int16x2 (global, score) instantiation (kernels_packed.cu), or null.
+const void* wavefront_packed(int nj, int nk);
 int launch_walk(const WalkParams& p, void* stream);
-size_t wavefront_smem_bytes(int nj, int nk, int KP);
+size_t wavefront_smem_bytes(int nj, int nk, int KP, bool pk);
 
 }  // namespace trioseq

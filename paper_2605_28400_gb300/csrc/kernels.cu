@@ -128,10 +128,11 @@ namespace {
 
 template <int NJ, int NK, bool TB>
 const void* kptr() {
-  return reinterpret_cast<const void*>(&wavefront_kernel<NJ, NK, TB, kGlobal>);
+  return reinterpret_cast<const void*>(&wavefront_kernel<NJ, NK, TB, kGlobal, false>);
 }
 
-const void* pick(int nj, int nk, bool tb, int at) {
+const void* pick(int nj, int nk, bool tb, int at, bool pk) {
+  if (pk) return (tb || at != kGlobal) ? nullptr : wavefront_packed(nj, nk);
   if (at != kGlobal) return tb ? nullptr : wavefront_variant(nj, nk, at);
   if (nj == 8 && nk == 8) return tb ? kptr<8, 8, true>() : kptr<8, 8, false>();
   if (nj == 4 && nk == 8) return tb ? kptr<4, 8, true>() : kptr<4, 8, false>();
@@ -141,16 +142,18 @@ const void* pick(int nj, int nk, bool tb, int at) {
 
 }  // namespace
 
-size_t wavefront_smem_bytes(int nj, int nk, int KP) {
+size_t wavefront_smem_bytes(int nj, int nk, int KP, bool pk) {
   const int WJ = kPR * nj, WK = kPC * nk;
   const int slot = kPC * (nk + 4) + WJ;
   const size_t sigN = (size_t)((KP * KP + 3) & ~3);
-  return (sigN + (size_t)kWarpsPerCta * (KP * ((WJ + 4) + (WK + 4)) + kRing * slot)) *
+  const size_t nprof = pk ? 2 : 1;  // packed mode: a profile set per half
+  return (sigN + (size_t)kWarpsPerCta * (nprof * KP * ((WJ + 4) + (WK + 4)) + kRing * slot)) *
          sizeof(int);
 }
 
-int wavefront_occupancy(int nj, int nk, bool tb, int at, size_t smem, int* blocks_per_sm) {
-  const void* k = pick(nj, nk, tb, at);
+int wavefront_occupancy(int nj, int nk, bool tb, int at, bool pk, size_t smem,
+                        int* blocks_per_sm) {
+  const void* k = pick(nj, nk, tb, at, pk);
   if (!k) return -1;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
@@ -161,9 +164,9 @@ int wavefront_occupancy(int nj, int nk, bool tb, int at, size_t smem, int* block
   return 0;
 }
 
-int launch_wavefront(int nj, int nk, bool tb, int at, const WaveParams& p, int grid, size_t smem,
-                     void* stream) {
-  const void* k = pick(nj, nk, tb, at);
+int launch_wavefront(int nj, int nk, bool tb, int at, bool pk, const WaveParams& p, int grid,
+                     size_t smem, void* stream) {
+  const void* k = pick(nj, nk, tb, at, pk);
   if (!k) return -1;
   void* args[] = {const_cast<WaveParams*>(&p)};
   const cudaError_t e = cudaLaunchKernel(k, dim3(grid), dim3(kWarpsPerCta * 32), args, smem,

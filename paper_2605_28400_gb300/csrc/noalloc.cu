@@ -113,6 +113,10 @@ __global__ void noalloc_setup_kernel(unsigned char* scratch, NoallocLayout L, No
     d.len[0] = a;
     d.len[1] = b;
     d.len[2] = c;
+    d.glen[0] = a;
+    d.glen[1] = b;
+    d.glen[2] = c;
+    d.pair = -1;
     d.nJ = L.nJ;
     d.nK = L.nK;
     d.T = L.T;
@@ -199,8 +203,9 @@ extern "C" trioseq_status trioseq_align_noalloc(const trioseq_scoring* sc,
     cudaGetLastError();
     return TRIOSEQ_ECUDA;
   }
-  const size_t smem = wavefront_smem_bytes(kNoallocNJ, kNoallocNK, KP);
-  if (wavefront_occupancy(kNoallocNJ, kNoallocNK, false, kGlobal, smem, &bpm) != 0 || bpm <= 0)
+  const size_t smem = wavefront_smem_bytes(kNoallocNJ, kNoallocNK, KP, false);
+  if (wavefront_occupancy(kNoallocNJ, kNoallocNK, false, kGlobal, false, smem, &bpm) != 0 ||
+      bpm <= 0)
     return TRIOSEQ_ECUDA;
   int32_t* prog = reinterpret_cast<int32_t*>(scratch + L.off_prog);
   WaveParams p{};
@@ -219,7 +224,8 @@ extern "C" trioseq_status trioseq_align_noalloc(const trioseq_scoring* sc,
   p.TI = 8;
   p.g2 = -2 * sc->gap;
   p.wait_ns = 2000000000LL;
-  if (launch_wavefront(kNoallocNJ, kNoallocNK, false, kGlobal, p, sms * bpm, smem, st) != 0) {
+  if (launch_wavefront(kNoallocNJ, kNoallocNK, false, kGlobal, false, p, sms * bpm, smem, st) !=
+      0) {
     cudaGetLastError();
     return TRIOSEQ_ECUDA;
   }

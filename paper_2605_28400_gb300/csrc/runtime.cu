@@ -25,6 +25,7 @@
 #include <new>
 #include <string>
 #include <thread>
+#include <tuple>
 #include <unordered_map>
 #include <vector>
 
@@ -132,6 +133,7 @@ struct trioseq_plan_s {
   int TI = 8;
   int64_t wait_ns = 2000000000LL;  // 2 s without progress = give up
   bool graphs = true;              // trioseq_batch_run replays a captured CUDA graph
+  bool packed16 = true;            // pair score-only global triplets in int16 halves if they fit
   Variant score_variant{8, 8};
   Variant tb_variant{4, 8};
   // Autotuner cache: (mode, single triplet or batch, bit length of the longest sequence) ->
@@ -173,6 +175,7 @@ struct trioseq_batch_s {
   int grid = 0;
   size_t smem = 0;
   int TI = 8;  // progress-publication interval of this batch's launches
+  bool packed = false;  // packed int16x2 mode: two triplets per column task
   bool uploaded = false;
   // results of the last run (host)
   std::vector<uint8_t> h_rows;
@@ -266,13 +269,14 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
   size_t pos = 0, face = 0, codes = 0, rows = 0;
   int64_t prog = 0;
   bt->cells = 0;
+  // 1. Per triplet: encode, range checks, output slots.
   for (size_t t = 0; t < n; t++) {
     TripDesc& d = bt->desc[t];
     int64_t sumlen = 0;
     for (int q = 0; q < 3; q++) {
       const uint32_t L = trip[t].len[q];
       d.s_off[q] = (int64_t)pos;
-      d.len[q] = (int32_t)L;
+      d.len[q] = d.glen[q] = (int32_t)L;
       const unsigned char* src = reinterpret_cast<const unsigned char*>(trip[t].s[q]);
       for (uint32_t e = 0; e < L; e++) {
         const int16_t code = plan->lut[src[e]];
@@ -288,7 +292,55 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
             sumlen >= (1LL << 26) - 1)
       return TRIOSEQ_EOVERFLOW;
     if (2LL * (int64_t)std::abs(plan->gap) * sumlen >= (1LL << 30)) return TRIOSEQ_EOVERFLOW;
-    const int a = d.len[0], b = d.len[1], c = d.len[2];
+    d.pair = -1;
+    d.score_base = 2 * plan->gap * (int32_t)sumlen;
+    d.out_idx = (int32_t)t;
+    d.tb_idx = -1;
+    d.code_off = -1;
+    bt->cells += (uint64_t)d.len[0] * (uint64_t)d.len[1] * (uint64_t)d.len[2];
+  }
+  // 2. Units of work: one triplet, or in packed int16x2 mode two triplets of the same column-task
+  //    grid class paired in one unit (the high halves run on the grid of their maximal lengths).
+  //    Packing needs every value of the pair's grid within the int16 margin of engine.h:
+  //    max|sigma''| * (a+b+c + 3) < 2^14 on the grid's lengths.
+  std::vector<std::pair<int32_t, int32_t>> units;  // (low-half triplet, high-half triplet or -1)
+  bt->packed = false;
+  if (!tb && plan->atype == kGlobal && plan->packed16 && n >= 2 &&
+      wavefront_packed(NJ, NK) != nullptr) {
+    std::vector<int32_t> order(n);
+    for (size_t t = 0; t < n; t++) order[t] = (int32_t)t;
+    const auto cls = [&](int32_t t) {
+      const TripDesc& d = bt->desc[t];
+      return std::make_tuple((d.len[1] + WJ) / WJ, (d.len[2] + WK) / WK, d.len[0]);
+    };
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t x, int32_t y) { return cls(x) < cls(y); });
+    bool fits = true;
+    for (size_t u = 0; u < n && fits; u += 2) {
+      const int32_t t0 = order[u], t1 = (u + 1 < n) ? order[u + 1] : order[u];
+      int64_t gsum = 0;
+      for (int q = 0; q < 3; q++)
+        gsum += std::max(bt->desc[t0].len[q], bt->desc[t1].len[q]);
+      fits = (int64_t)plan->max_abs_sig2 * (gsum + 3) < (1 << 14);
+      units.emplace_back(t0, t1);
+    }
+    if (fits) {
+      bt->packed = true;
+    } else {
+      units.clear();
+    }
+  }
+  if (!bt->packed)
+    for (size_t t = 0; t < n; t++) units.emplace_back((int32_t)t, -1);
+  // 3. Per unit: task grid, boundary records, progress flags, traceback codes and rows.
+  for (const auto& un : units) {
+    TripDesc& d = bt->desc[un.first];
+    if (un.second >= 0) {
+      const TripDesc& h = bt->desc[un.second];
+      for (int q = 0; q < 3; q++) d.glen[q] = std::max(d.len[q], h.len[q]);
+      d.pair = un.second;
+    }
+    const int a = d.glen[0], b = d.glen[1], c = d.glen[2];
     d.nJ = (b + 1 + WJ - 1) / WJ;
     d.nK = (c + 1 + WK - 1) / WK;
     d.T = a + 1 + (kPR - 1) + (kPC - 1);
@@ -301,47 +353,53 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
     face = align_up(face, 4);
     d.prog_base = prog;
     prog += (int64_t)d.nJ * d.nK;
-    d.score_base = 2 * plan->gap * (int32_t)sumlen;
-    d.out_idx = (int32_t)t;
-    d.tb_idx = -1;
-    d.code_off = -1;
+    if (un.second >= 0 && un.second != un.first) {  // the high half shares the grid
+      TripDesc& h = bt->desc[un.second];
+      for (int q = 0; q < 3; q++) h.glen[q] = d.glen[q];
+      h.nJ = d.nJ;
+      h.nK = d.nK;
+      h.T = d.T;
+      h.oj_off = d.oj_off;
+      h.ok_off = d.ok_off;
+      h.prog_base = d.prog_base;
+    }
     if (tb) {
+      const int32_t t = un.first;
       d.code_off = (int64_t)codes;
       codes += (size_t)d.nJ * d.nK * (size_t)d.T * 32 * W;
       d.tb_idx = (int32_t)bt->tb_trips.size();
       bt->tb_of[t] = d.tb_idx;
-      bt->tb_trips.push_back((int32_t)t);
+      bt->tb_trips.push_back(t);
       const int cap = std::max(1, a + b + c);
       bt->row_off.push_back((int64_t)rows);
       bt->row_cap.push_back(cap);
       rows += align_up((size_t)3 * cap, 16);
     }
-    bt->cells += (uint64_t)a * (uint64_t)b * (uint64_t)c;
   }
   bt->seq_bytes = bt->seq.size();
   bt->face_ints = std::max<size_t>(face, 4);
   bt->code_words = std::max<size_t>(codes, 4);
   bt->rows_bytes = std::max<size_t>(rows, 16);
-  // queue: (anti-diagonal, LPT rank of the triplet, J)
-  std::vector<int32_t> lpt(n);
+  // queue: (anti-diagonal, LPT rank of the unit's grid, J)
+  const size_t nu = units.size();
+  std::vector<int32_t> lpt(n, 0);
   {
-    std::vector<int32_t> order(n);
-    for (size_t t = 0; t < n; t++) order[t] = (int32_t)t;
-    std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) {
-      const auto vol = [&](int32_t t) {
-        return (double)(bt->desc[t].len[0] + 1) * (bt->desc[t].len[1] + 1) *
-               (bt->desc[t].len[2] + 1);
-      };
-      return vol(x) > vol(y);
-    });
-    for (size_t r = 0; r < n; r++) lpt[order[r]] = (int32_t)r;
+    std::vector<int32_t> order(nu);
+    for (size_t u = 0; u < nu; u++) order[u] = (int32_t)u;
+    const auto vol = [&](int32_t u) {
+      const TripDesc& d = bt->desc[units[u].first];
+      return (double)(d.glen[0] + 1) * (d.glen[1] + 1) * (d.glen[2] + 1);
+    };
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t x, int32_t y) { return vol(x) > vol(y); });
+    for (size_t r = 0; r < nu; r++) lpt[units[order[r]].first] = (int32_t)r;
   }
   bt->tasks.clear();
   bt->tasks.reserve((size_t)prog);
-  for (size_t t = 0; t < n; t++) {
-    const TripDesc& d = bt->desc[t];
+  for (const auto& un : units) {
+    const TripDesc& d = bt->desc[un.first];
     for (int J = 0; J < d.nJ; J++)
-      for (int K = 0; K < d.nK; K++) bt->tasks.push_back(Task{(int32_t)t, J, K, 0});
+      for (int K = 0; K < d.nK; K++) bt->tasks.push_back(Task{un.first, J, K, 0});
   }
   std::stable_sort(bt->tasks.begin(), bt->tasks.end(), [&](const Task& x, const Task& y) {
     const int dx = x.J + x.K, dy = y.J + y.K;
@@ -363,9 +421,9 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
   off = align_up(off + sizeof(int32_t) * std::max<size_t>(bt->row_cap.size(), 1), 256);
   bt->inputs_bytes = off;
   // launch shape
-  bt->smem = wavefront_smem_bytes(NJ, NK, plan->KP);
+  bt->smem = wavefront_smem_bytes(NJ, NK, plan->KP, bt->packed);
   int bpm = 0;
-  if (wavefront_occupancy(NJ, NK, tb, plan->atype, bt->smem, &bpm) != 0 || bpm <= 0)
+  if (wavefront_occupancy(NJ, NK, tb, plan->atype, bt->packed, bt->smem, &bpm) != 0 || bpm <= 0)
     return TRIOSEQ_ECUDA;
   const int want = env_int("TRIOSEQ_CTAS_PER_SM", bpm);
   bt->grid = plan->sms * std::max(1, std::min(bpm, want));
@@ -453,7 +511,8 @@ trioseq_status run(trioseq_batch_s* bt, cudaStream_t st) {
   bt->timed = false;
   if (bt->profile && record(bt->ev[0], st) != cudaSuccess)
     return cuda_status(cudaGetLastError());
-  if (launch_wavefront(bt->var.nj, bt->var.nk, tb, plan->atype, p, bt->grid, bt->smem, st) != 0)
+  if (launch_wavefront(bt->var.nj, bt->var.nk, tb, plan->atype, bt->packed, p, bt->grid, bt->smem,
+                       st) != 0)
     return cuda_status(cudaGetLastError());
   if (bt->profile && record(bt->ev[1], st) != cudaSuccess)
     return cuda_status(cudaGetLastError());
@@ -645,6 +704,7 @@ trioseq_status trioseq_plan(const trioseq_scoring* sc, uint32_t max_len_hint, ui
     return cuda_status(cudaGetLastError());
   plan->TI = std::max(1, env_int("TRIOSEQ_TI", 8));
   plan->graphs = env_int("TRIOSEQ_GRAPHS", 1) != 0;
+  plan->packed16 = env_int("TRIOSEQ_PACKED", 1) != 0;
   const char* sv = std::getenv("TRIOSEQ_SCORE_TILE");
   if (sv && std::strlen(sv) >= 3) plan->score_variant = Variant{sv[0] - '0', sv[2] - '0'};
   const char* tv = std::getenv("TRIOSEQ_TB_TILE");
@@ -735,6 +795,12 @@ trioseq_status trioseq_batch_info(trioseq_batch_t bt, size_t* n, uint64_t* cells
   if (tasks) *tasks = bt->tasks.size();
   if (tile_j) *tile_j = bt->var.nj;
   if (tile_k) *tile_k = bt->var.nk;
+  return TRIOSEQ_OK;
+}
+
+trioseq_status trioseq_batch_packing(trioseq_batch_t bt, int32_t* per_word) {
+  if (!bt || !per_word) return TRIOSEQ_EINVAL;
+  *per_word = bt->packed ? 2 : 1;
   return TRIOSEQ_OK;
 }
 

@@ -118,13 +118,17 @@ struct Geom {
 // cannot see that order and may warn (#549) without cause.
 #pragma nv_diag_suppress 549
 // AT selects the alignment type of Sec. II (kGlobal, kSemiGlobal, kLocal; engine.h); the
-// semi-global and local types are built for score mode only.
-template <int NJ, int NK, bool TB, int AT>
+// semi-global and local types are built for score mode only. PACK = true is the packed int16x2
+// mode (engine.h): the triplet of descriptor d in the low halves, that of d.pair in the high
+// halves, on the task grid of their maximal lengths (global type, score only).
+template <int NJ, int NK, bool TB, int AT, bool PACK>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::value)
     wavefront_kernel(const WaveParams p) {
   using G = Geom<NJ, NK>;
   static_assert(NJ % 4 == 0 && NK % 4 == 0, "tile sides must be multiples of 4");
   static_assert(AT == kGlobal || !TB, "semi-global and local types are score-only");
+  static_assert(!PACK || (!TB && AT == kGlobal), "the packed mode is global and score-only");
+  constexpr int NEG = PACK ? kNeg16x2 : kNeg;  // -infinity in every lane of a register
   static_assert(G::NCOPY <= 32, "one staged piece per lane per step");
   constexpr int WJ = G::WJ, WK = G::WK, W = G::W;
   extern __shared__ int4 smem4[];
@@ -134,9 +138,12 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
   const int sigN = (KP * KP + 3) & ~3;
   int* sig = smem;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int* profJ = smem + sigN + warp * (KP * (G::PJ + G::PK) + kRing * G::SLOT);
+  constexpr int NPROF = PACK ? 2 : 1;  // profile sets per warp (one per half)
+  int* profJ = smem + sigN + warp * (NPROF * KP * (G::PJ + G::PK) + kRing * G::SLOT);
   int* profK = profJ + KP * G::PJ;
-  int* ring = profK + KP * G::PK;
+  int* profJ1 = profK + KP * G::PK;               // packed mode: high halves
+  int* profK1 = profJ1 + KP * G::PJ;
+  int* ring = profJ + NPROF * KP * (G::PJ + G::PK);
   for (int e = threadIdx.x; e < KP * KP; e += blockDim.x) sig[e] = p.sig[e];
   __syncthreads();
   const int r = lane >> 3, lc = lane & 7;
@@ -165,12 +172,18 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
     if (task >= p.ntasks) return;
     const Task tk = p.tasks[task];
     const TripDesc& d = p.desc[tk.trip];
-    const int a = d.len[0], b = d.len[1], c = d.len[2];
+    const TripDesc& d1 = PACK ? p.desc[d.pair] : d;  // triplet of the high halves
+    const int a = d.glen[0], b = d.glen[1], c = d.glen[2];       // task grid
+    const int a0 = d.len[0], b0 = d.len[1], c0 = d.len[2];       // triplet of the low halves
+    const int a1 = d1.len[0], b1 = d1.len[1], c1 = d1.len[2];    // packed: the high halves
     const int nJ = d.nJ, nK = d.nK, T = d.T;
     const int J = tk.J, K = tk.K;
     const int8_t* S0 = p.seq + d.s_off[0];
     const int8_t* S1 = p.seq + d.s_off[1];
     const int8_t* S2 = p.seq + d.s_off[2];
+    const int8_t* T0 = p.seq + d1.s_off[0];
+    const int8_t* T1 = p.seq + d1.s_off[1];
+    const int8_t* T2 = p.seq + d1.s_off[2];
     const int j0 = J * WJ + r * NJ, k0 = K * WK + lc * NK;
     const int me = J * nK + K;
 
@@ -179,13 +192,21 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
     __syncwarp();
     for (int e = lane; e < KP * WJ; e += 32) {
       const int x = e / WJ, jl = e - x * WJ, j = J * WJ + jl;
-      const int y = (j >= 1 && j <= b) ? (int)S1[j - 1] : VIRT;
+      const int y = (j >= 1 && j <= b0) ? (int)S1[j - 1] : VIRT;
       profJ[x * G::PJ + jl] = sig[x * KP + y];
+      if (PACK) {
+        const int y1 = (j >= 1 && j <= b1) ? (int)T1[j - 1] : VIRT;
+        profJ1[x * G::PJ + jl] = sig[x * KP + y1];
+      }
     }
     for (int e = lane; e < KP * WK; e += 32) {
       const int x = e / WK, kl = e - x * WK, k = K * WK + kl;
-      const int z = (k >= 1 && k <= c) ? (int)S2[k - 1] : VIRT;
+      const int z = (k >= 1 && k <= c0) ? (int)S2[k - 1] : VIRT;
       profK[x * G::PK + kl] = sig[x * KP + z];
+      if (PACK) {
+        const int z1 = (k >= 1 && k <= c1) ? (int)T2[k - 1] : VIRT;
+        profK1[x * G::PK + kl] = sig[x * KP + z1];
+      }
     }
     // sigma''(y_j, z_k) is the same for every i: keep this lane's tile of it in registers.
     int Cv[NJ][NK];
@@ -194,24 +215,44 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
 #pragma unroll
       for (int pp = 0; pp < NJ; ++pp) {
         const int j = j0 + pp;
-        yo[pp] = ((j >= 1 && j <= b) ? (int)S1[j - 1] : VIRT) * KP;
+        yo[pp] = ((j >= 1 && j <= b0) ? (int)S1[j - 1] : VIRT) * KP;
       }
 #pragma unroll
       for (int qq = 0; qq < NK; ++qq) {
         const int k = k0 + qq;
-        zv[qq] = (k >= 1 && k <= c) ? (int)S2[k - 1] : VIRT;
+        zv[qq] = (k >= 1 && k <= c0) ? (int)S2[k - 1] : VIRT;
       }
 #pragma unroll
       for (int pp = 0; pp < NJ; ++pp)
 #pragma unroll
         for (int qq = 0; qq < NK; ++qq) Cv[pp][qq] = sig[yo[pp] + zv[qq]];
+      if (PACK) {  // high halves: sigma''(y'_j, z'_k) of the second triplet
+#pragma unroll
+        for (int pp = 0; pp < NJ; ++pp) {
+          const int j = j0 + pp;
+          yo[pp] = ((j >= 1 && j <= b1) ? (int)T1[j - 1] : VIRT) * KP;
+        }
+#pragma unroll
+        for (int qq = 0; qq < NK; ++qq) {
+          const int k = k0 + qq;
+          zv[qq] = (k >= 1 && k <= c1) ? (int)T2[k - 1] : VIRT;
+        }
+#pragma unroll
+        for (int pp = 0; pp < NJ; ++pp)
+#pragma unroll
+          for (int qq = 0; qq < NK; ++qq)
+            Cv[pp][qq] = (int)__byte_perm(Cv[pp][qq], sig[yo[pp] + zv[qq]], 0x5410);
+      }
     }
     __syncwarp();
 
-    // Owner of the final cell (a, b, c).
-    const bool owns_end = (J == b / WJ) && (K == c / WK) && (r == (b % WJ) / NJ) &&
-                          (lc == (c % WK) / NK);
-    const int end_p = b % NJ, end_q = c % NK;
+    // Owner of the final cell (a, b, c) (of each half in packed mode).
+    const bool owns_end = (J == b0 / WJ) && (K == c0 / WK) && (r == (b0 % WJ) / NJ) &&
+                          (lc == (c0 % WK) / NK);
+    const int end_p = b0 % NJ, end_q = c0 % NK;
+    const bool owns_end1 = PACK && (J == b1 / WJ) && (K == c1 / WK) &&
+                           (r == (b1 % WJ) / NJ) && (lc == (c1 % WK) / NK);
+    const int end_p1 = b1 % NJ, end_q1 = c1 % NK;
 
     int P[NJ][NK];
     // Halo rows / columns of two consecutive slices. Step t writes the halo of its slice into
@@ -222,14 +263,14 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
 #pragma unroll
     for (int pp = 0; pp < NJ; ++pp) {
 #pragma unroll
-      for (int qq = 0; qq < NK; ++qq) P[pp][qq] = kNeg;
-      colA[pp] = kNeg;
-      colB[pp] = kNeg;
+      for (int qq = 0; qq < NK; ++qq) P[pp][qq] = NEG;
+      colA[pp] = NEG;
+      colB[pp] = NEG;
     }
 #pragma unroll
     for (int qq = 0; qq <= NK; ++qq) {
-      rowA[qq] = kNeg;
-      rowB[qq] = kNeg;
+      rowA[qq] = NEG;
+      rowB[qq] = NEG;
     }
     // M'[-1][-1][-1] = 0 feeds the origin through the (1,1,1) move (stored as 8*0+7 with keys).
     if (J == 0 && K == 0 && lane == 0) rowB[0] = TB ? 7 : 0;
@@ -278,7 +319,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
     // 0..a, or whose producer does not exist, is parked as -infinity: the piece of lane column
     // l covers exactly the slice s = u - l that edge lane (0, l) (or row l, for k-pieces) works
     // on at step u, so the edge lanes take the ring value as is.
-    int4 pf = make_int4(kNeg, kNeg, kNeg, kNeg);
+    int4 pf = make_int4(NEG, NEG, NEG, NEG);
     int pf_u = -1;
     auto fetch = [&](int u) {
       const int needJ = min(u + kPR, T), needK = min(u + kPC, T);
@@ -301,7 +342,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
                                         : srcK + (int64_t)sl * G::RK + cp_col;
         pf = __ldcg(reinterpret_cast<const int4*>(src));
       } else {
-        pf = make_int4(kNeg, kNeg, kNeg, kNeg);
+        pf = make_int4(NEG, NEG, NEG, NEG);
       }
     };
     auto park = [&]() {
@@ -314,11 +355,15 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
     fetch(1);
     // Residues of S0 by slice: in block B, lane q holds the residue of slice 32*B + q. Blocks are
     // loaded one block ahead and read by shuffle, so no global load sits on the per-step path.
+    // Packed mode: the two triplets' residues in bits 0-7 and 8-15.
     auto xblock = [&](int base) -> int {
       const int sl = base + lane;
-      return (sl >= 1 && sl <= a) ? (int)__ldg(S0 + sl - 1) : VIRT;
+      const int x0 = (sl >= 1 && sl <= a0) ? (int)__ldg(S0 + sl - 1) : VIRT;
+      if (!PACK) return x0;
+      const int x1 = (sl >= 1 && sl <= a1) ? (int)__ldg(T0 + sl - 1) : VIRT;
+      return x0 | (x1 << 8);
     };
-    int xprev = VIRT, xcur = xblock(0), xnext = xblock(32);
+    int xprev = PACK ? (VIRT | (VIRT << 8)) : VIRT, xcur = xblock(0), xnext = xblock(32);
 
     int pub_in = p.TI;  // steps until the next progress publication
     // One step: the halo of slice s goes into rowCur / colCur, slice s-1 is in rowPrev /
@@ -393,7 +438,8 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
       if (s >= 0 && s <= a) {
         int A[NJ], B[NK];
         {
-          const int4* pa = reinterpret_cast<const int4*>(profJ + x * G::PJ + r * NJ);
+          const int xl = PACK ? (x & 0xff) : x;
+          const int4* pa = reinterpret_cast<const int4*>(profJ + xl * G::PJ + r * NJ);
 #pragma unroll
           for (int p4 = 0; p4 < NJ / 4; ++p4) {
             const int4 v = pa[p4];
@@ -402,7 +448,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
             A[4 * p4 + 2] = v.z;
             A[4 * p4 + 3] = v.w;
           }
-          const int4* pb = reinterpret_cast<const int4*>(profK + x * G::PK + lc * NK);
+          const int4* pb = reinterpret_cast<const int4*>(profK + xl * G::PK + lc * NK);
 #pragma unroll
           for (int q4 = 0; q4 < NK / 4; ++q4) {
             const int4 v = pb[q4];
@@ -410,6 +456,27 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
             B[4 * q4 + 1] = v.y;
             B[4 * q4 + 2] = v.z;
             B[4 * q4 + 3] = v.w;
+          }
+          if (PACK) {  // high halves from the second triplet's profiles
+            const int xh = x >> 8;
+            const int4* qa = reinterpret_cast<const int4*>(profJ1 + xh * G::PJ + r * NJ);
+#pragma unroll
+            for (int p4 = 0; p4 < NJ / 4; ++p4) {
+              const int4 v = qa[p4];
+              A[4 * p4] = (int)__byte_perm(A[4 * p4], v.x, 0x5410);
+              A[4 * p4 + 1] = (int)__byte_perm(A[4 * p4 + 1], v.y, 0x5410);
+              A[4 * p4 + 2] = (int)__byte_perm(A[4 * p4 + 2], v.z, 0x5410);
+              A[4 * p4 + 3] = (int)__byte_perm(A[4 * p4 + 3], v.w, 0x5410);
+            }
+            const int4* qb = reinterpret_cast<const int4*>(profK1 + xh * G::PK + lc * NK);
+#pragma unroll
+            for (int q4 = 0; q4 < NK / 4; ++q4) {
+              const int4 v = qb[q4];
+              B[4 * q4] = (int)__byte_perm(B[4 * q4], v.x, 0x5410);
+              B[4 * q4 + 1] = (int)__byte_perm(B[4 * q4 + 1], v.y, 0x5410);
+              B[4 * q4 + 2] = (int)__byte_perm(B[4 * q4 + 2], v.z, 0x5410);
+              B[4 * q4 + 3] = (int)__byte_perm(B[4 * q4 + 3], v.w, 0x5410);
+            }
           }
         }
         // Global and semi-global score kernels: two passes (below); the local type and the
@@ -432,17 +499,34 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
             const int Pxy = (pp == 0) ? rowPrev[qq + 1] : P[pp - 1][qq];
             const int Pxz = (qq == 0) ? colPrev[pp] : P[pp][qq - 1];
             const int Sx = P[pp][qq];
-            int e = max(Pd + A[pp] + B[qq] + Cv[pp][qq], Sx);
-            e = max(Pxy + A[pp], e);
-            e = max(Pxz + B[qq], e);
-            P[pp][qq] = e;
+            if constexpr (PACK) {
+              // Per 16-bit half: max(a + b, c). Sums from a -infinity operand are clamped at
+              // kNeg16, so nothing wraps.
+              const unsigned neg = (unsigned)kNeg16x2;
+              unsigned dd = __viaddmax_s16x2((unsigned)Pd, (unsigned)A[pp], neg);
+              dd = __viaddmax_s16x2(dd, (unsigned)B[qq], neg);
+              unsigned e = __viaddmax_s16x2((unsigned)Pxy, (unsigned)A[pp], (unsigned)Sx);
+              e = __viaddmax_s16x2((unsigned)Pxz, (unsigned)B[qq], e);
+              P[pp][qq] = (int)__viaddmax_s16x2(dd, (unsigned)Cv[pp][qq], e);
+            } else {
+              int e = max(Pd + A[pp] + B[qq] + Cv[pp][qq], Sx);
+              e = max(Pxy + A[pp], e);
+              e = max(Pxz + B[qq], e);
+              P[pp][qq] = e;
+            }
           };
           auto pass2 = [&](const int pp, const int qq) {
             const int Myz =
                 (pp == 0) ? rowCur[qq] : (qq == 0 ? colCur[pp - 1] : P[pp - 1][qq - 1]);
             const int Sy = (pp == 0) ? rowCur[qq + 1] : P[pp - 1][qq];
             const int Sz = (qq == 0) ? colCur[pp] : P[pp][qq - 1];
-            P[pp][qq] = max(max(Myz + Cv[pp][qq], P[pp][qq]), max(Sy, Sz));
+            if constexpr (PACK) {
+              const unsigned q =
+                  __viaddmax_s16x2((unsigned)Myz, (unsigned)Cv[pp][qq], (unsigned)P[pp][qq]);
+              P[pp][qq] = (int)__vimax3_s16x2(q, (unsigned)Sy, (unsigned)Sz);
+            } else {
+              P[pp][qq] = max(max(Myz + Cv[pp][qq], P[pp][qq]), max(Sy, Sz));
+            }
           };
 #pragma unroll
           for (int dg = NJ + NK - 2; dg >= 0; --dg) {
@@ -583,14 +667,24 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
               if ((edgeJ && pp == pb && qq <= qc) || (edgeK && qq == qc && pp <= pb))
                 best = max(best, P[pp][qq] - base - g2 * (pp + qq));
         }
-        if (AT == kGlobal && owns_end && s == a) {
+        if (AT == kGlobal && owns_end && s == a0) {
           int v = 0;
 #pragma unroll
           for (int pp = 0; pp < NJ; ++pp)
 #pragma unroll
             for (int qq = 0; qq < NK; ++qq)
               if (pp == end_p && qq == end_q) v = P[pp][qq];
+          if (PACK) v = (int)(short)(v & 0xffff);  // low half, sign-extended
           p.scores[d.out_idx] = (TB ? (v >> 3) : v) + d.score_base;
+        }
+        if (PACK && owns_end1 && s == a1) {
+          int v = 0;
+#pragma unroll
+          for (int pp = 0; pp < NJ; ++pp)
+#pragma unroll
+            for (int qq = 0; qq < NK; ++qq)
+              if (pp == end_p1 && qq == end_q1) v = P[pp][qq];
+          p.scores[d1.out_idx] = (v >> 16) + d1.score_base;  // high half, sign-extended
         }
       }
       if (--pub_in == 0 || t + 1 == T) {
