@@ -833,7 +833,7 @@ trioseq_status trioseq_plan_autotune(trioseq_plan_t plan, const trioseq_triplet*
   if (!plan || !sample || n == 0 || mode > TRIOSEQ_WITH_TRACEBACK) return TRIOSEQ_EINVAL;
   DeviceGuard g(plan->device);
   static const Variant kTiles[] = {{8, 8}, {4, 8}, {4, 4}};
-  static const int kTI[] = {4, 8, 16};
+  static const int kTI[] = {4, 8, 16, 32};
   uint32_t maxlen = 0;
   for (size_t t = 0; t < n; t++)
     for (int q = 0; q < 3; q++) maxlen = std::max(maxlen, sample[t].len[q]);
