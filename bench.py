@@ -64,6 +64,10 @@ def workloads():
                         "one related protein triplet, ancestor 1000, protein recipe, score only"),
         "protein2000": (lambda: synth.config3(L=2000),
                         "one related protein triplet, ancestor 2000, protein recipe, score only"),
+        # linear-space traceback: the 4-bit code cube (~256 GB) does not fit beside its records
+        "dna8000": (lambda: synth.config1(L=8000),
+                    "one related DNA triplet, ancestor 8000, config-1 recipe, score + traceback "
+                    "in slabs (linear-space traceback)"),
     }
 
 
@@ -256,21 +260,9 @@ def time_batch(B, torch, bt, steps: int, warmup: int, stream, flush, n):
     return step_ms, kern_ms, walk_ms, scores
 
 
-def serving_measurement(B, capacity_gcups: float, n_req: int = 2000, load: float = 0.7):
-    """Serving stream: mixed DNA/protein requests (20% traceback) submitted with Poisson gaps at
-    `load` x the measured batch capacity; latency = submit to the poll that returns the result.
-    A few served results are re-aligned alone and must match exactly."""
-    from paper_2605_28400_gb300 import synth
-    dna, prot, reqs = synth.config4(n=n_req)
-    plans = [B.trioseq_plan(dna.alphabet, dna.sub, dna.gap),
-             B.trioseq_plan(prot.alphabet, prot.sub, prot.gap)]
-    cells = [len(r["triplet"][0]) * len(r["triplet"][1]) * len(r["triplet"][2]) for r in reqs]
-    mean_cells = sum(cells) / len(cells)
-    rate = load * capacity_gcups * 1e9 / mean_cells  # requests per second
-    strs = [[synth.to_str(s, (prot if r["protein"] else dna).alphabet) for s in r["triplet"]]
-            for r in reqs]
-    cap = 3 * max(len(s) for st in strs for s in st) + 16
-    srv = B.trioseq_server_create(plans)
+def _serve(B, srv, reqs, strs, rate, cap):
+    """Submit `reqs` to the server with Poisson gaps at `rate` requests/s (None: all at once) and
+    poll until every result is back. Returns submit times, completion times, results, tickets."""
     t_sub, t_done, tickets, results = {}, {}, [None] * len(reqs), {}
     lock = threading.Lock()
 
@@ -278,9 +270,10 @@ def serving_measurement(B, capacity_gcups: float, n_req: int = 2000, load: float
         t0 = time.perf_counter()
         at = 0.0
         for i, r in enumerate(reqs):
-            at += r["gap"] / rate
-            while time.perf_counter() - t0 < at:
-                time.sleep(min(0.0005, max(0.0, at - (time.perf_counter() - t0))))
+            if rate is not None:
+                at += r["gap"] / rate
+                while time.perf_counter() - t0 < at:
+                    time.sleep(min(0.0005, max(0.0, at - (time.perf_counter() - t0))))
             mode = B.WITH_TRACEBACK if r["traceback"] else B.SCORE_ONLY
             while True:
                 st, tk = B.trioseq_submit(srv, strs[i], 1 if r["protein"] else 0, mode)
@@ -307,6 +300,31 @@ def serving_measurement(B, capacity_gcups: float, n_req: int = 2000, load: float
                 n_done += 1
         time.sleep(0.0002)
     th.join()
+    return t_sub, t_done, results, tickets
+
+
+def serving_measurement(B, n_req: int = 2000, load: float = 0.7, n_cal: int = 600):
+    """Serving stream: mixed DNA/protein requests (20% traceback). The server's capacity on this
+    mix is measured first with a closed-loop burst (n_cal requests submitted at once); the stream
+    then arrives with Poisson gaps at `load` x that capacity. Latency = submit to the poll that
+    returns the result. A few served results are re-aligned alone and must match exactly."""
+    from paper_2605_28400_gb300 import synth
+    dna, prot, reqs = synth.config4(n=n_req)
+    plans = [B.trioseq_plan(dna.alphabet, dna.sub, dna.gap),
+             B.trioseq_plan(prot.alphabet, prot.sub, prot.gap)]
+    cells = [len(r["triplet"][0]) * len(r["triplet"][1]) * len(r["triplet"][2]) for r in reqs]
+    mean_cells = sum(cells) / len(cells)
+    strs = [[synth.to_str(s, (prot if r["protein"] else dna).alphabet) for s in r["triplet"]]
+            for r in reqs]
+    cap = 3 * max(len(s) for st in strs for s in st) + 16
+    # capacity: a burst of the mix's first n_cal requests
+    srv = B.trioseq_server_create(plans)
+    ts, td, _, _ = _serve(B, srv, reqs[:n_cal], strs[:n_cal], None, cap)
+    B.trioseq_server_destroy(srv)
+    capacity = sum(cells[:n_cal]) / (max(td.values()) - min(ts.values())) / 1e9
+    rate = load * capacity * 1e9 / mean_cells  # requests per second
+    srv = B.trioseq_server_create(plans)
+    t_sub, t_done, results, tickets = _serve(B, srv, reqs, strs, rate, cap)
     B.trioseq_server_destroy(srv)
     lat = sorted(1e3 * (t_done[tk] - t_sub[tk]) for tk in t_done)
     span = max(t_done.values()) - min(t_sub.values())
@@ -322,7 +340,9 @@ def serving_measurement(B, capacity_gcups: float, n_req: int = 2000, load: float
             same &= rows == B.trioseq_traceback(pl, 0)
     for p in plans:
         B.trioseq_plan_destroy(p)
-    return {"requests": len(reqs), "arrival_rate_per_s": rate, "load_vs_batch_capacity": load,
+    return {"requests": len(reqs), "arrival_rate_per_s": rate,
+            "server_capacity_gcups": capacity, "capacity_burst_requests": n_cal,
+            "load_vs_server_capacity": load,
             "mean_cells_per_request": mean_cells, "p50_ms": lat[len(lat) // 2],
             "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))], "max_ms": lat[-1],
             "aggregate_gcups": sum(cells) / span / 1e9, "span_s": span,
@@ -428,8 +448,49 @@ def aux_measurements(B, torch, stream, flush, sms, clock_mhz, skip: str):
                      "unit": "TOPS (int32)" if packing == 1 else "TOPS (int16x2 lanes)",
                      "frac": ach_b / peak_b},
         "cells": w.cells}
-    out["serving_stream"] = serving_measurement(B, batched)
+    out["serving_stream"] = serving_measurement(B)
+    out["dna8000_linear_space_traceback"] = linear_space_measurement(B, torch, stream)
     return out
+
+
+def linear_space_measurement(B, torch, stream):
+    """Score + traceback of one related DNA triplet at ancestor length 8000 (5.1e11 cells). Its
+    4-bit code cube alone would take ~256 GB, so the batch runs in slabs: a forward pass keeps a
+    plane per slab boundary, then each slab is recomputed with codes from the top down while the
+    walk continues through it. Checks: the score equals the score-only run, and the aligned rows
+    with gaps removed are the inputs."""
+    make, desc = workloads()["dna8000"]
+    w = make()
+    strs = triplet_strings(w)
+    plan = B.trioseq_plan(w.scoring.alphabet, w.scoring.sub, w.scoring.gap)
+    try:
+        bt = B.trioseq_batch_create(plan, strs, B.WITH_TRACEBACK)
+        info = B.trioseq_batch_info(bt)
+        B.trioseq_batch_run(bt, stream)
+        B.trioseq_batch_scores(bt, 1, stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        reps = []
+        for _ in range(2):
+            e0.record(stream)
+            B.trioseq_batch_run(bt, stream)
+            e1.record(stream)
+            e1.synchronize()
+            reps.append(e0.elapsed_time(e1))
+        score = int(B.trioseq_batch_scores(bt, 1, stream)[0])
+        rows = B.trioseq_batch_alignment(bt, 0)
+        B.trioseq_batch_destroy(bt)
+        score_only = int(B.trioseq_align_batch(plan, strs, B.SCORE_ONLY, stream)[0])
+    finally:
+        B.trioseq_plan_destroy(plan)
+    ms = statistics.mean(reps)
+    return {"workload": f"{w.name}: {desc}", "cells": w.cells,
+            "gcups": w.cells / (ms / 1e3) / 1e9, "ms": ms,
+            "slab_slices": info["slab_slices"], "slabs": info["slabs"],
+            "code_cube_gb_if_stored_whole": w.cells * CODE_BYTES_PER_CELL / 1e9,
+            "alignment_columns": len(rows[0]), "score": score,
+            "score_equals_score_only_run": score == score_only,
+            "rows_strip_to_inputs": all(r.replace("-", "") == s for r, s in zip(rows, strs[0]))}
 
 
 def main():

@@ -167,6 +167,18 @@ trioseq_status trioseq_batch_info(trioseq_batch_t batch, size_t* n, uint64_t* ce
  * Results are identical either way. Errors: EINVAL (null). */
 trioseq_status trioseq_batch_packing(trioseq_batch_t batch, int32_t* per_word);
 
+/* trioseq_batch_slabs — slab layout of a one-triplet batch: *slices = slices per slab, *slabs =
+ * number of slabs, both 0 when the cube runs in one launch.
+ * A one-triplet, global-type batch runs in slabs when its boundary records, plus with traceback
+ * its 4-bit codes, would exceed the plan's budget at once. The budget is half the free device
+ * memory at trioseq_plan, or TRIOSEQ_SLAB_BUDGET_MB; TRIOSEQ_SLAB_SLICES forces a slab height.
+ * Each slab launch starts from the plane of stored values its predecessor left. Score mode
+ * keeps two planes. The traceback (linear-space in the cube's length) runs in two phases:
+ * a forward pass keeps one plane per slab boundary and no codes; then each slab from the top
+ * down recomputes its codes from the plane below it, and the walk continues through it.
+ * Scores and alignments are identical to the one-launch path. Errors: EINVAL (null). */
+trioseq_status trioseq_batch_slabs(trioseq_batch_t batch, int32_t* slices, int32_t* slabs);
+
 trioseq_status trioseq_batch_destroy(trioseq_batch_t batch);
 
 /* trioseq_batch_profile — when enable != 0, each trioseq_batch_run records CUDA events on its

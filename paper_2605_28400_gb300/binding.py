@@ -83,6 +83,7 @@ def load(build_if_missing: bool = True):
                                   i32),
         "trioseq_plan_autotune": ([vp, ctypes.POINTER(Triplet), sz, u32, i32p, i32p, i32p], i32),
         "trioseq_batch_packing": ([vp, i32p], i32),
+        "trioseq_batch_slabs": ([vp, i32p, i32p], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -99,7 +100,7 @@ def exported_symbols() -> list[str]:
             "trioseq_batch_destroy", "trioseq_batch_profile", "trioseq_batch_timing",
             "trioseq_plan_io_bytes", "trioseq_server_create", "trioseq_submit", "trioseq_poll",
             "trioseq_server_destroy", "trioseq_strerror", "trioseq_align_noalloc",
-            "trioseq_plan_autotune", "trioseq_batch_packing"]
+            "trioseq_plan_autotune", "trioseq_batch_packing", "trioseq_batch_slabs"]
 
 
 def trioseq_plan_autotune(plan, sample, mode: int = SCORE_ONLY) -> dict:
@@ -242,8 +243,11 @@ def trioseq_batch_info(batch) -> dict:
            "trioseq_batch_info")
     per = ctypes.c_int32()
     _check(load().trioseq_batch_packing(batch, ctypes.byref(per)), "trioseq_batch_packing")
+    sl, ns = ctypes.c_int32(), ctypes.c_int32()
+    _check(load().trioseq_batch_slabs(batch, ctypes.byref(sl), ctypes.byref(ns)),
+           "trioseq_batch_slabs")
     return {"n": n.value, "cells": cells.value, "tasks": tasks.value, "tile": (tj.value, tk.value),
-            "packing": per.value}
+            "packing": per.value, "slab_slices": sl.value, "slabs": ns.value}
 
 
 def trioseq_batch_destroy(batch):

@@ -1,7 +1,7 @@
 """Build the engine library (CUDA, sm_103a) in-tree: paper_2605_28400_gb300/_lib/libtrioseq.so.
 
-The translation units (host runtime, kernels, the semi-global/local and packed int16x2 kernel
-instantiations, the allocation-free entry) are compiled in parallel with nvcc for
+The translation units (host runtime, kernels, the semi-global/local, packed int16x2 and slab
+kernel instantiations, the allocation-free entry) are compiled in parallel with nvcc for
 sm_103a only, then linked into one shared library with the static CUDA runtime. No torch
 extension machinery is involved; the Python side loads the library with ctypes.
 """
@@ -19,7 +19,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libtrioseq.so")
-SOURCES = ["runtime.cu", "kernels.cu", "kernels_variants.cu", "kernels_packed.cu", "noalloc.cu"]
+SOURCES = ["runtime.cu", "kernels.cu", "kernels_variants.cu", "kernels_packed.cu",
+           "kernels_slab.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 _lock = threading.Lock()
 

@@ -91,6 +91,13 @@ struct WaveParams {
   int32_t TI;          // publish progress every TI steps
   int64_t wait_ns;     // a wait that sees no progress for this long gives up
   int32_t g2;          // -2*alpha (>= 0): the potential shift per consumed residue
+  // Slab launches (one triplet, global type, int32): the launch covers the slices
+  // i0 .. i0 + desc.len[0] of the cube. plane_in holds the stored values of slice i0 - 1 (null:
+  // i0 = 0, the cube's own start); plane_out, if set, receives the slab's last slice. Planes
+  // span the padded task grid: (nJ*WJ) rows of (nK*WK) int32, row-major in (j, k).
+  int32_t i0;
+  const int32_t* plane_in;
+  int32_t* plane_out;
 };
 
 struct WalkParams {
@@ -105,19 +112,28 @@ struct WalkParams {
   int32_t* aln_len;          // written: alignment length (the alignment is the last L bytes)
   int32_t* err;              // bit 1: corrupt code met during a walk
   int32_t NJ, NK;            // tile of the wavefront variant that wrote the codes
+  // Slab walks (linear-space traceback): codes hold only the slices i_lo .. of a slab launch
+  // with T_slab steps per task; state (i, j, k, n per request) carries the walk across slabs.
+  // i_lo = 0, T_slab = 0 and state = null walk the whole cube from (a, b, c) in one launch.
+  int32_t i_lo, T_slab;
+  int32_t* state;
+  int32_t init_state;        // 1: start at (a, b, c) (the top slab) instead of reading state
 };
 
 // Host-side launchers implemented in kernels.cu. `at` is the alignment type (kGlobal, ...);
 // semi-global and local exist for score mode (tb = false) only, and their scores are
 // accumulated with atomicMax, so the score array must hold INT_MIN-like values before launch.
-int launch_wavefront(int nj, int nk, bool tb, int at, bool pk, const WaveParams& p, int grid,
-                     size_t smem, void* stream);
-int wavefront_occupancy(int nj, int nk, bool tb, int at, bool pk, size_t smem,
+// `slab` selects the slab-launch instantiations (global type, int32, either mode).
+int launch_wavefront(int nj, int nk, bool tb, int at, bool pk, bool slab, const WaveParams& p,
+                     int grid, size_t smem, void* stream);
+int wavefront_occupancy(int nj, int nk, bool tb, int at, bool pk, bool slab, size_t smem,
                         int* blocks_per_sm);
 // Kernel entry of a semi-global or local score-mode instantiation (kernels_variants.cu), or null.
 const void* wavefront_variant(int nj, int nk, int at);
 // Kernel entry of a packed int16x2 (global, score) instantiation (kernels_packed.cu), or null.
 const void* wavefront_packed(int nj, int nk);
+// Kernel entry of a slab-launch instantiation (kernels_slab.cu), or null.
+const void* wavefront_slab(int nj, int nk, bool tb);
 int launch_walk(const WalkParams& p, void* stream);
 size_t wavefront_smem_bytes(int nj, int nk, int KP, bool pk);
 

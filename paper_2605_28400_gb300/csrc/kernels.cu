@@ -19,7 +19,8 @@ constexpr int kTubePer = (kTubeRecs + 31) / 32;
 
 template <int W>
 __device__ __forceinline__ void tube_load(uint32_t* win, int i0, int j0, int k0, int lj, int lk,
-                                          const uint32_t* codes, const TripDesc& d, int lane) {
+                                          const uint32_t* codes, const TripDesc& d, int T,
+                                          int i_lo, int lane) {
   constexpr int V = (W + 3) / 4;  // 16-byte vectors per record (W = 2 uses the low half)
   uint4 v[kTubePer][V];
   bool valid[kTubePer];
@@ -30,13 +31,13 @@ __device__ __forceinline__ void tube_load(uint32_t* win, int i0, int j0, int k0,
     const int ii = i0 - sx;
     const int gr = ((j0 - sx) >> lj) + rem / kTubeC - 1;
     const int gc = ((k0 - sx) >> lk) + rem % kTubeC - 1;
-    valid[u] = e < kTubeRecs && ii >= 0 && gr >= 0 && gc >= 0 && gr < d.nJ * kPR &&
+    valid[u] = e < kTubeRecs && ii >= i_lo && gr >= 0 && gc >= 0 && gr < d.nJ * kPR &&
                gc < d.nK * kPC;
     if (valid[u]) {
       const int task = (gr / kPR) * d.nK + (gc / kPC);
       const int lr = gr % kPR, lcc = gc % kPC;
       const uint32_t* src =
-          codes + (((int64_t)task * d.T + (ii + lr + lcc)) * 32 + (lr * kPC + lcc)) * W;
+          codes + (((int64_t)task * T + (ii - i_lo + lr + lcc)) * 32 + (lr * kPC + lcc)) * W;
       if (W == 2) {
         const uint2 h = __ldcg(reinterpret_cast<const uint2*>(src));
         v[u][0] = make_uint4(h.x, h.y, 0u, 0u);
@@ -76,13 +77,20 @@ __global__ void __launch_bounds__(32) walk_kernel(const WalkParams p) {
   uint8_t* row1 = row0 + cap;
   uint8_t* row2 = row1 + cap;
   const uint32_t* codes = p.codes + d.code_off;
+  const int T = p.T_slab > 0 ? p.T_slab : d.T, i_lo = p.i_lo;
   int i = a, j = b, k = c, n = 0, bad = 0;
-  while ((i | j | k) != 0 && !bad) {
+  if (p.state && !p.init_state) {  // a linear-space traceback resumes where the slab above left it
+    i = p.state[4 * q];
+    j = p.state[4 * q + 1];
+    k = p.state[4 * q + 2];
+    n = p.state[4 * q + 3];
+  }
+  while ((i | j | k) != 0 && i >= i_lo && !bad) {
     const int i0 = i, j0 = j, k0 = k;
-    tube_load<W>(win, i0, j0, k0, lj, lk, codes, d, lane);
+    tube_load<W>(win, i0, j0, k0, lj, lk, codes, d, T, i_lo, lane);
     __syncwarp();
     if (lane == 0) {
-      while ((i | j | k) != 0) {
+      while ((i | j | k) != 0 && i >= i_lo) {
         const int sx = i0 - i;
         if (sx >= kTubeS) break;
         const int dr = (j >> lj) - ((j0 - sx) >> lj) + 1;
@@ -115,10 +123,16 @@ __global__ void __launch_bounds__(32) walk_kernel(const WalkParams p) {
     bad = __shfl_sync(kFull, bad, 0);
   }
   if (lane == 0) {
+    if (p.state) {
+      p.state[4 * q] = i;
+      p.state[4 * q + 1] = j;
+      p.state[4 * q + 2] = k;
+      p.state[4 * q + 3] = n;
+    }
     if (bad) {
       atomicOr(p.err, 2);
       p.aln_len[q] = -1;
-    } else {
+    } else if ((i | j | k) == 0) {
       p.aln_len[q] = n;
     }
   }
@@ -128,10 +142,11 @@ namespace {
 
 template <int NJ, int NK, bool TB>
 const void* kptr() {
-  return reinterpret_cast<const void*>(&wavefront_kernel<NJ, NK, TB, kGlobal, false>);
+  return reinterpret_cast<const void*>(&wavefront_kernel<NJ, NK, TB, kGlobal, false, false>);
 }
 
-const void* pick(int nj, int nk, bool tb, int at, bool pk) {
+const void* pick(int nj, int nk, bool tb, int at, bool pk, bool slab) {
+  if (slab) return (pk || at != kGlobal) ? nullptr : wavefront_slab(nj, nk, tb);
   if (pk) return (tb || at != kGlobal) ? nullptr : wavefront_packed(nj, nk);
   if (at != kGlobal) return tb ? nullptr : wavefront_variant(nj, nk, at);
   if (nj == 8 && nk == 8) return tb ? kptr<8, 8, true>() : kptr<8, 8, false>();
@@ -151,9 +166,9 @@ size_t wavefront_smem_bytes(int nj, int nk, int KP, bool pk) {
          sizeof(int);
 }
 
-int wavefront_occupancy(int nj, int nk, bool tb, int at, bool pk, size_t smem,
+int wavefront_occupancy(int nj, int nk, bool tb, int at, bool pk, bool slab, size_t smem,
                         int* blocks_per_sm) {
-  const void* k = pick(nj, nk, tb, at, pk);
+  const void* k = pick(nj, nk, tb, at, pk, slab);
   if (!k) return -1;
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
@@ -164,9 +179,9 @@ int wavefront_occupancy(int nj, int nk, bool tb, int at, bool pk, size_t smem,
   return 0;
 }
 
-int launch_wavefront(int nj, int nk, bool tb, int at, bool pk, const WaveParams& p, int grid,
-                     size_t smem, void* stream) {
-  const void* k = pick(nj, nk, tb, at, pk);
+int launch_wavefront(int nj, int nk, bool tb, int at, bool pk, bool slab, const WaveParams& p,
+                     int grid, size_t smem, void* stream) {
+  const void* k = pick(nj, nk, tb, at, pk, slab);
   if (!k) return -1;
   void* args[] = {const_cast<WaveParams*>(&p)};
   const cudaError_t e = cudaLaunchKernel(k, dim3(grid), dim3(kWarpsPerCta * 32), args, smem,

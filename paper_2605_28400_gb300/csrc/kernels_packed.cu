@@ -9,7 +9,7 @@ namespace {
 
 template <int NJ, int NK>
 const void* pptr() {
-  return reinterpret_cast<const void*>(&wavefront_kernel<NJ, NK, false, kGlobal, true>);
+  return reinterpret_cast<const void*>(&wavefront_kernel<NJ, NK, false, kGlobal, true, false>);
 }
 
 }  // namespace

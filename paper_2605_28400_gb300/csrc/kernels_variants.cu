@@ -8,7 +8,7 @@ namespace {
 
 template <int NJ, int NK, int AT>
 const void* vptr() {
-  return reinterpret_cast<const void*>(&wavefront_kernel<NJ, NK, false, AT, false>);
+  return reinterpret_cast<const void*>(&wavefront_kernel<NJ, NK, false, AT, false, false>);
 }
 
 }  // namespace

@@ -204,7 +204,7 @@ extern "C" trioseq_status trioseq_align_noalloc(const trioseq_scoring* sc,
     return TRIOSEQ_ECUDA;
   }
   const size_t smem = wavefront_smem_bytes(kNoallocNJ, kNoallocNK, KP, false);
-  if (wavefront_occupancy(kNoallocNJ, kNoallocNK, false, kGlobal, false, smem, &bpm) != 0 ||
+  if (wavefront_occupancy(kNoallocNJ, kNoallocNK, false, kGlobal, false, false, smem, &bpm) != 0 ||
       bpm <= 0)
     return TRIOSEQ_ECUDA;
   int32_t* prog = reinterpret_cast<int32_t*>(scratch + L.off_prog);
@@ -224,8 +224,8 @@ extern "C" trioseq_status trioseq_align_noalloc(const trioseq_scoring* sc,
   p.TI = 8;
   p.g2 = -2 * sc->gap;
   p.wait_ns = 2000000000LL;
-  if (launch_wavefront(kNoallocNJ, kNoallocNK, false, kGlobal, false, p, sms * bpm, smem, st) !=
-      0) {
+  if (launch_wavefront(kNoallocNJ, kNoallocNK, false, kGlobal, false, false, p, sms * bpm, smem,
+                       st) != 0) {
     cudaGetLastError();
     return TRIOSEQ_ECUDA;
   }

@@ -104,6 +104,8 @@ struct Workspace {
   DevBuf scores;    // int32 per triplet
   DevBuf rows;      // traceback rows
   DevBuf lens;      // alignment lengths
+  DevBuf planes;    // slab mode: checkpoint planes (traceback) or two ping-pong planes (score)
+  DevBuf walkstate; // slab mode: (i, j, k, n) of the traceback walk between slabs
   HostPinned staging;
   cudaStream_t alloc_stream = nullptr;  // grow buffers in this stream's order (serving slots)
 };
@@ -134,6 +136,8 @@ struct trioseq_plan_s {
   int64_t wait_ns = 2000000000LL;  // 2 s without progress = give up
   bool graphs = true;              // trioseq_batch_run replays a captured CUDA graph
   bool packed16 = true;            // pair score-only global triplets in int16 halves if they fit
+  size_t slab_budget = 0;          // bytes a one-triplet batch may use before it runs in slabs
+  int slab_slices = 0;             // forced slab height (0: chosen from the budget)
   Variant score_variant{8, 8};
   Variant tb_variant{4, 8};
   // Autotuner cache: (mode, single triplet or batch, bit length of the longest sequence) ->
@@ -176,6 +180,11 @@ struct trioseq_batch_s {
   size_t smem = 0;
   int TI = 8;  // progress-publication interval of this batch's launches
   bool packed = false;  // packed int16x2 mode: two triplets per column task
+  // Slab mode (one triplet whose records, or codes, would not fit at once): the cube runs as
+  // nslab launches of `slab` slices, chained through planes of plane_ints int32 each.
+  int slab = 0, nslab = 0;
+  size_t plane_ints = 0, nplanes = 0, off_slab = 0;
+  std::vector<TripDesc> slab_desc;
   bool uploaded = false;
   // results of the last run (host)
   std::vector<uint8_t> h_rows;
@@ -376,6 +385,62 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
       rows += align_up((size_t)3 * cap, 16);
     }
   }
+  // 4. Slab mode: one global-type int32 triplet whose boundary records (and, with traceback,
+  //    codes) would exceed the plan's budget at once, or any such triplet when a slab height is
+  //    forced. The cube then runs slab by slab, each launch seeded from the plane the slab below
+  //    left (DESIGN: linear-space traceback).
+  bt->slab = bt->nslab = 0;
+  bt->nplanes = bt->plane_ints = 0;
+  bt->slab_desc.clear();
+  if (n == 1 && plan->atype == kGlobal && !bt->packed) {
+    TripDesc& d = bt->desc[0];
+    const size_t ntask = (size_t)d.nJ * (size_t)d.nK;
+    const size_t A = (size_t)d.len[0] + 1;                     // slices of the cube
+    const size_t rec = ntask * (size_t)((WK + 4) + WJ);         // record ints per slice
+    const size_t cw = tb ? ntask * 32 * (size_t)W : 0;          // code words per step
+    const size_t plane = (size_t)d.nJ * WJ * (size_t)d.nK * WK;  // ints per plane
+    const auto bytes = [&](size_t S) {  // workspace of slab height S
+      const size_t slabs = (A + S - 1) / S;
+      const size_t planes = tb ? slabs - 1 : std::min<size_t>(2, slabs - 1);
+      return 4 * (S * rec + (S + 10) * cw + planes * plane);
+    };
+    size_t S = (size_t)plan->slab_slices;
+    if (S == 0 && 4 * (A * rec + (A + 10) * cw) > plan->slab_budget) {
+      // the largest power-of-two fraction of the cube that fits; fall back to the smallest
+      // workspace when none does (the allocation then reports ENOMEM)
+      size_t best = A;
+      for (S = A; S >= 1; S = S / 2) {
+        if (bytes(S) < bytes(best)) best = S;
+        if (bytes(S) <= plan->slab_budget) break;
+        if (S == 1) {
+          S = best;
+          break;
+        }
+      }
+    }
+    if (S > 0) {
+      S = std::min(S, A);
+      bt->slab = (int)S;
+      bt->nslab = (int)((A + S - 1) / S);
+      bt->plane_ints = plane;
+      bt->nplanes = tb ? bt->nslab - 1 : std::min(2, bt->nslab - 1);
+      for (int m = 0; m < bt->nslab; m++) {
+        TripDesc sd = d;
+        const int len0 = (int)std::min(S, A - (size_t)m * S) - 1;  // last local slice
+        sd.len[0] = sd.glen[0] = len0;
+        sd.T = len0 + 1 + (kPR - 1) + (kPC - 1);
+        sd.oj_off = 0;
+        sd.ok_off = (int64_t)(ntask * S * (size_t)(WK + 4));
+        sd.prog_base = 0;
+        sd.code_off = 0;
+        sd.out_idx = (m == bt->nslab - 1) ? 0 : -1;  // only the top slab ends at (a, b, c)
+        bt->slab_desc.push_back(sd);
+      }
+      d.code_off = 0;  // the walk reads the one slab of codes in the buffer
+      face = ntask * S * (size_t)((WK + 4) + WJ);
+      codes = tb ? ntask * (S + 10) * 32 * (size_t)W : 0;
+    }
+  }
   bt->seq_bytes = bt->seq.size();
   bt->face_ints = std::max<size_t>(face, 4);
   bt->code_words = std::max<size_t>(codes, 4);
@@ -411,6 +476,8 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
   size_t off = align_up(bt->seq_bytes, 256);
   bt->off_desc = off;
   off = align_up(off + sizeof(TripDesc) * std::max<size_t>(n, 1), 256);
+  bt->off_slab = off;
+  off = align_up(off + sizeof(TripDesc) * bt->slab_desc.size(), 256);
   bt->off_tasks = off;
   off = align_up(off + sizeof(Task) * std::max<size_t>(bt->tasks.size(), 1), 256);
   bt->off_tb = off;
@@ -423,7 +490,9 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
   // launch shape
   bt->smem = wavefront_smem_bytes(NJ, NK, plan->KP, bt->packed);
   int bpm = 0;
-  if (wavefront_occupancy(NJ, NK, tb, plan->atype, bt->packed, bt->smem, &bpm) != 0 || bpm <= 0)
+  if (wavefront_occupancy(NJ, NK, tb, plan->atype, bt->packed, bt->slab > 0, bt->smem, &bpm) !=
+          0 ||
+      bpm <= 0)
     return TRIOSEQ_ECUDA;
   const int want = env_int("TRIOSEQ_CTAS_PER_SM", bpm);
   bt->grid = plan->sms * std::max(1, std::min(bpm, want));
@@ -438,12 +507,15 @@ trioseq_status upload(trioseq_batch_s* bt, cudaStream_t st, bool pinned) {
   const bool tb = bt->mode == TRIOSEQ_WITH_TRACEBACK;
   const size_t nprog = bt->tasks.size() + 64;
   cudaStream_t as = ws.alloc_stream;
-  if (!ws.inputs.ensure(bt->inputs_bytes, as) || !ws.faces.ensure(bt->face_ints * sizeof(int32_t), as) ||
+  if (!ws.inputs.ensure(bt->inputs_bytes, as) ||
+      !ws.faces.ensure(bt->face_ints * sizeof(int32_t), as) ||
       !ws.progress.ensure(nprog * sizeof(int32_t), as) ||
       !ws.scores.ensure(std::max<size_t>(bt->n, 1) * sizeof(int32_t), as) ||
       (tb && (!ws.codes.ensure(bt->code_words * sizeof(uint32_t), as) ||
               !ws.rows.ensure(bt->rows_bytes, as) ||
               !ws.lens.ensure(std::max<size_t>(bt->tb_trips.size(), 1) * sizeof(int32_t), as))) ||
+      (bt->nplanes && !ws.planes.ensure(bt->nplanes * bt->plane_ints * sizeof(int32_t), as)) ||
+      (bt->slab && tb && !ws.walkstate.ensure(4 * sizeof(int32_t), as)) ||
       (pinned && !ws.staging.ensure(bt->inputs_bytes)))
     return TRIOSEQ_ENOMEM;
   std::vector<char> pageable;
@@ -452,6 +524,8 @@ trioseq_status upload(trioseq_batch_s* bt, cudaStream_t st, bool pinned) {
   std::memcpy(h, bt->seq.data(), bt->seq_bytes);
   std::memcpy(h + bt->off_desc, bt->desc.data(), sizeof(TripDesc) * bt->n);
   std::memcpy(h + bt->off_tasks, bt->tasks.data(), sizeof(Task) * bt->tasks.size());
+  if (!bt->slab_desc.empty())
+    std::memcpy(h + bt->off_slab, bt->slab_desc.data(), sizeof(TripDesc) * bt->slab_desc.size());
   if (tb) {
     std::memcpy(h + bt->off_tb, bt->tb_trips.data(), sizeof(int32_t) * bt->tb_trips.size());
     std::memcpy(h + bt->off_rowoff, bt->row_off.data(), sizeof(int64_t) * bt->row_off.size());
@@ -508,29 +582,74 @@ trioseq_status run(trioseq_batch_s* bt, cudaStream_t st) {
   if (plan->atype != kGlobal &&
       (e = cudaMemsetAsync(p.scores, 0x80, bt->n * sizeof(int32_t), st)) != cudaSuccess)
     return cuda_status(e);
+  WalkParams w{};
+  w.desc = p.desc;
+  w.tb_trips = reinterpret_cast<const int32_t*>(in + bt->off_tb);
+  w.ntb = (int32_t)bt->tb_trips.size();
+  w.seq = p.seq;
+  w.codes = p.codes;
+  w.rows = ws.rows.as<uint8_t>();
+  w.row_off = reinterpret_cast<const int64_t*>(in + bt->off_rowoff);
+  w.row_cap = reinterpret_cast<const int32_t*>(in + bt->off_rowcap);
+  w.aln_len = ws.lens.as<int32_t>();
+  w.err = err;
+  w.NJ = bt->var.nj;
+  w.NK = bt->var.nk;
   bt->timed = false;
   if (bt->profile && record(bt->ev[0], st) != cudaSuccess)
     return cuda_status(cudaGetLastError());
-  if (launch_wavefront(bt->var.nj, bt->var.nk, tb, plan->atype, bt->packed, p, bt->grid, bt->smem,
-                       st) != 0)
-    return cuda_status(cudaGetLastError());
-  if (bt->profile && record(bt->ev[1], st) != cudaSuccess)
-    return cuda_status(cudaGetLastError());
-  if (tb && !bt->tb_trips.empty()) {
-    WalkParams w{};
-    w.desc = p.desc;
-    w.tb_trips = reinterpret_cast<const int32_t*>(in + bt->off_tb);
-    w.ntb = (int32_t)bt->tb_trips.size();
-    w.seq = p.seq;
-    w.codes = p.codes;
-    w.rows = ws.rows.as<uint8_t>();
-    w.row_off = reinterpret_cast<const int64_t*>(in + bt->off_rowoff);
-    w.row_cap = reinterpret_cast<const int32_t*>(in + bt->off_rowcap);
-    w.aln_len = ws.lens.as<int32_t>();
-    w.err = err;
-    w.NJ = bt->var.nj;
-    w.NK = bt->var.nk;
-    if (launch_walk(w, st) != 0) return cuda_status(cudaGetLastError());
+  if (bt->slab) {
+    // Slab mode. Slab m covers the slices m*S .. of the cube; plane m holds its last slice.
+    // Score: forward through all slabs, planes ping-pong. Traceback: forward through all but the
+    // top slab keeping every plane (no codes), then from the top slab down: recompute the slab
+    // with codes from the plane below it and continue the walk through it.
+    const TripDesc* sdesc = reinterpret_cast<const TripDesc*>(in + bt->off_slab);
+    int32_t* planes = ws.planes.as<int32_t>();
+    const auto plane = [&](int idx) { return planes + (size_t)idx * bt->plane_ints; };
+    const auto wave = [&](int m, const int32_t* pin, int32_t* pout, bool codes) {
+      const cudaError_t ee = cudaMemsetAsync(prog, 0, nprog * sizeof(int32_t), st);
+      if (ee != cudaSuccess) return cuda_status(ee);
+      WaveParams q = p;
+      q.desc = sdesc + m;
+      q.i0 = m * bt->slab;
+      q.plane_in = pin;
+      q.plane_out = pout;
+      q.codes = codes ? p.codes : nullptr;
+      if (launch_wavefront(bt->var.nj, bt->var.nk, tb, kGlobal, false, true, q, bt->grid,
+                           bt->smem, st) != 0)
+        return cuda_status(cudaGetLastError());
+      return TRIOSEQ_OK;
+    };
+    const int M = bt->nslab;
+    trioseq_status s = TRIOSEQ_OK;
+    if (!tb) {
+      for (int m = 0; m < M && s == TRIOSEQ_OK; m++)
+        s = wave(m, m ? plane((m - 1) & 1) : nullptr, m + 1 < M ? plane(m & 1) : nullptr, false);
+    } else {
+      for (int m = 0; m + 1 < M && s == TRIOSEQ_OK; m++)
+        s = wave(m, m ? plane(m - 1) : nullptr, plane(m), false);
+      for (int m = M - 1; m >= 0 && s == TRIOSEQ_OK; m--) {
+        s = wave(m, m ? plane(m - 1) : nullptr, nullptr, true);
+        if (s != TRIOSEQ_OK) break;
+        WalkParams wm = w;
+        wm.i_lo = m * bt->slab;
+        wm.T_slab = bt->slab_desc[m].T;  // steps per task of the slab that wrote the codes
+        wm.state = ws.walkstate.as<int32_t>();
+        wm.init_state = (m == M - 1) ? 1 : 0;
+        if (launch_walk(wm, st) != 0) s = cuda_status(cudaGetLastError());
+      }
+    }
+    if (s != TRIOSEQ_OK) return s;
+    if (bt->profile && record(bt->ev[1], st) != cudaSuccess)
+      return cuda_status(cudaGetLastError());
+  } else {
+    if (launch_wavefront(bt->var.nj, bt->var.nk, tb, plan->atype, bt->packed, false, p, bt->grid,
+                         bt->smem, st) != 0)
+      return cuda_status(cudaGetLastError());
+    if (bt->profile && record(bt->ev[1], st) != cudaSuccess)
+      return cuda_status(cudaGetLastError());
+    if (tb && !bt->tb_trips.empty() && launch_walk(w, st) != 0)
+      return cuda_status(cudaGetLastError());
   }
   if (bt->profile) {
     if (record(bt->ev[2], st) != cudaSuccess) return cuda_status(cudaGetLastError());
@@ -705,6 +824,16 @@ trioseq_status trioseq_plan(const trioseq_scoring* sc, uint32_t max_len_hint, ui
   plan->TI = std::max(1, env_int("TRIOSEQ_TI", 8));
   plan->graphs = env_int("TRIOSEQ_GRAPHS", 1) != 0;
   plan->packed16 = env_int("TRIOSEQ_PACKED", 1) != 0;
+  {
+    size_t fr = 0, tot = 0;
+    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+      cudaGetLastError();
+      fr = 0;
+    }
+    const int mb = env_int("TRIOSEQ_SLAB_BUDGET_MB", 0);
+    plan->slab_budget = mb > 0 ? (size_t)mb << 20 : fr / 2;
+    plan->slab_slices = std::max(0, env_int("TRIOSEQ_SLAB_SLICES", 0));
+  }
   const char* sv = std::getenv("TRIOSEQ_SCORE_TILE");
   if (sv && std::strlen(sv) >= 3) plan->score_variant = Variant{sv[0] - '0', sv[2] - '0'};
   const char* tv = std::getenv("TRIOSEQ_TB_TILE");
@@ -795,6 +924,13 @@ trioseq_status trioseq_batch_info(trioseq_batch_t bt, size_t* n, uint64_t* cells
   if (tasks) *tasks = bt->tasks.size();
   if (tile_j) *tile_j = bt->var.nj;
   if (tile_k) *tile_k = bt->var.nk;
+  return TRIOSEQ_OK;
+}
+
+trioseq_status trioseq_batch_slabs(trioseq_batch_t bt, int32_t* slices, int32_t* slabs) {
+  if (!bt || !slices || !slabs) return TRIOSEQ_EINVAL;
+  *slices = bt->slab;
+  *slabs = bt->nslab;
   return TRIOSEQ_OK;
 }
 

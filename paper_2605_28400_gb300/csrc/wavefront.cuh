@@ -120,14 +120,17 @@ struct Geom {
 // AT selects the alignment type of Sec. II (kGlobal, kSemiGlobal, kLocal; engine.h); the
 // semi-global and local types are built for score mode only. PACK = true is the packed int16x2
 // mode (engine.h): the triplet of descriptor d in the low halves, that of d.pair in the high
-// halves, on the task grid of their maximal lengths (global type, score only).
-template <int NJ, int NK, bool TB, int AT, bool PACK>
+// halves, on the task grid of their maximal lengths (global type, score only). SLAB = true builds
+// the slab launches of one triplet (global type, int32; WaveParams i0 / plane_in / plane_out):
+// a kept apart so that the regular instantiations carry none of its registers.
+template <int NJ, int NK, bool TB, int AT, bool PACK, bool SLAB>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::value)
     wavefront_kernel(const WaveParams p) {
   using G = Geom<NJ, NK>;
   static_assert(NJ % 4 == 0 && NK % 4 == 0, "tile sides must be multiples of 4");
   static_assert(AT == kGlobal || !TB, "semi-global and local types are score-only");
   static_assert(!PACK || (!TB && AT == kGlobal), "the packed mode is global and score-only");
+  static_assert(!SLAB || (!PACK && AT == kGlobal), "slab launches are global and int32");
   constexpr int NEG = PACK ? kNeg16x2 : kNeg;  // -infinity in every lane of a register
   static_assert(G::NCOPY <= 32, "one staged piece per lane per step");
   constexpr int WJ = G::WJ, WK = G::WK, W = G::W;
@@ -274,6 +277,28 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
     }
     // M'[-1][-1][-1] = 0 feeds the origin through the (1,1,1) move (stored as 8*0+7 with keys).
     if (J == 0 && K == 0 && lane == 0) rowB[0] = TB ? 7 : 0;
+    const int PW = nK * WK;  // row stride of a slab plane
+    if (SLAB && p.plane_in) {
+      // Slab launch: the state before the first slice is slice i0 - 1 of the cube. Every lane's
+      // tile starts from the plane; the halos matter for lane (0,0) only (the other lanes meet
+      // local slice -1 inside the loop, from shuffles of these tiles or from plane pieces).
+      const int* pl = p.plane_in;
+#pragma unroll
+      for (int pp = 0; pp < NJ; ++pp) {
+#pragma unroll
+        for (int q4 = 0; q4 < NK / 4; ++q4) {
+          const int4 v = *reinterpret_cast<const int4*>(pl + (int64_t)(j0 + pp) * PW + k0 + 4 * q4);
+          P[pp][4 * q4] = v.x;
+          P[pp][4 * q4 + 1] = v.y;
+          P[pp][4 * q4 + 2] = v.z;
+          P[pp][4 * q4 + 3] = v.w;
+        }
+        colB[pp] = (k0 >= 1) ? pl[(int64_t)(j0 + pp) * PW + k0 - 1] : NEG;
+      }
+#pragma unroll
+      for (int qq = 0; qq <= NK; ++qq)
+        rowB[qq] = (j0 >= 1 && k0 + qq >= 1) ? pl[(int64_t)(j0 - 1) * PW + k0 + qq - 1] : NEG;
+    }
     // Semi-global (Sec. II): the axes are zero in the original frame, i.e. M'[i][0][0] = g2*i,
     // M'[0][j][0] = g2*j, M'[0][0][k] = g2*k with g2 = -2*alpha. They enter through the halo
     // cells that feed each axis through a move whose cost is 0 there (all involve the virtual
@@ -308,8 +333,9 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
     const int* progK = p.progress + d.prog_base + (me - 1);
     int* progMe = p.progress + d.prog_base + me;
     int cachedJ = J > 0 ? 0 : 1 << 30, cachedK = K > 0 ? 0 : 1 << 30;  // warp-uniform
-    uint32_t* code_base =
-        TB ? p.codes + d.code_off + (int64_t)me * T * 32 * W + lane * W : nullptr;
+    uint32_t* code_base = (TB && (!SLAB || p.codes))
+                              ? p.codes + d.code_off + (int64_t)me * T * 32 * W + lane * W
+                              : nullptr;
     bool ok = true;
 
     // Face pieces of step u: each lane loads its 16-byte piece from L2 into registers at step
@@ -341,6 +367,18 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
         const int* src = (cp_kind == 1) ? srcJ + (int64_t)sl * G::RJ + cp_col
                                         : srcK + (int64_t)sl * G::RK + cp_col;
         pf = __ldcg(reinterpret_cast<const int4*>(src));
+      } else if (SLAB && p.plane_in && sl == -1 && cp_kind != 0 &&
+                 (cp_kind == 1 ? J > 0 : K > 0)) {
+        // Slab launch, local slice -1: the producer's record of that slice is plane i0 - 1.
+        const int* pl = p.plane_in;
+        if (cp_kind == 1) {  // j-record slots cp_col..+3: row J*WJ-1, k = K*WK + slot - 4
+          const int k = K * WK + cp_col - 4;
+          pf = (k >= 0) ? *reinterpret_cast<const int4*>(pl + (int64_t)(J * WJ - 1) * PW + k)
+                        : make_int4(NEG, NEG, NEG, NEG);
+        } else {  // k-record slots cp_col..+3: column K*WK-1, rows J*WJ + slot
+          const int64_t base = (int64_t)(J * WJ + cp_col) * PW + K * WK - 1;
+          pf = make_int4(pl[base], pl[base + PW], pl[base + 2 * PW], pl[base + 3 * PW]);
+        }
       } else {
         pf = make_int4(NEG, NEG, NEG, NEG);
       }
@@ -357,8 +395,8 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
     // loaded one block ahead and read by shuffle, so no global load sits on the per-step path.
     // Packed mode: the two triplets' residues in bits 0-7 and 8-15.
     auto xblock = [&](int base) -> int {
-      const int sl = base + lane;
-      const int x0 = (sl >= 1 && sl <= a0) ? (int)__ldg(S0 + sl - 1) : VIRT;
+      const int sl = base + lane, gi = sl + (SLAB ? p.i0 : 0);  // local slice, cube slice
+      const int x0 = (gi >= 1 && sl <= a0) ? (int)__ldg(S0 + gi - 1) : VIRT;
       if (!PACK) return x0;
       const int x1 = (sl >= 1 && sl <= a1) ? (int)__ldg(T0 + sl - 1) : VIRT;
       return x0 | (x1 << 8);
@@ -627,7 +665,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
             for (int qq = 0; qq < NK; ++qq) P[pp][qq] = Q[pp][qq];
         }
 
-        if (TB) {
+        if (TB && (!SLAB || code_base)) {
           uint32_t* dst = code_base + (int64_t)t * 32 * W;
           if (W % 4 == 0) {
 #pragma unroll
@@ -639,6 +677,16 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
             for (int w2 = 0; w2 < W / 2; ++w2)
               reinterpret_cast<uint2*>(dst)[w2] = make_uint2(cw[2 * w2], cw[2 * w2 + 1]);
           }
+        }
+        if (SLAB && p.plane_out && s == a) {
+          // Slab launch: the last slice becomes the next slab's input plane.
+#pragma unroll
+          for (int pp = 0; pp < NJ; ++pp)
+#pragma unroll
+            for (int q4 = 0; q4 < NK / 4; ++q4)
+              *reinterpret_cast<int4*>(p.plane_out + (int64_t)(j0 + pp) * PW + k0 + 4 * q4) =
+                  make_int4(P[pp][4 * q4], P[pp][4 * q4 + 1], P[pp][4 * q4 + 2],
+                            P[pp][4 * q4 + 3]);
         }
         if (r == kPR - 1 && has_out_j) {
           int* dst = dstJ + (int64_t)s * G::RJ;
@@ -667,7 +715,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
               if ((edgeJ && pp == pb && qq <= qc) || (edgeK && qq == qc && pp <= pb))
                 best = max(best, P[pp][qq] - base - g2 * (pp + qq));
         }
-        if (AT == kGlobal && owns_end && s == a0) {
+        if (AT == kGlobal && owns_end && s == a0 && (!SLAB || d.out_idx >= 0)) {
           int v = 0;
 #pragma unroll
           for (int pp = 0; pp < NJ; ++pp)
