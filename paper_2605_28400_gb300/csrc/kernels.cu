@@ -3,7 +3,9 @@
 //
 // walk_kernel: one warp per traceback request. Lane 0 follows the stored moves back from
 //   (a, b, c) through a tube of code records along the diagonal, staged in shared memory by the
-//   whole warp in one round trip; repeated until the origin.
+//   whole warp in one round trip; repeated until the origin. In the linear-space traceback the
+//   codes hold one slab of slices at a time: the walk resumes from a saved (i, j, k, n) and stops
+//   when it leaves the slab.
 #include "wavefront.cuh"
 
 namespace trioseq {
