@@ -62,6 +62,11 @@ def _load():
         lib.oracle_align_type.argtypes = [u8p, ctypes.c_int, u8p, ctypes.c_int, u8p, ctypes.c_int,
                                           ctypes.c_int, i32p, ctypes.c_int32, ctypes.c_int, i64p]
         lib.oracle_align_type.restype = ctypes.c_int
+        lib.oracle_align_type_tb.argtypes = [u8p, ctypes.c_int, u8p, ctypes.c_int, u8p,
+                                             ctypes.c_int, ctypes.c_int, i32p, ctypes.c_int32,
+                                             ctypes.c_int, i64p, u8p, ctypes.c_int64, i64p, i32p,
+                                             i32p]
+        lib.oracle_align_type_tb.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -178,3 +183,26 @@ def align_type(s0, s1, s2, sub, gap: int, kind: int) -> int:
     if rc:
         raise RuntimeError(f"oracle_align_type failed ({rc})")
     return int(score.value)
+
+
+def align_type_tb(s0, s1, s2, sub, gap: int, kind: int):
+    """(score, rows (3, L), begin (i0, j0, k0), end (i1, j1, k1)) of the alignment type ``kind``:
+    the rows align S0[i0:i1], S1[j0:j1], S2[k0:k1]. End cell: the first cell in (i, j, k) order
+    with the best score among those that count; walk: first maximal move in Eq. 1's order, v
+    last; stops at axis cells and, for LOCAL, where v = 0 alone is maximal."""
+    lib = _load()
+    n = [len(s0), len(s1), len(s2)]
+    a0, a1, a2 = _u8(s0), _u8(s1), _u8(s2)
+    sm, K = _sub(sub)
+    cap = max(1, sum(n))
+    rows = np.zeros(3 * cap, dtype=np.uint8)
+    score, L = ctypes.c_int64(0), ctypes.c_int64(0)
+    beg, end = (ctypes.c_int32 * 3)(), (ctypes.c_int32 * 3)()
+    rc = lib.oracle_align_type_tb(_ptr(a0, ctypes.c_uint8), n[0], _ptr(a1, ctypes.c_uint8), n[1],
+                                  _ptr(a2, ctypes.c_uint8), n[2], K, _ptr(sm, ctypes.c_int32),
+                                  int(gap), int(kind), ctypes.byref(score),
+                                  _ptr(rows, ctypes.c_uint8), cap, ctypes.byref(L), beg, end)
+    if rc:
+        raise RuntimeError(f"oracle_align_type_tb failed ({rc})")
+    r = rows.reshape(3, cap)[:, : L.value].copy()
+    return int(score.value), r, tuple(beg), tuple(end)

@@ -193,6 +193,116 @@ int oracle_align_type(const uint8_t* s0, int a, const uint8_t* s1, int b, const 
   return 0;
 }
 
+// Score and alignment of the three alignment types of Sec. II, with the span of the cube the
+// alignment covers: begin[3] = (i0, j0, k0), end[3] = (i1, j1, k1); the rows align
+// S0[i0:i1], S1[j0:j1], S2[k0:k1] (columns of the path from begin to end).
+//   type 0 (global): as oracle_align; begin = (0,0,0), end = (a,b,c).
+//   type 1 (semi-global) and 2 (local): the cube as in oracle_align_type. The end cell is the
+//     first cell in (i, j, k) order holding the best score among the cells that count (the last
+//     faces for semi-global, every cell for local). From it the walk follows, at each cell, the
+//     first maximal candidate in Eq. 1's listing order, v being listed last: the walk stops at an
+//     axis cell (two zero indices, initialised, not computed) and, for local, where v = 0 is the
+//     only maximal candidate.
+// rows/cap/len_out as in oracle_align (cap >= a+b+c). Returns 0, -1 (bad arguments), -2.
+int oracle_align_type_tb(const uint8_t* s0, int a, const uint8_t* s1, int b, const uint8_t* s2,
+                         int c, int K, const int32_t* sub, int32_t gap, int type,
+                         int64_t* score_out, uint8_t* rows, int64_t cap, int64_t* len_out,
+                         int32_t* begin, int32_t* end) {
+  if (a < 0 || b < 0 || c < 0 || K <= 0 || !sub || !score_out || !rows || !len_out || !begin ||
+      !end || type < 0 || type > 2 || cap < (int64_t)a + b + c)
+    return -1;
+  if (type == 0) {
+    const int rc = oracle_align(s0, a, s1, b, s2, c, K, sub, gap, score_out, rows, cap, len_out);
+    begin[0] = begin[1] = begin[2] = 0;
+    end[0] = a;
+    end[1] = b;
+    end[2] = c;
+    return rc;
+  }
+  Scoring sc{K, sub, gap};
+  const int64_t C = c + 1, plane = (int64_t)(b + 1) * C;
+  std::vector<uint8_t> code;  // winning move 0..6, or 7 = start here (axis cell, or v won)
+  try {
+    code.assign((size_t)(a + 1) * (size_t)plane, 7);
+  } catch (...) {
+    return -2;
+  }
+  std::vector<int64_t> prev(plane), cur(plane);
+  bool have_score = false;
+  int64_t score = 0;
+  int ei = 0, ej = 0, ek = 0;
+  for (int i = 0; i <= a; i++) {
+    for (int j = 0; j <= b; j++) {
+      for (int k = 0; k <= c; k++) {
+        const int zeros = (i == 0) + (j == 0) + (k == 0);
+        int64_t best = 0;
+        int arg = 7;
+        if (zeros < 2) {
+          bool have = false;
+          for (int m = 0; m < 7; m++) {
+            const int di = kMoves[m][0], dj = kMoves[m][1], dk = kMoves[m][2];
+            const int pi = i - di, pj = j - dj, pk = k - dk;
+            if (pi < 0 || pj < 0 || pk < 0) continue;
+            const int64_t pv = (di ? prev : cur)[(int64_t)pj * C + pk];
+            const int x = di ? (int)s0[i - 1] : -1;
+            const int y = dj ? (int)s1[j - 1] : -1;
+            const int z = dk ? (int)s2[k - 1] : -1;
+            const int64_t cand = pv + sc.sop(x, y, z);
+            if (!have || cand > best) {
+              best = cand;
+              arg = m;
+              have = true;
+            }
+          }
+          if (type == 2 && best < 0) {  // v = 0 is listed last: it wins only when alone
+            best = 0;
+            arg = 7;
+          }
+        }
+        cur[(int64_t)j * C + k] = best;
+        code[(size_t)i * plane + (size_t)j * C + k] = (uint8_t)arg;
+        const bool counts = type == 2 || i == a || j == b || k == c;
+        if (counts && (!have_score || best > score)) {  // first cell with the best score
+          score = best;
+          have_score = true;
+          ei = i;
+          ej = j;
+          ek = k;
+        }
+      }
+    }
+    std::swap(prev, cur);
+  }
+  *score_out = score;
+  std::vector<uint8_t> r0, r1, r2;
+  int i = ei, j = ej, k = ek;
+  for (;;) {
+    const int m = code[(size_t)i * plane + (size_t)j * C + k];
+    if (m > 6) break;  // start cell
+    const int di = kMoves[m][0], dj = kMoves[m][1], dk = kMoves[m][2];
+    r0.push_back(di ? s0[i - 1] : ORACLE_GAP);
+    r1.push_back(dj ? s1[j - 1] : ORACLE_GAP);
+    r2.push_back(dk ? s2[k - 1] : ORACLE_GAP);
+    i -= di;
+    j -= dj;
+    k -= dk;
+  }
+  const int64_t L = (int64_t)r0.size();
+  for (int64_t t = 0; t < L; t++) {
+    rows[t] = r0[L - 1 - t];
+    rows[cap + t] = r1[L - 1 - t];
+    rows[2 * cap + t] = r2[L - 1 - t];
+  }
+  *len_out = L;
+  begin[0] = i;
+  begin[1] = j;
+  begin[2] = k;
+  end[0] = ei;
+  end[1] = ej;
+  end[2] = ek;
+  return 0;
+}
+
 // Sum-of-pairs score of a given 3-row alignment (Sec. II SOP summed over columns).
 // rows: 3 rows of length L at stride cap, gap = 255. Returns 0, or -1 on a residue >= K.
 int oracle_sp_score(const uint8_t* rows, int64_t L, int64_t cap, int K, const int32_t* sub,

@@ -72,3 +72,49 @@ def brute_force(s0, s1, s2, sub, gap):
     rec(len(s[0]), len(s[1]), len(s[2]), 0)
     rows = [[GAP if col[q] is None else col[q] for col in best[1]] for q in range(3)]
     return best[0], rows
+
+
+def brute_best_ending_at(s0, s1, s2, sub, gap, end, kind):
+    """Best score of an alignment path that ends at cell `end` and starts where the alignment type
+    allows: any cell s <= end for local (the empty path scores 0), an axis cell (two zero
+    indices) for semi-global. Enumerates every start and every path (tiny inputs only)."""
+    i1, j1, k1 = end
+    best = 0 if kind == 2 else None
+    for i0 in range(i1 + 1):
+        for j0 in range(j1 + 1):
+            for k0 in range(k1 + 1):
+                if kind == 1 and (i0 == 0) + (j0 == 0) + (k0 == 0) < 2:
+                    continue
+                v, _ = brute_force(s0[i0:i1], s1[j0:j1], s2[k0:k1], sub, gap)
+                best = v if best is None else max(best, v)
+    return best
+
+
+def brute_walk(s0, s1, s2, sub, gap, end, kind, target):
+    """First path (in the order: moves by Eq. 1's listing, then stopping) that walks back from
+    `end` to a start with total score `target`. Starts: axis cells always (they are initialised);
+    for local also any cell (v = 0, listed after the moves). Returns (rows, begin)."""
+    s = [list(map(int, s0)), list(map(int, s1)), list(map(int, s2))]
+    cols = []
+    found = [None]
+
+    def rec(i, j, k, acc):
+        axis = (i == 0) + (j == 0) + (k == 0) >= 2
+        if not axis:
+            for di, dj, dk in MOVES:
+                if i < di or j < dj or k < dk:
+                    continue
+                col = (s[0][i - 1] if di else None, s[1][j - 1] if dj else None,
+                       s[2][k - 1] if dk else None)
+                cols.append(col)
+                if rec(i - di, j - dj, k - dk, acc + column_score(col, sub, gap)):
+                    return True
+                cols.pop()
+        if (axis or kind == 2) and acc == target:
+            rows = [[GAP if c[q] is None else c[q] for c in reversed(cols)] for q in range(3)]
+            found[0] = (rows, (i, j, k))
+            return True
+        return False
+
+    rec(*end, 0)
+    return found[0]

@@ -132,3 +132,56 @@ def test_empty_and_planted_motif():
     s0 = np.concatenate([rseq(rng, 20, 4), motif, rseq(rng, 20, 4)])
     s = oracle.align_type(s0, motif, motif, DNA.sub, DNA.gap, oracle.SEMIGLOBAL)
     assert s >= 3 * 2 * len(motif)
+
+
+# ---- tracebacks of the semi-global and local types ----------------------------------------------
+
+from tests.brute import GAP, brute_best_ending_at, brute_walk  # noqa: E402
+
+
+def _strip(row):
+    return np.array([r for r in row if r != GAP], dtype=np.uint8)
+
+
+@pytest.mark.parametrize("shape", [s for s in itertools.product(range(4), repeat=3) if sum(s) <= 7])
+def test_variant_traceback_bruteforce(shape):
+    rng = np.random.default_rng(300 + sum(q * 5 ** n for n, q in enumerate(shape)))
+    sub = rand_sub(rng, 3)
+    gap = -int(rng.integers(0, 4))
+    t = [rseq(rng, n, 3) for n in shape]
+    for kind in (oracle.SEMIGLOBAL, oracle.LOCAL):
+        score, rows, beg, end = oracle.align_type_tb(*t, sub, gap, kind)
+        assert score == oracle.align_type(*t, sub, gap, kind)
+        # the end cell is the first cell (i, j, k order) whose best ending score is the optimum
+        cells = [(i, j, k) for i in range(shape[0] + 1) for j in range(shape[1] + 1)
+                 for k in range(shape[2] + 1)
+                 if kind == oracle.LOCAL or i == shape[0] or j == shape[1] or k == shape[2]]
+        first = next(e for e in cells if brute_best_ending_at(*t, sub, gap, e, kind) == score)
+        assert end == first
+        # the path is the first optimal one in move priority order
+        want_rows, want_beg = brute_walk(*t, sub, gap, end, kind, score)
+        assert beg == want_beg
+        assert rows.tolist() == [list(r) for r in want_rows]
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_variant_traceback_consistency(seed):
+    rng = np.random.default_rng(400 + seed)
+    sc = DNA if seed % 2 == 0 else PROT
+    K = sc.sub.shape[0]
+    t = [rseq(rng, int(n), K) for n in rng.integers(0, 60, size=3)]
+    for kind in (oracle.SEMIGLOBAL, oracle.LOCAL):
+        score, rows, beg, end = oracle.align_type_tb(*t, sc.sub, sc.gap, kind)
+        assert score == oracle.align_type(*t, sc.sub, sc.gap, kind)
+        assert all(b <= e for b, e in zip(beg, end))
+        for q in range(3):
+            assert np.array_equal(_strip(rows[q]), t[q][beg[q]:end[q]])
+        assert not any(all(rows[q][c] == GAP for q in range(3)) for c in range(rows.shape[1]))
+        assert oracle.sp_score(rows, sc.sub, sc.gap) == score  # the path scores the optimum
+        if kind == oracle.SEMIGLOBAL:
+            assert sum(b == 0 for b in beg) >= 2  # starts on an axis
+            assert end[0] == len(t[0]) or end[1] == len(t[1]) or end[2] == len(t[2])
+    g, grows, gb, ge = oracle.align_type_tb(*t, sc.sub, sc.gap, oracle.GLOBAL)
+    want, wrows = oracle.align(*t, sc.sub, sc.gap, traceback=True)
+    assert (g, gb, ge) == (want, (0, 0, 0), tuple(len(x) for x in t))
+    assert np.array_equal(grows, wrows)
