@@ -82,7 +82,12 @@ enum { TRIOSEQ_SCORE_ONLY = 0, TRIOSEQ_WITH_TRACEBACK = 1 };
  *              Eq. 1), as the section writes it.
  *  LOCAL       the same zero axes and v = 0 in Eq. 1 (no cell is negative); the score is the
  *              best cell of the cube ("Local Alignments").
- * SEMIGLOBAL and LOCAL are score-only: WITH_TRACEBACK under such a plan gives ENOTIMPL. */
+ * With WITH_TRACEBACK, SEMIGLOBAL and LOCAL report the alignment of the best cell: the first cell
+ * in (i, j, k) order holding the best score among the cells that count. The walk back from it
+ * takes the first maximal candidate in Eq. 1's order, v listed last, and stops at an axis cell
+ * (two zero indices) or, for LOCAL, where v = 0 alone is maximal. The rows are that path's
+ * columns. trioseq_traceback_span gives the cells it joins, i.e. the substrings it aligns.
+ * Such batches need (a+1)(b+1)(c+1) < 2^37 per triplet (else EOVERFLOW). */
 enum { TRIOSEQ_GLOBAL = 0, TRIOSEQ_SEMIGLOBAL = 1, TRIOSEQ_LOCAL = 2 };
 
 typedef struct trioseq_plan_s* trioseq_plan_t;
@@ -119,6 +124,13 @@ trioseq_status trioseq_align_batch(trioseq_plan_t plan, const trioseq_triplet* t
 trioseq_status trioseq_traceback(trioseq_plan_t plan, size_t idx, char* row0, char* row1,
                                  char* row2, size_t cap, size_t* aln_len);
 
+/* trioseq_traceback_span — the cells the alignment of triplet idx joins: begin = (i0, j0, k0),
+ * end = (i1, j1, k1); its rows align S0[i0:i1], S1[j0:j1], S2[k0:k1]. For GLOBAL plans begin =
+ * (0,0,0) and end = (a,b,c); for SEMIGLOBAL begin lies on an axis and end on a last face.
+ * Errors: EINVAL (no traceback batch, idx out of range, null). */
+trioseq_status trioseq_traceback_span(trioseq_plan_t plan, size_t idx, int32_t begin[3],
+                                      int32_t end[3]);
+
 /* ---- device-resident batches (inputs already in HBM; used by benchmarks and servers) ---- */
 
 typedef struct trioseq_batch_s* trioseq_batch_t;
@@ -151,6 +163,10 @@ trioseq_status trioseq_batch_device_scores(trioseq_batch_t batch, int32_t** d_sc
  * triplet idx as in trioseq_traceback. */
 trioseq_status trioseq_batch_alignment(trioseq_batch_t batch, size_t idx, char* row0, char* row1,
                                        char* row2, size_t cap, size_t* aln_len);
+
+/* trioseq_batch_span — as trioseq_traceback_span, for triplet idx of a device-resident batch. */
+trioseq_status trioseq_batch_span(trioseq_batch_t batch, size_t idx, int32_t begin[3],
+                                  int32_t end[3]);
 
 /* Work statistics of a batch: number of triplets, the paper's cell count
  * (sum of |S0|*|S1|*|S2|, the TCUPS numerator), the number of column tasks in the queue, and the

@@ -84,6 +84,8 @@ def load(build_if_missing: bool = True):
         "trioseq_plan_autotune": ([vp, ctypes.POINTER(Triplet), sz, u32, i32p, i32p, i32p], i32),
         "trioseq_batch_packing": ([vp, i32p], i32),
         "trioseq_batch_slabs": ([vp, i32p, i32p], i32),
+        "trioseq_traceback_span": ([vp, sz, i32p, i32p], i32),
+        "trioseq_batch_span": ([vp, sz, i32p, i32p], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -100,7 +102,8 @@ def exported_symbols() -> list[str]:
             "trioseq_batch_destroy", "trioseq_batch_profile", "trioseq_batch_timing",
             "trioseq_plan_io_bytes", "trioseq_server_create", "trioseq_submit", "trioseq_poll",
             "trioseq_server_destroy", "trioseq_strerror", "trioseq_align_noalloc",
-            "trioseq_plan_autotune", "trioseq_batch_packing", "trioseq_batch_slabs"]
+            "trioseq_plan_autotune", "trioseq_batch_packing", "trioseq_batch_slabs",
+            "trioseq_traceback_span", "trioseq_batch_span"]
 
 
 def trioseq_plan_autotune(plan, sample, mode: int = SCORE_ONLY) -> dict:
@@ -232,6 +235,21 @@ def trioseq_batch_device_scores(batch) -> int:
 
 def trioseq_batch_alignment(batch, idx: int, cap: int | None = None):
     return _rows(load().trioseq_batch_alignment, batch, idx, cap)
+
+
+def _span(fn, handle, idx: int):
+    beg, end = (ctypes.c_int32 * 3)(), (ctypes.c_int32 * 3)()
+    _check(fn(handle, idx, beg, end), fn.__name__)
+    return tuple(beg), tuple(end)
+
+
+def trioseq_traceback_span(plan, idx: int):
+    """((i0, j0, k0), (i1, j1, k1)): the rows of triplet idx align S0[i0:i1], S1[j0:j1], S2[k0:k1]."""
+    return _span(load().trioseq_traceback_span, plan, idx)
+
+
+def trioseq_batch_span(batch, idx: int):
+    return _span(load().trioseq_batch_span, batch, idx)
 
 
 def trioseq_batch_info(batch) -> dict:

@@ -98,6 +98,10 @@ struct WaveParams {
   int32_t i0;
   const int32_t* plane_in;
   int32_t* plane_out;
+  // Semi-global / local with traceback: per triplet, the 64-bit max of
+  // (M + 2^26) << 37 | (2^37 - 1 - cell index), i.e. the best score and its first cell in
+  // (i, j, k) order; zeroed before launch. The walk starts there and writes the score.
+  unsigned long long* best64;
 };
 
 struct WalkParams {
@@ -118,6 +122,10 @@ struct WalkParams {
   int32_t i_lo, T_slab;
   int32_t* state;
   int32_t init_state;        // 1: start at (a, b, c) (the top slab) instead of reading state
+  int32_t atype;             // alignment type: semi-global and local start at best64's cell,
+  const unsigned long long* best64;  // stop at axis cells, and local also at rank 0 (v won)
+  int32_t* scores;           // written from best64 for those types
+  int32_t* span;             // per request: begin (i, j, k) and end (i, j, k) of the alignment
 };
 
 // Host-side launchers implemented in kernels.cu. `at` is the alignment type (kGlobal, ...);
@@ -128,8 +136,8 @@ int launch_wavefront(int nj, int nk, bool tb, int at, bool pk, bool slab, const 
                      int grid, size_t smem, void* stream);
 int wavefront_occupancy(int nj, int nk, bool tb, int at, bool pk, bool slab, size_t smem,
                         int* blocks_per_sm);
-// Kernel entry of a semi-global or local score-mode instantiation (kernels_variants.cu), or null.
-const void* wavefront_variant(int nj, int nk, int at);
+// Kernel entry of a semi-global or local instantiation (kernels_variants.cu), or null.
+const void* wavefront_variant(int nj, int nk, int at, bool tb);
 // Kernel entry of a packed int16x2 (global, score) instantiation (kernels_packed.cu), or null.
 const void* wavefront_packed(int nj, int nk);
 // Kernel entry of a slab-launch instantiation (kernels_slab.cu), or null.

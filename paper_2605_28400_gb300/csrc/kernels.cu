@@ -80,19 +80,35 @@ __global__ void __launch_bounds__(32) walk_kernel(const WalkParams p) {
   uint8_t* row2 = row1 + cap;
   const uint32_t* codes = p.codes + d.code_off;
   const int T = p.T_slab > 0 ? p.T_slab : d.T, i_lo = p.i_lo;
+  const bool global = p.atype == kGlobal, local = p.atype == kLocal;
   int i = a, j = b, k = c, n = 0, bad = 0;
   if (p.state && !p.init_state) {  // a linear-space traceback resumes where the slab above left it
     i = p.state[4 * q];
     j = p.state[4 * q + 1];
     k = p.state[4 * q + 2];
     n = p.state[4 * q + 3];
+  } else if (!global) {  // semi-global / local: the first cell with the best score
+    const unsigned long long key = p.best64[d.out_idx];
+    const unsigned long long lin = ((1ull << 37) - 1) - (key & ((1ull << 37) - 1));
+    const unsigned long long bc = (unsigned long long)(b + 1) * (unsigned long long)(c + 1);
+    i = (int)(lin / bc);
+    j = (int)((lin % bc) / (unsigned long long)(c + 1));
+    k = (int)(lin % (unsigned long long)(c + 1));
+    if (lane == 0) p.scores[d.out_idx] = (int)(key >> 37) - (1 << 26);
+    if (key == 0 || i > a || j > b || k > c) bad = 1;
   }
-  while ((i | j | k) != 0 && i >= i_lo && !bad) {
+  const int ei = i, ej = j, ek = k;  // end cell of the alignment (for the span)
+  // start cells: the origin (global), any axis cell (semi-global, local)
+  const auto start = [&](int ii, int jj, int kk) {
+    return global ? (ii | jj | kk) == 0 : (ii == 0) + (jj == 0) + (kk == 0) >= 2;
+  };
+  int done = start(i, j, k);
+  while (!done && i >= i_lo && !bad) {
     const int i0 = i, j0 = j, k0 = k;
     tube_load<W>(win, i0, j0, k0, lj, lk, codes, d, T, i_lo, lane);
     __syncwarp();
     if (lane == 0) {
-      while ((i | j | k) != 0 && i >= i_lo) {
+      while (!done && i >= i_lo) {
         const int sx = i0 - i;
         if (sx >= kTubeS) break;
         const int dr = (j >> lj) - ((j0 - sx) >> lj) + 1;
@@ -101,6 +117,10 @@ __global__ void __launch_bounds__(32) walk_kernel(const WalkParams p) {
         const int e = ((j & ((1 << lj) - 1)) << lk) + (k & ((1 << lk) - 1));
         const uint32_t word = win[((sx * kTubeR + dr) * kTubeC + dc) * W + (e >> 3)];
         const int rank = (word >> code_bit(e)) & 7;
+        if (rank == 0 && local) {  // v = 0 won: the local alignment starts here
+          done = 1;
+          break;
+        }
         // rank -> move (Eq. 1 listing order, rank 7 first)
         const int di = (0xE8 >> rank) & 1, dj = (0xD4 >> rank) & 1, dk = (0xB2 >> rank) & 1;
         if (rank == 0 || n >= cap || i < di || j < dj || k < dk) {
@@ -115,6 +135,7 @@ __global__ void __launch_bounds__(32) walk_kernel(const WalkParams p) {
         j -= dj;
         k -= dk;
         ++n;
+        done = start(i, j, k);
       }
     }
     __syncwarp();
@@ -123,6 +144,7 @@ __global__ void __launch_bounds__(32) walk_kernel(const WalkParams p) {
     k = __shfl_sync(kFull, k, 0);
     n = __shfl_sync(kFull, n, 0);
     bad = __shfl_sync(kFull, bad, 0);
+    done = __shfl_sync(kFull, done, 0);
   }
   if (lane == 0) {
     if (p.state) {
@@ -134,8 +156,17 @@ __global__ void __launch_bounds__(32) walk_kernel(const WalkParams p) {
     if (bad) {
       atomicOr(p.err, 2);
       p.aln_len[q] = -1;
-    } else if ((i | j | k) == 0) {
+    } else if (done) {
       p.aln_len[q] = n;
+      if (p.span) {
+        int* sp = p.span + 6 * q;
+        sp[0] = i;
+        sp[1] = j;
+        sp[2] = k;
+        sp[3] = p.state ? a : ei;  // a slab walk ends at (a, b, c)
+        sp[4] = p.state ? b : ej;
+        sp[5] = p.state ? c : ek;
+      }
     }
   }
 }
@@ -150,7 +181,7 @@ const void* kptr() {
 const void* pick(int nj, int nk, bool tb, int at, bool pk, bool slab) {
   if (slab) return (pk || at != kGlobal) ? nullptr : wavefront_slab(nj, nk, tb);
   if (pk) return (tb || at != kGlobal) ? nullptr : wavefront_packed(nj, nk);
-  if (at != kGlobal) return tb ? nullptr : wavefront_variant(nj, nk, at);
+  if (at != kGlobal) return wavefront_variant(nj, nk, at, tb);
   if (nj == 8 && nk == 8) return tb ? kptr<8, 8, true>() : kptr<8, 8, false>();
   if (nj == 4 && nk == 8) return tb ? kptr<4, 8, true>() : kptr<4, 8, false>();
   if (nj == 4 && nk == 4) return tb ? kptr<4, 4, true>() : kptr<4, 4, false>();

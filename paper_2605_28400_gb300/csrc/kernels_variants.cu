@@ -1,28 +1,30 @@
-// kernels_variants.cu — the semi-global and local alignment types of Sec. II (score mode) of
-// the wavefront kernel (wavefront.cuh), compiled apart from the global instantiations.
+// kernels_variants.cu — the semi-global and local alignment types of Sec. II (score and
+// traceback modes) of the wavefront kernel (wavefront.cuh), compiled apart from the global
+// instantiations.
 #include "wavefront.cuh"
 
 namespace trioseq {
 
 namespace {
 
-template <int NJ, int NK, int AT>
+template <int NJ, int NK, bool TB, int AT>
 const void* vptr() {
-  return reinterpret_cast<const void*>(&wavefront_kernel<NJ, NK, false, AT, false, false>);
+  return reinterpret_cast<const void*>(&wavefront_kernel<NJ, NK, TB, AT, false, false>);
+}
+
+template <int AT>
+const void* pick_type(int nj, int nk, bool tb) {
+  if (nj == 8 && nk == 8) return tb ? vptr<8, 8, true, AT>() : vptr<8, 8, false, AT>();
+  if (nj == 4 && nk == 8) return tb ? vptr<4, 8, true, AT>() : vptr<4, 8, false, AT>();
+  if (nj == 4 && nk == 4) return tb ? vptr<4, 4, true, AT>() : vptr<4, 4, false, AT>();
+  return nullptr;
 }
 
 }  // namespace
 
-const void* wavefront_variant(int nj, int nk, int at) {
-  if (at == kSemiGlobal) {
-    if (nj == 8 && nk == 8) return vptr<8, 8, kSemiGlobal>();
-    if (nj == 4 && nk == 8) return vptr<4, 8, kSemiGlobal>();
-    if (nj == 4 && nk == 4) return vptr<4, 4, kSemiGlobal>();
-  } else if (at == kLocal) {
-    if (nj == 8 && nk == 8) return vptr<8, 8, kLocal>();
-    if (nj == 4 && nk == 8) return vptr<4, 8, kLocal>();
-    if (nj == 4 && nk == 4) return vptr<4, 4, kLocal>();
-  }
+const void* wavefront_variant(int nj, int nk, int at, bool tb) {
+  if (at == kSemiGlobal) return pick_type<kSemiGlobal>(nj, nk, tb);
+  if (at == kLocal) return pick_type<kLocal>(nj, nk, tb);
   return nullptr;
 }
 

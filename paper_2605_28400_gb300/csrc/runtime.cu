@@ -106,6 +106,8 @@ struct Workspace {
   DevBuf lens;      // alignment lengths
   DevBuf planes;    // slab mode: checkpoint planes (traceback) or two ping-pong planes (score)
   DevBuf walkstate; // slab mode: (i, j, k, n) of the traceback walk between slabs
+  DevBuf best64;    // semi-global / local traceback: (score, first cell) key per triplet
+  DevBuf spans;     // traceback: begin and end cell of each alignment (6 int32)
   HostPinned staging;
   cudaStream_t alloc_stream = nullptr;  // grow buffers in this stream's order (serving slots)
 };
@@ -189,6 +191,7 @@ struct trioseq_batch_s {
   // results of the last run (host)
   std::vector<uint8_t> h_rows;
   std::vector<int32_t> h_lens;
+  std::vector<int32_t> h_spans;  // 6 per traceback request
   bool have_rows = false;
   // optional per-kernel timing (events on the launching stream)
   bool profile = false;
@@ -238,7 +241,6 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
   if (!trip && n) return TRIOSEQ_EINVAL;
   if (mode > TRIOSEQ_WITH_TRACEBACK) return TRIOSEQ_EINVAL;
   const bool tb = mode == TRIOSEQ_WITH_TRACEBACK;
-  if (tb && plan->atype != kGlobal) return TRIOSEQ_ENOTIMPL;  // variants are score-only
   bt->plan = plan;
   bt->n = n;
   bt->mode = mode;
@@ -301,6 +303,10 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
             sumlen >= (1LL << 26) - 1)
       return TRIOSEQ_EOVERFLOW;
     if (2LL * (int64_t)std::abs(plan->gap) * sumlen >= (1LL << 30)) return TRIOSEQ_EOVERFLOW;
+    // semi-global / local traceback: the best cell's index must fit 37 bits (engine.h, best64)
+    if (tb && plan->atype != kGlobal &&
+        (double)(d.len[0] + 1) * (d.len[1] + 1) * (d.len[2] + 1) >= (double)(1ULL << 37))
+      return TRIOSEQ_EOVERFLOW;
     d.pair = -1;
     d.score_base = 2 * plan->gap * (int32_t)sumlen;
     d.out_idx = (int32_t)t;
@@ -499,6 +505,8 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
   return TRIOSEQ_OK;
 }
 
+int plan_atype(const trioseq_batch_s* bt) { return bt->plan->atype; }
+
 // Size the workspace and copy the inputs of `bt` into it (stream-ordered).
 // `pinned`: stage through the workspace's pinned buffer and copy asynchronously on `st` (the
 // per-call path); otherwise copy synchronously from pageable memory (one-off batch creation).
@@ -516,6 +524,10 @@ trioseq_status upload(trioseq_batch_s* bt, cudaStream_t st, bool pinned) {
               !ws.lens.ensure(std::max<size_t>(bt->tb_trips.size(), 1) * sizeof(int32_t), as))) ||
       (bt->nplanes && !ws.planes.ensure(bt->nplanes * bt->plane_ints * sizeof(int32_t), as)) ||
       (bt->slab && tb && !ws.walkstate.ensure(4 * sizeof(int32_t), as)) ||
+      (tb && !ws.spans.ensure(std::max<size_t>(bt->tb_trips.size(), 1) * 6 * sizeof(int32_t),
+                              as)) ||
+      (tb && plan_atype(bt) != kGlobal &&
+       !ws.best64.ensure(std::max<size_t>(bt->n, 1) * sizeof(unsigned long long), as)) ||
       (pinned && !ws.staging.ensure(bt->inputs_bytes)))
     return TRIOSEQ_ENOMEM;
   std::vector<char> pageable;
@@ -578,6 +590,11 @@ trioseq_status run(trioseq_batch_s* bt, cudaStream_t st) {
   p.TI = std::max(1, bt->TI);
   p.wait_ns = plan->wait_ns;
   p.g2 = -2 * plan->gap;
+  if (tb && plan->atype != kGlobal) {  // (score, first cell) keys start from 0
+    p.best64 = ws.best64.as<unsigned long long>();
+    if ((e = cudaMemsetAsync(p.best64, 0, bt->n * sizeof(unsigned long long), st)) != cudaSuccess)
+      return cuda_status(e);
+  }
   // Semi-global and local scores are maxima accumulated with atomicMax: start from 0x80808080.
   if (plan->atype != kGlobal &&
       (e = cudaMemsetAsync(p.scores, 0x80, bt->n * sizeof(int32_t), st)) != cudaSuccess)
@@ -595,6 +612,10 @@ trioseq_status run(trioseq_batch_s* bt, cudaStream_t st) {
   w.err = err;
   w.NJ = bt->var.nj;
   w.NK = bt->var.nk;
+  w.atype = plan->atype;
+  w.best64 = p.best64;
+  w.scores = p.scores;
+  w.span = tb ? ws.spans.as<int32_t>() : nullptr;
   bt->timed = false;
   if (bt->profile && record(bt->ev[0], st) != cudaSuccess)
     return cuda_status(cudaGetLastError());
@@ -716,6 +737,10 @@ trioseq_status fetch(trioseq_batch_s* bt, cudaStream_t st, int32_t* scores_out) 
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(bt->h_lens.data(), ws.lens.p, bt->h_lens.size() * sizeof(int32_t),
                             cudaMemcpyDeviceToHost, st);
+      bt->h_spans.resize(6 * bt->tb_trips.size());
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(bt->h_spans.data(), ws.spans.p, bt->h_spans.size() * sizeof(int32_t),
+                            cudaMemcpyDeviceToHost, st);
     }
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
@@ -725,7 +750,19 @@ trioseq_status fetch(trioseq_batch_s* bt, cudaStream_t st, int32_t* scores_out) 
   bt->have_rows = tb;
   bt->d2h_bytes = bt->n ? sizeof(int32_t) * (1 + bt->n) : 0;
   if (tb && !bt->tb_trips.empty())
-    bt->d2h_bytes += bt->rows_bytes + bt->h_lens.size() * sizeof(int32_t);
+    bt->d2h_bytes += bt->rows_bytes + bt->h_lens.size() * sizeof(int32_t) +
+                     bt->h_spans.size() * sizeof(int32_t);
+  return TRIOSEQ_OK;
+}
+
+trioseq_status copy_span(const trioseq_batch_s* bt, size_t idx, int32_t* begin, int32_t* end) {
+  if (!bt || !bt->have_rows || idx >= bt->n || !begin || !end) return TRIOSEQ_EINVAL;
+  const int32_t q = bt->tb_of[idx];
+  if (q < 0 || bt->h_lens[q] < 0) return TRIOSEQ_EINVAL;
+  for (int t = 0; t < 3; t++) {
+    begin[t] = bt->h_spans[6 * q + t];
+    end[t] = bt->h_spans[6 * q + 3 + t];
+  }
   return TRIOSEQ_OK;
 }
 
@@ -876,6 +913,12 @@ trioseq_status trioseq_traceback(trioseq_plan_t plan, size_t idx, char* row0, ch
   return copy_alignment(plan->last.get(), idx, row0, row1, row2, cap, aln_len);
 }
 
+trioseq_status trioseq_traceback_span(trioseq_plan_t plan, size_t idx, int32_t begin[3],
+                                      int32_t end[3]) {
+  if (!plan || !plan->last) return TRIOSEQ_EINVAL;
+  return copy_span(plan->last.get(), idx, begin, end);
+}
+
 trioseq_status trioseq_batch_create(trioseq_plan_t plan, const trioseq_triplet* triplets,
                                     size_t n, uint32_t mode, trioseq_batch_t* out) {
   if (!plan || !out) return TRIOSEQ_EINVAL;
@@ -914,6 +957,11 @@ trioseq_status trioseq_batch_device_scores(trioseq_batch_t bt, int32_t** d_score
 trioseq_status trioseq_batch_alignment(trioseq_batch_t bt, size_t idx, char* row0, char* row1,
                                        char* row2, size_t cap, size_t* aln_len) {
   return copy_alignment(bt, idx, row0, row1, row2, cap, aln_len);
+}
+
+trioseq_status trioseq_batch_span(trioseq_batch_t bt, size_t idx, int32_t begin[3],
+                                  int32_t end[3]) {
+  return copy_span(bt, idx, begin, end);
 }
 
 trioseq_status trioseq_batch_info(trioseq_batch_t bt, size_t* n, uint64_t* cells, uint64_t* tasks,
@@ -1322,7 +1370,6 @@ trioseq_status trioseq_submit(trioseq_server_t S, const trioseq_triplet* t, int3
   if ((int64_t)std::max(plan->max_abs_sig2, plan->atype != kGlobal ? -2 * plan->gap : 0) *
           sumlen >= (1LL << 26) - 1)
     return TRIOSEQ_EOVERFLOW;
-  if (mode == TRIOSEQ_WITH_TRACEBACK && plan->atype != kGlobal) return TRIOSEQ_ENOTIMPL;
   r.bytes = request_bytes(plan, mode, t->len);
   {
     std::lock_guard<std::mutex> lk(S->mu);

@@ -128,7 +128,6 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
     wavefront_kernel(const WaveParams p) {
   using G = Geom<NJ, NK>;
   static_assert(NJ % 4 == 0 && NK % 4 == 0, "tile sides must be multiples of 4");
-  static_assert(AT == kGlobal || !TB, "semi-global and local types are score-only");
   static_assert(!PACK || (!TB && AT == kGlobal), "the packed mode is global and score-only");
   static_assert(!SLAB || (!PACK && AT == kGlobal), "slab launches are global and int32");
   constexpr int NEG = PACK ? kNeg16x2 : kNeg;  // -infinity in every lane of a register
@@ -306,17 +305,30 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
     // the j axis and M'[-1][-1][k] (move (1,1,0)) for the k axis. Slice -1 of lane (0,0) is
     // its state before step 0; the other lanes meet slice -1 inside the loop.
     const int g2 = p.g2;
+    // a halo value M' in the stored form: the key 8*M' + 7 with traceback, M' itself without
+    const auto axis_feed = [](int v) { return TB ? 8 * v + 7 : v; };
     if (AT == kSemiGlobal && lane == 0) {
       if (J == 0) {
 #pragma unroll
-        for (int qq = 0; qq <= NK; ++qq) rowB[qq] = g2 * max(k0 + qq - 1, 0);
+        for (int qq = 0; qq <= NK; ++qq) rowB[qq] = axis_feed(g2 * max(k0 + qq - 1, 0));
       }
       if (K == 0) {
 #pragma unroll
-        for (int pp = 0; pp < NJ; ++pp) colB[pp] = g2 * (j0 + pp);
+        for (int pp = 0; pp < NJ; ++pp) colB[pp] = axis_feed(g2 * (j0 + pp));
       }
     }
     int best = kNeg;  // semi-global / local: best original-frame score seen by this lane
+    // With traceback also its cell: local slice and tile cell pp*NK+qq. The first best cell in
+    // (i, j, k) order is kept: a lane meets its cells in that order except for the face i = a of
+    // semi-global, read at the end, hence the explicit comparison.
+    int bestS = 0, bestE = 0;
+    const auto note = [&](int m, int sl, int e) {
+      if (m > best || (m == best && (sl < bestS || (sl == bestS && e < bestE)))) {
+        best = m;
+        bestS = sl;
+        bestE = e;
+      }
+    };
     // Semi-global: local indices of the last row j = b and the last column k = c if this lane's
     // tile holds them (only lanes of the last column tasks do).
     const int pb = b - j0, qc = c - k0;
@@ -463,12 +475,14 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
 #pragma unroll
             for (int qq = 0; qq <= NK; ++qq) {
               const int k = k0 + qq - 1;
-              rowCur[qq] = (s == -1) ? g2 * k : ((s >= 0 && k == -1) ? g2 * s : rowCur[qq]);
+              rowCur[qq] = (s == -1) ? axis_feed(g2 * k)
+                                     : ((s >= 0 && k == -1) ? axis_feed(g2 * s) : rowCur[qq]);
             }
           }
           if (K == 0 && lc == 0) {
 #pragma unroll
-            for (int pp = 0; pp < NJ; ++pp) colCur[pp] = (s == -1) ? g2 * (j0 + pp) : colCur[pp];
+            for (int pp = 0; pp < NJ; ++pp)
+              colCur[pp] = (s == -1) ? axis_feed(g2 * (j0 + pp)) : colCur[pp];
           }
         }
       }
@@ -615,10 +629,13 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
               const int w = max(d0, Myz - 3);
               int u = max(Pxy + (A[pp] - 1), Sx - 4);
               u = max(Pxz + (B[qq] - 2), u);
+              const int flc = fl + g2 * (pp + qq);       // local: M' floor of this cell
+              if (AT == kLocal) u = max(u, flc << 3);     // the v = 0 candidate, rank 0
               int v = max(w + Cv[pp][qq], u);
               v = max(v, max(Sy - 5, Sz - 6));
               const int e = pp * NK + qq;
               raw[e & 7] = v;
+              if (AT == kLocal && j0 + pp <= b0 && k0 + qq <= c0) note((v >> 3) - flc, s, e);
               Q[pp][qq] = v | 7;
               if ((e & 7) == 7) {  // pack 8 ranks: bytes via PRMT, then nibbles (code_bit)
                 const uint32_t lo = __byte_perm(__byte_perm(raw[0], raw[1], 0x0040),
@@ -712,8 +729,12 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
           for (int pp = 0; pp < NJ; ++pp)
 #pragma unroll
             for (int qq = 0; qq < NK; ++qq)
-              if ((edgeJ && pp == pb && qq <= qc) || (edgeK && qq == qc && pp <= pb))
-                best = max(best, P[pp][qq] - base - g2 * (pp + qq));
+              if ((edgeJ && pp == pb && qq <= qc) || (edgeK && qq == qc && pp <= pb)) {
+                if (TB)
+                  note((P[pp][qq] >> 3) - base - g2 * (pp + qq), s, pp * NK + qq);
+                else
+                  best = max(best, P[pp][qq] - base - g2 * (pp + qq));
+              }
         }
         if (AT == kGlobal && owns_end && s == a0 && (!SLAB || d.out_idx >= 0)) {
           int v = 0;
@@ -758,12 +779,36 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
       for (int pp = 0; pp < NJ; ++pp)
 #pragma unroll
         for (int qq = 0; qq < NK; ++qq)
-          if (pp <= pb && qq <= qc) best = max(best, P[pp][qq] - base - g2 * (pp + qq));
+          if (pp <= pb && qq <= qc) {
+            if (TB)
+              note((P[pp][qq] >> 3) - base - g2 * (pp + qq), a, pp * NK + qq);
+            else
+              best = max(best, P[pp][qq] - base - g2 * (pp + qq));
+          }
     }
-    if (AT != kGlobal) {  // the triplet's score is the max over its tasks' lanes
+    if (AT != kGlobal && !TB) {  // the triplet's score is the max over its tasks' lanes
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) best = max(best, __shfl_xor_sync(kFull, best, off));
       if (lane == 0) atomicMax(p.scores + d.out_idx, best);
+    }
+    if (AT != kGlobal && TB) {
+      // (score, first cell) of the triplet: key = (M + 2^26) << 37 | (2^37 - 1 - cell index), so
+      // the 64-bit max picks the best score and, among equals, the first cell in (i, j, k) order.
+      unsigned long long key = 0;
+      if (best != kNeg) {
+        const int pp_b = bestE / NK, qq_b = bestE % NK;
+        const unsigned long long lin =
+            ((unsigned long long)bestS * (unsigned)(b0 + 1) + (unsigned)(j0 + pp_b)) *
+                (unsigned)(c0 + 1) +
+            (unsigned)(k0 + qq_b);
+        key = ((unsigned long long)(best + (1 << 26)) << 37) | ((1ull << 37) - 1 - lin);
+      }
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(kFull, key, off);
+        key = o > key ? o : key;
+      }
+      if (lane == 0) atomicMax(p.best64 + d.out_idx, key);
     }
   }
 }

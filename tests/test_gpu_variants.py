@@ -1,8 +1,9 @@
 """GPU parity of the semi-global and local alignment types (Sec. II) against the CPU oracle.
 
-Scores are int32 and must be identical to ``oracle.align_type``. Cases span ragged multi-block
-shapes on every tile variant, empty sequences, both scoring schemes, mixed batches, the
-autotuner, and a full-size protein triplet checked through properties.
+Scores are int32 and must be identical to ``oracle.align_type``; with traceback the rows and the
+span (begin and end cell) must be identical to ``oracle.align_type_tb``. Cases span ragged
+multi-block shapes on every tile variant, empty sequences, both scoring schemes, mixed batches,
+the autotuner, and a full-size protein triplet checked through properties.
 """
 import itertools
 import os
@@ -108,17 +109,77 @@ def test_protein_exact_medium(kinds):
         B.trioseq_plan_destroy(plan)
 
 
-def test_traceback_not_built_for_variants():
-    plan = _plan(DNA, B.LOCAL)
+def _plan_tb(sc, flags, tile=None):
+    old = os.environ.get("TRIOSEQ_TB_TILE")
+    if tile:
+        os.environ["TRIOSEQ_TB_TILE"] = tile
     try:
-        with pytest.raises(B.TrioseqError) as e:
-            B.trioseq_align_batch(plan, [("ACGT", "AC", "GT")], B.WITH_TRACEBACK)
-        assert e.value.status == B.ENOTIMPL
-        with pytest.raises(B.TrioseqError) as e:
-            B.trioseq_plan(DNA.alphabet, DNA.sub, DNA.gap, 3)
-        assert e.value.status == B.EINVAL
+        return B.trioseq_plan(sc.alphabet, sc.sub, sc.gap, flags)
+    finally:
+        if old is None:
+            os.environ.pop("TRIOSEQ_TB_TILE", None)
+        else:
+            os.environ["TRIOSEQ_TB_TILE"] = old
+
+
+def rows_str(rows, sc):
+    return tuple("".join("-" if v == 255 else sc.alphabet[v] for v in row) for row in rows)
+
+
+def check_tb(plan, sc, kind, triplets):
+    got = B.trioseq_align_batch(plan, [strs(t, sc) for t in triplets], B.WITH_TRACEBACK)
+    for i, t in enumerate(triplets):
+        score, rows, beg, end = oracle.align_type_tb(*t, sc.sub, sc.gap, kind)
+        assert int(got[i]) == score, (i, [len(x) for x in t])
+        assert B.trioseq_traceback(plan, i) == rows_str(rows, sc), i
+        assert B.trioseq_traceback_span(plan, i) == (beg, end), i
+    return got
+
+
+@pytest.mark.parametrize("tile", ["4x4", "4x8", "8x8"])
+@pytest.mark.parametrize("kinds", KINDS, ids=IDS)
+def test_traceback_exact_all_tiles(kinds, tile):
+    flags, kind = kinds
+    rng = np.random.default_rng(23)
+    shapes = [(37, 70, 130), (129, 33, 65), (0, 100, 100), (100, 0, 77), (64, 64, 0),
+              (5, 60, 3), (31, 32, 63), (1, 1, 1), (0, 0, 0)]
+    dna = [rand_trip(rng, sh, 4) for sh in shapes]
+    prot = [rand_trip(rng, sh, 20) for sh in shapes[:6]]
+    for sc, trips in ((DNA, dna), (PROT, prot)):
+        plan = _plan_tb(sc, flags, tile)
+        try:
+            got = check_tb(plan, sc, kind, trips)
+            score_only = B.trioseq_align_batch(plan, [strs(t, sc) for t in trips])
+            assert got.tolist() == score_only.tolist()  # both modes give the same scores
+        finally:
+            B.trioseq_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("kinds", KINDS, ids=IDS)
+def test_traceback_tiny_shapes_and_related(kinds):
+    flags, kind = kinds
+    rng = np.random.default_rng(24)
+    trips = [rand_trip(rng, s, 4) for s in itertools.product(range(4), repeat=3)]
+    trips += synth.config2(seed=97, n=12, lo=30, hi=120).triplets
+    plan = _plan_tb(DNA, flags)
+    try:
+        check_tb(plan, DNA, kind, trips)
     finally:
         B.trioseq_plan_destroy(plan)
+
+
+def test_global_span_and_invalid_flags():
+    rng = np.random.default_rng(25)
+    t = rand_trip(rng, (30, 40, 50), 4)
+    plan = _plan_tb(DNA, B.GLOBAL)
+    try:
+        B.trioseq_align_batch(plan, [strs(t, DNA)], B.WITH_TRACEBACK)
+        assert B.trioseq_traceback_span(plan, 0) == ((0, 0, 0), (30, 40, 50))
+    finally:
+        B.trioseq_plan_destroy(plan)
+    with pytest.raises(B.TrioseqError) as e:
+        B.trioseq_plan(DNA.alphabet, DNA.sub, DNA.gap, 3)
+    assert e.value.status == B.EINVAL
 
 
 @pytest.mark.parametrize("kinds", KINDS, ids=IDS)
