@@ -102,6 +102,12 @@ struct WaveParams {
   // (M + 2^26) << 37 | (2^37 - 1 - cell index), i.e. the best score and its first cell in
   // (i, j, k) order; zeroed before launch. The walk starts there and writes the score.
   unsigned long long* best64;
+  // First-wave pacing (launches of at least two waves of tasks): queue task n < pace_n starts
+  // once task 0 (no producers, never waits) has published n * pace_T / pace_n steps at
+  // *pace_flag, spreading the first wave's starts, hence its completions, over one task
+  // duration; 0 disables.
+  int32_t pace_n, pace_T;
+  const int32_t* pace_flag;
 };
 
 struct WalkParams {

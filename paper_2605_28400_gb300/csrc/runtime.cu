@@ -139,6 +139,7 @@ struct trioseq_plan_s {
   bool graphs = true;              // trioseq_batch_run replays a captured CUDA graph
   bool packed16 = true;            // pair score-only global triplets in int16 halves if they fit
   size_t slab_budget = 0;          // bytes a one-triplet batch may use before it runs in slabs
+  bool pace = true;                // pace the first wave of multi-wave launches
   int slab_slices = 0;             // forced slab height (0: chosen from the budget)
   Variant score_variant{8, 8};
   Variant tb_variant{4, 8};
@@ -590,6 +591,13 @@ trioseq_status run(trioseq_batch_s* bt, cudaStream_t st) {
   p.TI = std::max(1, bt->TI);
   p.wait_ns = plan->wait_ns;
   p.g2 = -2 * plan->gap;
+  if (!bt->slab && plan->pace && bt->tasks.size() >= 2 * (size_t)bt->grid * kWarpsPerCta) {
+    // pace the first wave against the progress of queue task 0, the (0,0) block of its triplet
+    const TripDesc& d0 = bt->desc[bt->tasks[0].trip];
+    p.pace_n = bt->grid * kWarpsPerCta;
+    p.pace_T = d0.T;
+    p.pace_flag = prog + d0.prog_base;
+  }
   if (tb && plan->atype != kGlobal) {  // (score, first cell) keys start from 0
     p.best64 = ws.best64.as<unsigned long long>();
     if ((e = cudaMemsetAsync(p.best64, 0, bt->n * sizeof(unsigned long long), st)) != cudaSuccess)
@@ -861,6 +869,7 @@ trioseq_status trioseq_plan(const trioseq_scoring* sc, uint32_t max_len_hint, ui
   plan->TI = std::max(1, env_int("TRIOSEQ_TI", 8));
   plan->graphs = env_int("TRIOSEQ_GRAPHS", 1) != 0;
   plan->packed16 = env_int("TRIOSEQ_PACKED", 1) != 0;
+  plan->pace = env_int("TRIOSEQ_PACE", 1) != 0;
   {
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {

@@ -172,6 +172,18 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
     if (lane == 0) task = atomicAdd(p.queue, 1);
     task = __shfl_sync(kFull, task, 0);
     if (task >= p.ntasks) return;
+    if (task < p.pace_n && task > 0) {
+      // Pace the first wave (all warps grab at once otherwise, and the cohorts that finish
+      // together would grab deep producer chains together in every later wave).
+      const int need = (int)((long long)task * p.pace_T / p.pace_n);
+      bool okp = true;
+      int seen = 0;
+      if (lane == 0 && need > 0) okp = wait_flag(p.pace_flag, need, &seen, p.wait_ns);
+      if (!__shfl_sync(kFull, okp, 0)) {
+        if (lane == 0) atomicOr(p.err, 1);
+        return;
+      }
+    }
     const Task tk = p.tasks[task];
     const TripDesc& d = p.desc[tk.trip];
     const TripDesc& d1 = PACK ? p.desc[d.pair] : d;  // triplet of the high halves
