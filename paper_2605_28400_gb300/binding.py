@@ -142,19 +142,36 @@ def _as_bytes(s) -> bytes:
     return bytes(np.asarray(s, dtype=np.uint8))
 
 
+_TRIPLET_DTYPE = np.dtype({"names": ["s", "len"], "formats": [("<u8", 3), ("<u4", 3)],
+                           "offsets": [Triplet.s.offset, Triplet.len.offset],
+                           "itemsize": ctypes.sizeof(Triplet)})
+
+
 def _triplet_array(triplets):
-    """ctypes array of Triplet plus the byte objects keeping the strings alive."""
-    keep = []
-    arr = (Triplet * max(1, len(triplets)))()
-    for t, trip in enumerate(triplets):
-        if len(trip) != 3:
-            raise ValueError("a triplet has three sequences")
-        for q in range(3):
-            b = _as_bytes(trip[q])
-            keep.append(b)
-            arr[t].s[q] = b
-            arr[t].len[q] = len(b)
-    return arr, keep
+    """Triplet records (as a ctypes pointer) plus the buffers keeping the strings alive.
+
+    All sequences are joined into one buffer and the records are filled with numpy, so
+    marshalling thousands of triplets costs one copy of the residues rather than one Python
+    call per field."""
+    n = len(triplets)
+    if any(len(t) != 3 for t in triplets):
+        raise ValueError("a triplet has three sequences")
+    flat = [t[q] for t in triplets for q in range(3)]
+    if all(isinstance(x, str) for x in flat):
+        lens = np.fromiter(map(len, flat), dtype=np.uint32, count=3 * n)
+        joined = "".join(flat).encode("latin-1")  # one byte per character, as residues are
+    else:
+        parts = [_as_bytes(x) for x in flat]
+        lens = np.fromiter(map(len, parts), dtype=np.uint32, count=3 * n)
+        joined = b"".join(parts)
+    buf = ctypes.create_string_buffer(joined, max(1, len(joined)))
+    offs = np.zeros(3 * n, dtype=np.uint64)
+    if n:
+        offs[1:] = np.cumsum(lens[:-1], dtype=np.uint64)
+    rec = np.zeros(max(1, n), dtype=_TRIPLET_DTYPE)
+    rec["s"][:n] = (np.uint64(ctypes.addressof(buf)) + offs).reshape(n, 3)
+    rec["len"][:n] = lens.reshape(n, 3)
+    return rec.ctypes.data_as(ctypes.POINTER(Triplet)), (buf, rec)
 
 
 def trioseq_plan(alphabet: str, sub, gap: int, flags: int = 0):
