@@ -452,33 +452,39 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
   bt->face_ints = std::max<size_t>(face, 4);
   bt->code_words = std::max<size_t>(codes, 4);
   bt->rows_bytes = std::max<size_t>(rows, 16);
-  // queue: (anti-diagonal, LPT rank of the unit's grid, J)
+  // queue: (anti-diagonal, LPT rank of the unit's grid, J), built by counting sort on the
+  // anti-diagonal: units visited in LPT order and J ascending within a unit give the same order as
+  // a stable sort on the full key.
   const size_t nu = units.size();
-  std::vector<int32_t> lpt(n, 0);
+  std::vector<int32_t> order(nu);
+  for (size_t u = 0; u < nu; u++) order[u] = (int32_t)u;
   {
-    std::vector<int32_t> order(nu);
-    for (size_t u = 0; u < nu; u++) order[u] = (int32_t)u;
     const auto vol = [&](int32_t u) {
       const TripDesc& d = bt->desc[units[u].first];
       return (double)(d.glen[0] + 1) * (d.glen[1] + 1) * (d.glen[2] + 1);
     };
     std::stable_sort(order.begin(), order.end(),
                      [&](int32_t x, int32_t y) { return vol(x) > vol(y); });
-    for (size_t r = 0; r < nu; r++) lpt[units[order[r]].first] = (int32_t)r;
   }
-  bt->tasks.clear();
-  bt->tasks.reserve((size_t)prog);
+  int maxD = 0;
+  for (const auto& un : units) {
+    const TripDesc& d = bt->desc[un.first];
+    maxD = std::max(maxD, d.nJ + d.nK - 2);
+  }
+  std::vector<size_t> start((size_t)maxD + 2, 0);
   for (const auto& un : units) {
     const TripDesc& d = bt->desc[un.first];
     for (int J = 0; J < d.nJ; J++)
-      for (int K = 0; K < d.nK; K++) bt->tasks.push_back(Task{un.first, J, K, 0});
+      for (int K = 0; K < d.nK; K++) start[(size_t)(J + K) + 1]++;
   }
-  std::stable_sort(bt->tasks.begin(), bt->tasks.end(), [&](const Task& x, const Task& y) {
-    const int dx = x.J + x.K, dy = y.J + y.K;
-    if (dx != dy) return dx < dy;
-    if (lpt[x.trip] != lpt[y.trip]) return lpt[x.trip] < lpt[y.trip];
-    return x.J < y.J;
-  });
+  for (size_t D = 1; D < start.size(); D++) start[D] += start[D - 1];
+  bt->tasks.assign((size_t)prog, Task{0, 0, 0, 0});
+  for (const int32_t u : order) {
+    const int32_t t = units[u].first;
+    const TripDesc& d = bt->desc[t];
+    for (int J = 0; J < d.nJ; J++)
+      for (int K = 0; K < d.nK; K++) bt->tasks[start[(size_t)(J + K)]++] = Task{t, J, K, 0};
+  }
   // device layout of the input block
   size_t off = align_up(bt->seq_bytes, 256);
   bt->off_desc = off;
