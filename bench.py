@@ -167,6 +167,47 @@ def triplet_strings(w):
 
 
 # ------------------------------------------------------------------------------------------
+def host_cpu() -> dict:
+    """CPU model and logical core count of the host running the oracle."""
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware") and not model:
+                    model = line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    return {"cpu": model, "nproc": os.cpu_count()}
+
+
+def cpu_all_cores_sample(triplets, sc, target_s: float = 3.0):
+    """The oracle's batch entry on every host core (independent triplets, one per thread at a
+    time), timed on a prefix of the batch sized for about target_s seconds."""
+    import oracle
+    n_cores = os.cpu_count() or 1
+    probe = triplets[:8]
+    t0 = time.perf_counter()
+    oracle.align_many(probe, sc.sub, sc.gap)
+    per_cell = (time.perf_counter() - t0) / sum(len(a) * len(b) * len(c) for a, b, c in probe)
+    budget = target_s * n_cores / per_cell
+    sample, tot = [], 0
+    for t in triplets:
+        sample.append(t)
+        tot += len(t[0]) * len(t[1]) * len(t[2])
+        if tot >= budget:
+            break
+    t0 = time.perf_counter()
+    oracle.align_many(sample, sc.sub, sc.gap, threads=n_cores)
+    dt = time.perf_counter() - t0
+    return {"value": tot / dt / 1e9, "unit": "GCUPS", "cores": n_cores, "kind": "oracle",
+            "sample": f"first {len(sample)} triplets of the batch ({tot} cells, {dt:.1f} s)",
+            "host": host_cpu()}
+
+
 def cpu_oracle_sample(w, target_cells: float, traceback: bool):
     """Time the oracle on prefixes of the workload's first triplet(s) (~target_cells cells)."""
     import oracle
@@ -193,7 +234,7 @@ def cpu_oracle_sample(w, target_cells: float, traceback: bool):
     dt = time.perf_counter() - t0
     mode = "score + traceback" if traceback else "score only"
     return {"value": cells / dt / 1e9, "unit": "GCUPS", "cores": 1, "kind": "oracle",
-            "sample": f"{desc} ({cells} cells, {mode}, {dt:.1f} s)"}, dt
+            "sample": f"{desc} ({cells} cells, {mode}, {dt:.1f} s)", "host": host_cpu()}, dt
 
 
 def run_reference(args, rank: int):
@@ -351,7 +392,7 @@ def serving_measurement(B, n_req: int = 2000, load: float = 0.7, n_cal: int = 60
                    "clipped to [50, 2000]"}
 
 
-def aux_measurements(B, torch, stream, flush, sms, clock_mhz, skip: str):
+def aux_measurements(B, torch, stream, flush, sms, clock_mhz, skip: str, cpu_legs: bool = True):
     """Secondary lines of the metric: the traceback workload (related DNA triplet n~1000, score +
     4-bit codes + walk), the semi-global and local types on the n=4000 protein triplet, the
     4096-triplet batch in one persistent launch versus one launch per triplet, and the serving
@@ -444,6 +485,7 @@ def aux_measurements(B, torch, stream, flush, sms, clock_mhz, skip: str):
         "batched_gcups": batched, "per_triplet_launch_gcups": per_triplet,
         "batched_over_per_triplet": batched / per_triplet, "identical_scores": bool(same),
         "tuned_batched": tuned_batch, "packing": packing, "kernel_ms": kb,
+        "cpu_all_cores": cpu_all_cores_sample(w.triplets, w.scoring) if cpu_legs else None,
         "roofline": {"bound": "alu", "achieved": ach_b, "peak": peak_b,
                      "unit": "TOPS (int32)" if packing == 1 else "TOPS (int16x2 lanes)",
                      "frac": ach_b / peak_b},
@@ -608,7 +650,8 @@ def main():
     B.trioseq_plan_destroy(plan)
 
     if rank == 0 and not args.no_aux:
-        line["aux"] = aux_measurements(B, torch, stream, flush, sms, clock_mhz, args.workload)
+        line["aux"] = aux_measurements(B, torch, stream, flush, sms, clock_mhz, args.workload,
+                                       not args.no_cpu)
     if rank == 0 and not args.no_cpu:
         cb, _ = cpu_oracle_sample(w, 2.5e8, tb)
         line["cpu_baseline"] = cb

@@ -32,7 +32,8 @@ def build(force: bool = False) -> str:
     with _lock:
         if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
             tmp = _LIB + f".tmp{os.getpid()}"
-            subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", _SRC, "-o", tmp])
+            subprocess.check_call(["g++", "-O2", "-std=c++17", "-pthread", "-shared", "-fPIC", _SRC,
+                                   "-o", tmp])
             os.replace(tmp, _LIB)
     return _LIB
 
@@ -59,6 +60,10 @@ def _load():
                                           ctypes.c_int64, ctypes.c_int, i32p, ctypes.c_int32,
                                           i64p]
         lib.oracle_align_many.restype = ctypes.c_int
+        lib.oracle_align_many_mt.argtypes = [u8p, i64p, ctypes.POINTER(ctypes.c_int32),
+                                             ctypes.c_int64, ctypes.c_int, i32p, ctypes.c_int32,
+                                             i64p, ctypes.c_int]
+        lib.oracle_align_many_mt.restype = ctypes.c_int
         lib.oracle_align_type.argtypes = [u8p, ctypes.c_int, u8p, ctypes.c_int, u8p, ctypes.c_int,
                                           ctypes.c_int, i32p, ctypes.c_int32, ctypes.c_int, i64p]
         lib.oracle_align_type.restype = ctypes.c_int
@@ -147,8 +152,9 @@ def nw2(x, y, sub, gap: int) -> int:
     return int(out.value)
 
 
-def align_many(triplets, sub, gap: int) -> np.ndarray:
-    """Scores (int64) of a list of (s0, s1, s2) triplets, one after another on one core."""
+def align_many(triplets, sub, gap: int, threads: int = 1) -> np.ndarray:
+    """Scores (int64) of a list of (s0, s1, s2) triplets: one after another on one core, or
+    spread over `threads` host threads (independent triplets, the same per-triplet DP)."""
     lib = _load()
     seqs = [np.asarray(s, dtype=np.uint8) for t in triplets for s in t]
     lens = np.array([len(s) for s in seqs], dtype=np.int32)
@@ -158,9 +164,15 @@ def align_many(triplets, sub, gap: int) -> np.ndarray:
     codes = _u8(np.concatenate(seqs) if seqs else [])
     sm, K = _sub(sub)
     out = np.zeros(len(triplets), dtype=np.int64)
-    rc = lib.oracle_align_many(_ptr(codes, ctypes.c_uint8), _ptr(offs, ctypes.c_int64),
-                               _ptr(lens, ctypes.c_int32), len(triplets), K,
-                               _ptr(sm, ctypes.c_int32), int(gap), _ptr(out, ctypes.c_int64))
+    if threads > 1:
+        rc = lib.oracle_align_many_mt(_ptr(codes, ctypes.c_uint8), _ptr(offs, ctypes.c_int64),
+                                      _ptr(lens, ctypes.c_int32), len(triplets), K,
+                                      _ptr(sm, ctypes.c_int32), int(gap),
+                                      _ptr(out, ctypes.c_int64), int(threads))
+    else:
+        rc = lib.oracle_align_many(_ptr(codes, ctypes.c_uint8), _ptr(offs, ctypes.c_int64),
+                                   _ptr(lens, ctypes.c_int32), len(triplets), K,
+                                   _ptr(sm, ctypes.c_int32), int(gap), _ptr(out, ctypes.c_int64))
     if rc:
         raise RuntimeError(f"oracle_align_many failed ({rc})")
     return out

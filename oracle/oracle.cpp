@@ -20,11 +20,13 @@
 // Arithmetic is int64 throughout, so it cannot overflow for any input the library accepts.
 // Residues are codes 0..K-1; in emitted alignment rows, the gap is ORACLE_GAP (255).
 
+#include <algorithm>
+#include <atomic>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <thread>
 #include <vector>
-#include <algorithm>
 
 namespace {
 
@@ -355,6 +357,27 @@ int oracle_align_many(const uint8_t* codes, const int64_t* offs, const int32_t* 
     if (rc) return rc;
   }
   return 0;
+}
+
+// The same on `nthreads` host threads: independent triplets, taken one at a time from a shared
+// counter (the plain per-triplet DP above, run concurrently). Used for the all-core CPU baseline.
+int oracle_align_many_mt(const uint8_t* codes, const int64_t* offs, const int32_t* lens, int64_t n,
+                         int K, const int32_t* sub, int32_t gap, int64_t* scores, int nthreads) {
+  std::atomic<int64_t> next{0};
+  std::atomic<int> rc{0};
+  const auto work = [&]() {
+    for (int64_t t = next++; t < n; t = next++) {
+      const int r = oracle_align(codes + offs[3 * t], lens[3 * t], codes + offs[3 * t + 1],
+                                 lens[3 * t + 1], codes + offs[3 * t + 2], lens[3 * t + 2], K,
+                                 sub, gap, &scores[t], nullptr, 0, nullptr);
+      if (r) rc = r;
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int i = 1; i < std::max(1, nthreads); i++) pool.emplace_back(work);
+  work();
+  for (auto& th : pool) th.join();
+  return rc;
 }
 
 }  // extern "C"

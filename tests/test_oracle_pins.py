@@ -251,3 +251,10 @@ def test_align_many_matches_single():
     got = oracle.align_many(w.triplets, w.scoring.sub, w.scoring.gap)
     want = [oracle.align(*t, w.scoring.sub, w.scoring.gap) for t in w.triplets]
     assert got.tolist() == want
+
+
+def test_align_many_threads_match_one_core():
+    w = synth.config2(seed=12, n=40, lo=20, hi=60)
+    one = oracle.align_many(w.triplets, DNA.sub, DNA.gap)
+    many = oracle.align_many(w.triplets, DNA.sub, DNA.gap, threads=4)
+    assert one.tolist() == many.tolist()
