@@ -170,6 +170,14 @@ def triplet_strings(w):
 def host_cpu() -> dict:
     """CPU model and logical core count of the host running the oracle."""
     model = ""
+    try:  # lscpu names Arm cores (Neoverse-V2 on Grace); /proc/cpuinfo there does not
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
     try:
         with open("/proc/cpuinfo") as fh:
             for line in fh:
