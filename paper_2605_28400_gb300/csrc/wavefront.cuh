@@ -499,7 +499,9 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
         }
       }
 
-      if (s >= 0 && s <= a) {
+      const bool active = s >= 0 && s <= a;
+      uint32_t cw[W];
+      if (active) {
         int A[NJ], B[NK];
         {
           const int xl = PACK ? (x & 0xff) : x;
@@ -545,7 +547,6 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
         }
         // Global and semi-global score kernels: two passes (below); the local type and the
         // traceback keys: one pass over the cells with a second tile Q.
-        uint32_t cw[W];
         if constexpr (!TB && AT != kLocal) {
           // Two passes, both in place in P, so no second tile and no copy-back:
           //  pass 1 (anti-diagonals in decreasing order) replaces P (slice s-1) by
@@ -693,7 +694,16 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
 #pragma unroll
             for (int qq = 0; qq < NK; ++qq) P[pp][qq] = Q[pp][qq];
         }
-
+      }
+      // Publish progress t (steps < t computed and stored) between this step's compute and its
+      // stores: the release then waits only for the previous step's stores, issued a whole step
+      // of compute ago, instead of the ones just issued.
+      if (--pub_in == 0) {
+        pub_in = p.TI;
+        __syncwarp();
+        if (lane == 0) st_release(progMe, t);
+      }
+      if (active) {
         if (TB && (!SLAB || code_base)) {
           uint32_t* dst = code_base + (int64_t)t * 32 * W;
           if (W % 4 == 0) {
@@ -768,11 +778,6 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
           p.scores[d1.out_idx] = (v >> 16) + d1.score_base;  // high half, sign-extended
         }
       }
-      if (--pub_in == 0 || t + 1 == T) {
-        pub_in = p.TI;
-        __syncwarp();
-        if (lane == 0) st_release(progMe, t + 1);
-      }
       return true;
     };
     for (int t = 0; t < T; t += 2) {
@@ -780,6 +785,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
       if (t + 1 < T && !step(t + 1, rowB, rowA, colB, colA)) break;
     }
     __syncwarp();
+    if (ok && lane == 0) st_release(progMe, T);  // all steps computed and stored
     if (!ok) {
       if (lane == 0) atomicOr(p.err, 1);
       return;
