@@ -108,6 +108,7 @@ struct WaveParams {
   // duration; 0 disables.
   int32_t pace_n, pace_T;
   const int32_t* pace_flag;
+  int32_t one;         // 1, as a launch argument (multiply-adds by it stay on the FMA pipe)
 };
 
 struct WalkParams {

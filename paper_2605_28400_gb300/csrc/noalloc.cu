@@ -223,6 +223,7 @@ extern "C" trioseq_status trioseq_align_noalloc(const trioseq_scoring* sc,
   p.err = prog + L.ntasks + 32;
   p.TI = 8;
   p.g2 = -2 * sc->gap;
+  p.one = 1;
   p.wait_ns = 2000000000LL;
   if (launch_wavefront(kNoallocNJ, kNoallocNK, false, kGlobal, false, false, p, sms * bpm, smem,
                        st) != 0) {

@@ -597,6 +597,7 @@ trioseq_status run(trioseq_batch_s* bt, cudaStream_t st) {
   p.TI = std::max(1, bt->TI);
   p.wait_ns = plan->wait_ns;
   p.g2 = -2 * plan->gap;
+  p.one = 1;
   if (!bt->slab && plan->pace && bt->tasks.size() >= 2 * (size_t)bt->grid * kWarpsPerCta) {
     // pace the first wave against the progress of queue task 0, the (0,0) block of its triplet
     const TripDesc& d0 = bt->desc[bt->tasks[0].trip];
