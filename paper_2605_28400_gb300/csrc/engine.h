@@ -36,6 +36,9 @@ constexpr int kGlobal = 0, kSemiGlobal = 1, kLocal = 2;
 // and the sentinel never wins against a finite candidate.
 constexpr int kNeg16 = -(1 << 14);
 constexpr int kNeg16x2 = (int)0xC000C000u;  // kNeg16 in both halves
+// Biased packed mode (all sigma'' >= 0): a half stores M' + 2^14; -infinity is 0, M' = 0 is
+// kBias16x2. Real M' are >= 0 there, so real halves are >= 2^14 and every sum stays below 2^16.
+constexpr int kBias16x2 = 0x40004000;
 
 // Rank of each move in the tie-break (Eq. 1 listing order): rank 7 wins ties over rank 6 ...
 // rank -> (di, dj, dk):
@@ -139,14 +142,15 @@ struct WalkParams {
 // semi-global and local exist for score mode (tb = false) only, and their scores are
 // accumulated with atomicMax, so the score array must hold INT_MIN-like values before launch.
 // `slab` selects the slab-launch instantiations (global type, int32, either mode).
-int launch_wavefront(int nj, int nk, bool tb, int at, bool pk, bool slab, const WaveParams& p,
+// `pk` is the packed mode: 0 int32, 1 signed int16x2, 2 biased unsigned int16x2.
+int launch_wavefront(int nj, int nk, bool tb, int at, int pk, bool slab, const WaveParams& p,
                      int grid, size_t smem, void* stream);
-int wavefront_occupancy(int nj, int nk, bool tb, int at, bool pk, bool slab, size_t smem,
+int wavefront_occupancy(int nj, int nk, bool tb, int at, int pk, bool slab, size_t smem,
                         int* blocks_per_sm);
 // Kernel entry of a semi-global or local instantiation (kernels_variants.cu), or null.
 const void* wavefront_variant(int nj, int nk, int at, bool tb);
 // Kernel entry of a packed int16x2 (global, score) instantiation (kernels_packed.cu), or null.
-const void* wavefront_packed(int nj, int nk);
+const void* wavefront_packed(int nj, int nk, int mode);
 // Kernel entry of a slab-launch instantiation (kernels_slab.cu), or null.
 const void* wavefront_slab(int nj, int nk, bool tb);
 int launch_walk(const WalkParams& p, void* stream);

@@ -175,12 +175,12 @@ namespace {
 
 template <int NJ, int NK, bool TB>
 const void* kptr() {
-  return reinterpret_cast<const void*>(&wavefront_kernel<NJ, NK, TB, kGlobal, false, false>);
+  return reinterpret_cast<const void*>(&wavefront_kernel<NJ, NK, TB, kGlobal, 0, false>);
 }
 
-const void* pick(int nj, int nk, bool tb, int at, bool pk, bool slab) {
+const void* pick(int nj, int nk, bool tb, int at, int pk, bool slab) {
   if (slab) return (pk || at != kGlobal) ? nullptr : wavefront_slab(nj, nk, tb);
-  if (pk) return (tb || at != kGlobal) ? nullptr : wavefront_packed(nj, nk);
+  if (pk) return (tb || at != kGlobal) ? nullptr : wavefront_packed(nj, nk, pk);
   if (at != kGlobal) return wavefront_variant(nj, nk, at, tb);
   if (nj == 8 && nk == 8) return tb ? kptr<8, 8, true>() : kptr<8, 8, false>();
   if (nj == 4 && nk == 8) return tb ? kptr<4, 8, true>() : kptr<4, 8, false>();
@@ -199,7 +199,7 @@ size_t wavefront_smem_bytes(int nj, int nk, int KP, bool pk) {
          sizeof(int);
 }
 
-int wavefront_occupancy(int nj, int nk, bool tb, int at, bool pk, bool slab, size_t smem,
+int wavefront_occupancy(int nj, int nk, bool tb, int at, int pk, bool slab, size_t smem,
                         int* blocks_per_sm) {
   const void* k = pick(nj, nk, tb, at, pk, slab);
   if (!k) return -1;
@@ -212,7 +212,7 @@ int wavefront_occupancy(int nj, int nk, bool tb, int at, bool pk, bool slab, siz
   return 0;
 }
 
-int launch_wavefront(int nj, int nk, bool tb, int at, bool pk, bool slab, const WaveParams& p,
+int launch_wavefront(int nj, int nk, bool tb, int at, int pk, bool slab, const WaveParams& p,
                      int grid, size_t smem, void* stream) {
   const void* k = pick(nj, nk, tb, at, pk, slab);
   if (!k) return -1;

@@ -9,7 +9,7 @@ namespace {
 
 template <int NJ, int NK, bool TB>
 const void* sptr() {
-  return reinterpret_cast<const void*>(&wavefront_kernel<NJ, NK, TB, kGlobal, false, true>);
+  return reinterpret_cast<const void*>(&wavefront_kernel<NJ, NK, TB, kGlobal, 0, true>);
 }
 
 }  // namespace

@@ -9,7 +9,7 @@ namespace {
 
 template <int NJ, int NK, bool TB, int AT>
 const void* vptr() {
-  return reinterpret_cast<const void*>(&wavefront_kernel<NJ, NK, TB, AT, false, false>);
+  return reinterpret_cast<const void*>(&wavefront_kernel<NJ, NK, TB, AT, 0, false>);
 }
 
 template <int AT>

@@ -138,6 +138,7 @@ struct trioseq_plan_s {
   int64_t wait_ns = 2000000000LL;  // 2 s without progress = give up
   bool graphs = true;              // trioseq_batch_run replays a captured CUDA graph
   bool packed16 = true;            // pair score-only global triplets in int16 halves if they fit
+  bool sig2_nonneg = false;        // every sigma'' >= 0: the biased packed mode applies
   size_t slab_budget = 0;          // bytes a one-triplet batch may use before it runs in slabs
   bool pace = true;                // pace the first wave of multi-wave launches
   int slab_slices = 0;             // forced slab height (0: chosen from the budget)
@@ -182,7 +183,7 @@ struct trioseq_batch_s {
   int grid = 0;
   size_t smem = 0;
   int TI = 8;  // progress-publication interval of this batch's launches
-  bool packed = false;  // packed int16x2 mode: two triplets per column task
+  int packed = 0;  // packed int16x2 mode (0: none, 1: signed, 2: biased): two triplets per task
   // Slab mode (one triplet whose records, or codes, would not fit at once): the cube runs as
   // nslab launches of `slab` slices, chained through planes of plane_ints int32 each.
   int slab = 0, nslab = 0;
@@ -320,9 +321,10 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
   //    Packing needs every value of the pair's grid within the int16 margin of engine.h:
   //    max|sigma''| * (a+b+c + 3) < 2^14 on the grid's lengths.
   std::vector<std::pair<int32_t, int32_t>> units;  // (low-half triplet, high-half triplet or -1)
-  bt->packed = false;
+  bt->packed = 0;
+  const int pmode = plan->sig2_nonneg ? 2 : 1;
   if (!tb && plan->atype == kGlobal && plan->packed16 && n >= 2 &&
-      wavefront_packed(NJ, NK) != nullptr) {
+      wavefront_packed(NJ, NK, pmode) != nullptr) {
     std::vector<int32_t> order(n);
     for (size_t t = 0; t < n; t++) order[t] = (int32_t)t;
     const auto cls = [&](int32_t t) {
@@ -341,7 +343,7 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
       units.emplace_back(t0, t1);
     }
     if (fits) {
-      bt->packed = true;
+      bt->packed = pmode;
     } else {
       units.clear();
     }
@@ -501,7 +503,7 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
   off = align_up(off + sizeof(int32_t) * std::max<size_t>(bt->row_cap.size(), 1), 256);
   bt->inputs_bytes = off;
   // launch shape
-  bt->smem = wavefront_smem_bytes(NJ, NK, plan->KP, bt->packed);
+  bt->smem = wavefront_smem_bytes(NJ, NK, plan->KP, bt->packed != 0);
   int bpm = 0;
   if (wavefront_occupancy(NJ, NK, tb, plan->atype, bt->packed, bt->slab > 0, bt->smem, &bpm) !=
           0 ||
@@ -858,15 +860,17 @@ trioseq_status trioseq_plan(const trioseq_scoring* sc, uint32_t max_len_hint, ui
   }
   const int KP = K + 1;
   std::vector<int32_t> s2((size_t)KP * KP, 0), s8((size_t)KP * KP, 0);
-  int32_t mx = 0;
+  int32_t mx = 0, mn = 0;
   for (int i = 0; i < K; i++)
     for (int j = 0; j < K; j++) {
       const int32_t v = (int32_t)sc->sub[i * K + j] - 2 * sc->gap;  // sigma'' = sigma - 2 alpha
       s2[(size_t)i * KP + j] = v;
       s8[(size_t)i * KP + j] = 8 * v;
       mx = std::max(mx, std::abs(v));
+      mn = std::min(mn, v);
     }
   plan->max_abs_sig2 = std::max(mx, 1);
+  plan->sig2_nonneg = mn >= 0;
   if (!plan->sig_score.ensure(s2.size() * 4) || !plan->sig_tb.ensure(s8.size() * 4))
     return TRIOSEQ_ENOMEM;
   if (cudaMemcpy(plan->sig_score.p, s2.data(), s2.size() * 4, cudaMemcpyHostToDevice) !=

@@ -125,19 +125,24 @@ struct Geom {
 // cannot see that order and may warn (#549) without cause.
 #pragma nv_diag_suppress 549
 // AT selects the alignment type of Sec. II (kGlobal, kSemiGlobal, kLocal; engine.h); the
-// semi-global and local types are built for score mode only. PACK = true is the packed int16x2
+// semi-global and local types are built for score mode only. PACK != 0 is the packed int16x2
 // mode (engine.h): the triplet of descriptor d in the low halves, that of d.pair in the high
-// halves, on the task grid of their maximal lengths (global type, score only). SLAB = true builds
+// halves, on the task grid of their maximal lengths (global type, score only). PACK = 1 keeps
+// signed halves (DPX s16x2 add-max, adds from -infinity clamped); PACK = 2, for scoring schemes
+// whose sigma'' are all >= 0, keeps each half as M' + 2^14 (-infinity = 0): every half then stays
+// in 0 .. 2^16 - 1 through the adds, so a plain 32-bit add is the two 16-bit adds and the diagonal
+// sum goes to the FMA pipe, with the unsigned u16x2 add-max for the rest. SLAB = true builds
 // the slab launches of one triplet (global type, int32; WaveParams i0 / plane_in / plane_out):
 // a kept apart so that the regular instantiations carry none of its registers.
-template <int NJ, int NK, bool TB, int AT, bool PACK, bool SLAB>
+template <int NJ, int NK, bool TB, int AT, int PACK, bool SLAB>
 __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::value)
     wavefront_kernel(const WaveParams p) {
   using G = Geom<NJ, NK>;
   static_assert(NJ % 4 == 0 && NK % 4 == 0, "tile sides must be multiples of 4");
   static_assert(!PACK || (!TB && AT == kGlobal), "the packed mode is global and score-only");
   static_assert(!SLAB || (!PACK && AT == kGlobal), "slab launches are global and int32");
-  constexpr int NEG = PACK ? kNeg16x2 : kNeg;  // -infinity in every lane of a register
+  // -infinity in every lane of a register
+  constexpr int NEG = PACK == 1 ? kNeg16x2 : (PACK == 2 ? 0 : kNeg);
   static_assert(G::NCOPY <= 32, "one staged piece per lane per step");
   constexpr int WJ = G::WJ, WK = G::WK, W = G::W;
   extern __shared__ int4 smem4[];
@@ -294,7 +299,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
       rowB[qq] = NEG;
     }
     // M'[-1][-1][-1] = 0 feeds the origin through the (1,1,1) move (stored as 8*0+7 with keys).
-    if (J == 0 && K == 0 && lane == 0) rowB[0] = TB ? 7 : 0;
+    if (J == 0 && K == 0 && lane == 0) rowB[0] = TB ? 7 : (PACK == 2 ? kBias16x2 : 0);
     const int PW = nK * WK;  // row stride of a slab plane
     if (SLAB && p.plane_in) {
       // Slab launch: the state before the first slice is slice i0 - 1 of the cube. Every lane's
@@ -571,7 +576,14 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
             const int Pxy = (pp == 0) ? rowPrev[qq + 1] : P[pp - 1][qq];
             const int Pxz = (qq == 0) ? colPrev[pp] : P[pp][qq - 1];
             const int Sx = P[pp][qq];
-            if constexpr (PACK) {
+            if constexpr (PACK == 2) {
+              // Biased halves: the 32-bit multiply-adds are the two 16-bit adds (no carry out of
+              // the low half, engine.h), then unsigned per-half max(a + b, c).
+              const unsigned x2 = (unsigned)mad_lo(B[qq], p.one, mad_lo(A[pp], p.one, Pd));
+              unsigned e = __viaddmax_u16x2((unsigned)Pxy, (unsigned)A[pp], (unsigned)Sx);
+              e = __viaddmax_u16x2((unsigned)Pxz, (unsigned)B[qq], e);
+              P[pp][qq] = (int)__viaddmax_u16x2(x2, (unsigned)Cv[pp][qq], e);
+            } else if constexpr (PACK == 1) {
               // Per 16-bit half: max(a + b, c). Sums from a -infinity operand are clamped at
               // kNeg16, so nothing wraps.
               const unsigned neg = (unsigned)kNeg16x2;
@@ -595,7 +607,11 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
                 (pp == 0) ? rowCur[qq] : (qq == 0 ? colCur[pp - 1] : P[pp - 1][qq - 1]);
             const int Sy = (pp == 0) ? rowCur[qq + 1] : P[pp - 1][qq];
             const int Sz = (qq == 0) ? colCur[pp] : P[pp][qq - 1];
-            if constexpr (PACK) {
+            if constexpr (PACK == 2) {
+              const unsigned q =
+                  __viaddmax_u16x2((unsigned)Myz, (unsigned)Cv[pp][qq], (unsigned)P[pp][qq]);
+              P[pp][qq] = (int)__vimax3_u16x2(q, (unsigned)Sy, (unsigned)Sz);
+            } else if constexpr (PACK == 1) {
               const unsigned q =
                   __viaddmax_s16x2((unsigned)Myz, (unsigned)Cv[pp][qq], (unsigned)P[pp][qq]);
               P[pp][qq] = (int)__vimax3_s16x2(q, (unsigned)Sy, (unsigned)Sz);
@@ -775,7 +791,8 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
 #pragma unroll
             for (int qq = 0; qq < NK; ++qq)
               if (pp == end_p && qq == end_q) v = P[pp][qq];
-          if (PACK) v = (int)(short)(v & 0xffff);  // low half, sign-extended
+          if (PACK == 1) v = (int)(short)(v & 0xffff);    // low half, sign-extended
+          if (PACK == 2) v = (v & 0xffff) - (1 << 14);   // low half, unbiased
           p.scores[d.out_idx] = (TB ? (v >> 3) : v) + d.score_base;
         }
         if (PACK && owns_end1 && s == a1) {
@@ -785,7 +802,8 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
 #pragma unroll
             for (int qq = 0; qq < NK; ++qq)
               if (pp == end_p1 && qq == end_q1) v = P[pp][qq];
-          p.scores[d1.out_idx] = (v >> 16) + d1.score_base;  // high half, sign-extended
+          const int hi = PACK == 2 ? (int)((unsigned)v >> 16) - (1 << 14) : (v >> 16);
+          p.scores[d1.out_idx] = hi + d1.score_base;  // high half
         }
       }
       return true;
