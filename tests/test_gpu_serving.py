@@ -97,3 +97,40 @@ def test_server_rejects_bad_requests():
     finally:
         B.trioseq_server_destroy(srv)
         B.trioseq_plan_destroy(plan)
+
+
+def test_variant_plans_served_with_traceback():
+    # a server over a local-type DNA plan and a semi-global protein plan, traceback requests
+    # included: every result equals the oracle's alignment of its type
+    dna, prot = synth.dna_scoring(), synth.protein_scoring(1005)
+    plans = [B.trioseq_plan(dna.alphabet, dna.sub, dna.gap, B.LOCAL),
+             B.trioseq_plan(prot.alphabet, prot.sub, prot.gap, B.SEMIGLOBAL)]
+    kinds = [oracle.LOCAL, oracle.SEMIGLOBAL]
+    rng = np.random.default_rng(8)
+    reqs = []
+    for i in range(24):
+        pid = i % 2
+        sc = prot if pid else dna
+        trip = tuple(rng.integers(0, sc.sub.shape[0], size=int(rng.integers(5, 90))).astype(
+            np.uint8) for _ in range(3))
+        reqs.append((pid, bool(i % 3 == 0), trip, sc))
+    srv = B.trioseq_server_create(plans)
+    try:
+        tickets = []
+        for pid, tb, trip, sc in reqs:
+            st, tk = B.trioseq_submit(srv, [synth.to_str(s, sc.alphabet) for s in trip], pid,
+                                      B.WITH_TRACEBACK if tb else B.SCORE_ONLY)
+            assert st == B.OK
+            tickets.append(tk)
+        got = _poll_all(srv, tickets, 3 * 100)
+    finally:
+        B.trioseq_server_destroy(srv)
+        for p in plans:
+            B.trioseq_plan_destroy(p)
+    for (pid, tb, trip, sc), tk in zip(reqs, tickets):
+        score, rows, _, _ = oracle.align_type_tb(*trip, sc.sub, sc.gap, kinds[pid])
+        got_score, got_rows = got[tk]
+        assert got_score == score
+        if tb:  # an empty alignment comes back as no rows
+            assert (got_rows or ("", "", "")) == tuple(
+                "".join("-" if v == 255 else sc.alphabet[v] for v in r) for r in rows)
