@@ -40,6 +40,12 @@ __device__ __forceinline__ int ld_relaxed(const int* p) {
   return v;
 }
 
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 __device__ __forceinline__ void fence_acq_rel() {
   asm volatile("fence.acq_rel.gpu;" ::: "memory");
 }
@@ -54,13 +60,13 @@ __device__ __forceinline__ uint64_t global_ns() {
   return t;
 }
 
-// Lane-0 wait until *flag >= need. `cached` keeps the last value seen. Polls with relaxed loads
-// and exponential back-off (light on L2 while many warps wait); the fence after the satisfying
-// load makes it an acquire. Gives up (returns false) when the flag has not moved for wait_ns.
+// Lane-0 wait until *flag >= need. `cached` keeps the last value seen. Polls with acquire loads
+// (the satisfying one orders the record loads that follow; unlike a fence it does not wait for
+// this warp's own record stores in flight) and exponential back-off, light on L2 while many
+// warps wait. Gives up (returns false) when the flag has not moved for wait_ns.
 __device__ __noinline__ bool wait_flag(const int* flag, int need, int* cached, int64_t wait_ns) {
-  int v = ld_relaxed(flag);
+  int v = ld_acquire(flag);
   if (v >= need) {
-    fence_acq_rel();
     *cached = v;
     return true;
   }
@@ -70,9 +76,8 @@ __device__ __noinline__ bool wait_flag(const int* flag, int need, int* cached, i
   for (;;) {
     __nanosleep(ns);
     if (ns < 1024) ns <<= 1;
-    v = ld_relaxed(flag);
+    v = ld_acquire(flag);
     if (v >= need) {
-      fence_acq_rel();
       *cached = v;
       return true;
     }
