@@ -1,28 +1,56 @@
 // kernels.cu — sm_103a kernels of the 3-way alignment engine: the global-alignment
 // instantiations of the wavefront kernel (wavefront.cuh), the traceback walk, and the launchers.
 //
-// walk_kernel: one warp per traceback request. Lane 0 follows the stored moves back from
-//   (a, b, c) through a tube of code records along the diagonal, staged in shared memory by the
-//   whole warp in one round trip; repeated until the origin. In the linear-space traceback the
-//   codes hold one slab of slices at a time: the walk resumes from a saved (i, j, k, n) and stops
-//   when it leaves the slab.
+// walk_kernel: one warp per traceback request. The warp follows the stored moves back from
+//   (a, b, c) through a tube of code records along the diagonal, staged in shared memory in one
+//   round trip; runs of diagonal moves are found and emitted 32 cells at a time. In the
+//   linear-space traceback the codes hold one slab of slices at a time: the walk resumes from a
+//   saved (i, j, k, n) and stops when it leaves the slab.
 #include "wavefront.cuh"
 
 namespace trioseq {
 // ---------------------------------------------------------------------------------------------
 // Traceback walk. Optimal paths of related sequences run close to the cube's main diagonal, so
 // the warp stages a "tube" of code records along the diagonal from the current cell: for each
-// of the next kTubeS slices, the 3 x 3 lane tiles around the diagonal cell. All lanes load the
-// tube in one round trip (independent loads, then shared-memory stores); lane 0 then follows
-// the stored moves until the path leaves the tube, and the warp stages the next tube there.
-constexpr int kTubeS = 32, kTubeR = 3, kTubeC = 3;
+// of the next kTubeS slices, the 3 x 3 lane tiles around the diagonal cell, plus the window of
+// each sequence's residues that a path inside the tube can consume. All lanes load the tube in
+// one round trip (independent loads, then shared-memory stores). The walk then proceeds in
+// warp-wide probes: lane m reads the code of the cell m diagonal moves ahead, a ballot gives the
+// run of (1,1,1) moves from the current cell (at most 32), and the lanes of the run write its
+// columns at once. The first cell after the run holds a move other than (1,1,1) (applied by
+// the whole warp, one column), a start cell, or lies outside the tube, where the next tube is
+// staged. Every step is warp-uniform, so the walk carries no serial per-column chain.
+constexpr int kTubeS = 64, kTubeR = 3, kTubeC = 3;
 constexpr int kTubeRecs = kTubeS * kTubeR * kTubeC;
 constexpr int kTubePer = (kTubeRecs + 31) / 32;
+// Residue window per sequence: S0 needs the kTubeS residues above the tube's top slice; S1 (S2)
+// needs the lane-tile rows (columns) the tube spans plus one, at most
+// NJ * (floor((kTubeS - 1) / NJ) + 4) <= 88 cells for tile sides of 4 or 8.
+constexpr int kWin = 96;
+
+// First index of the S1 (S2) residue window of a tube whose top cell has index x along that
+// axis, for lane tiles of 2^l cells: one below the lowest cell of the tube's lowest tile.
+__device__ __forceinline__ int win_base(int x, int l) {
+  return ((((x - (kTubeS - 1)) >> l) - 1) << l) - 1;
+}
 
 template <int W>
-__device__ __forceinline__ void tube_load(uint32_t* win, int i0, int j0, int k0, int lj, int lk,
-                                          const uint32_t* codes, const TripDesc& d, int T,
+__device__ __forceinline__ void tube_load(uint32_t* win, uint8_t (*res)[kWin], int i0, int j0,
+                                          int k0, int lj, int lk, const uint32_t* codes,
+                                          const TripDesc& d, const int8_t* const* S, int T,
                                           int i_lo, int lane) {
+  // residue windows: res[0][m] = S0[i0 - kTubeS + m], res[1][m] = S1[win_base(j0) + m], ...
+  uint8_t rv[3][kWin / 32];
+  {
+    const int base[3] = {i0 - kTubeS, win_base(j0, lj), win_base(k0, lk)};
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+#pragma unroll
+      for (int h = 0; h < kWin / 32; ++h) {
+        const int x = base[q] + lane + 32 * h;
+        rv[q][h] = (x >= 0 && x < d.len[q]) ? (uint8_t)S[q][x] : (uint8_t)255;
+      }
+  }
   constexpr int V = (W + 3) / 4;  // 16-byte vectors per record (W = 2 uses the low half)
   uint4 v[kTubePer][V];
   bool valid[kTubePer];
@@ -50,6 +78,10 @@ __device__ __forceinline__ void tube_load(uint32_t* win, int i0, int j0, int k0,
     }
   }
 #pragma unroll
+  for (int q = 0; q < 3; ++q)
+#pragma unroll
+    for (int h = 0; h < kWin / 32; ++h) res[q][lane + 32 * h] = rv[q][h];
+#pragma unroll
   for (int u = 0; u < kTubePer; ++u) {
     if (!valid[u]) continue;
     uint32_t* dst = win + (lane + 32 * u) * W;
@@ -65,15 +97,14 @@ __device__ __forceinline__ void tube_load(uint32_t* win, int i0, int j0, int k0,
 template <int W>
 __global__ void __launch_bounds__(32) walk_kernel(const WalkParams p) {
   __shared__ uint4 win4[kTubeRecs * W / 4 + 1];
+  __shared__ uint8_t res[3][kWin];
   uint32_t* win = reinterpret_cast<uint32_t*>(win4);
   const int lane = threadIdx.x & 31;
   const int q = blockIdx.x;
   const TripDesc& d = p.desc[p.tb_trips[q]];
   const int a = d.len[0], b = d.len[1], c = d.len[2];
   const int lj = __ffs(p.NJ) - 1, lk = __ffs(p.NK) - 1;  // tile sides are powers of two
-  const int8_t* S0 = p.seq + d.s_off[0];
-  const int8_t* S1 = p.seq + d.s_off[1];
-  const int8_t* S2 = p.seq + d.s_off[2];
+  const int8_t* const S[3] = {p.seq + d.s_off[0], p.seq + d.s_off[1], p.seq + d.s_off[2]};
   const int cap = p.row_cap[q];
   uint8_t* row0 = p.rows + p.row_off[q];
   uint8_t* row1 = row0 + cap;
@@ -105,46 +136,77 @@ __global__ void __launch_bounds__(32) walk_kernel(const WalkParams p) {
   int done = start(i, j, k);
   while (!done && i >= i_lo && !bad) {
     const int i0 = i, j0 = j, k0 = k;
-    tube_load<W>(win, i0, j0, k0, lj, lk, codes, d, T, i_lo, lane);
+    tube_load<W>(win, res, i0, j0, k0, lj, lk, codes, d, S, T, i_lo, lane);
     __syncwarp();
-    if (lane == 0) {
-      while (!done && i >= i_lo) {
-        const int sx = i0 - i;
-        if (sx >= kTubeS) break;
-        const int dr = (j >> lj) - ((j0 - sx) >> lj) + 1;
-        const int dc = (k >> lk) - ((k0 - sx) >> lk) + 1;
-        if ((unsigned)dr >= (unsigned)kTubeR || (unsigned)dc >= (unsigned)kTubeC) break;
-        const int e = ((j & ((1 << lj) - 1)) << lk) + (k & ((1 << lk) - 1));
-        const uint32_t word = win[((sx * kTubeR + dr) * kTubeC + dc) * W + (e >> 3)];
-        const int rank = (word >> code_bit(e)) & 7;
-        if (rank == 0 && local) {  // v = 0 won: the local alignment starts here
-          done = 1;
-          break;
-        }
-        // rank -> move (Eq. 1 listing order, rank 7 first)
-        const int di = (0xE8 >> rank) & 1, dj = (0xD4 >> rank) & 1, dk = (0xB2 >> rank) & 1;
-        if (rank == 0 || n >= cap || i < di || j < dj || k < dk) {
-          bad = 1;
-          break;
-        }
+    // residue windows: S0[x - 1] is res[0][x - iw], and likewise for S1 and S2
+    const int iw = i0 - kTubeS + 1, jw = win_base(j0, lj) + 1, kw = win_base(k0, lk) + 1;
+    // rank of the move stored at cell (ci, cj, ck) if the tube holds it, else -1
+    const auto rank_at = [&](int ci, int cj, int ck) -> int {
+      const int sx = i0 - ci;
+      if (sx >= kTubeS || ci < i_lo || cj < 0 || ck < 0) return -1;
+      const int dr = (cj >> lj) - ((j0 - sx) >> lj) + 1;
+      const int dc = (ck >> lk) - ((k0 - sx) >> lk) + 1;
+      if ((unsigned)dr >= (unsigned)kTubeR || (unsigned)dc >= (unsigned)kTubeC) return -1;
+      const int e = ((cj & ((1 << lj) - 1)) << lk) + (ck & ((1 << lk) - 1));
+      const uint32_t word = win[((sx * kTubeR + dr) * kTubeC + dc) * W + (e >> 3)];
+      return (word >> code_bit(e)) & 7;
+    };
+    for (;;) {  // warp-uniform
+      // Lane m probes the cell m diagonal moves ahead; the run is the leading lanes whose cell
+      // holds the (1,1,1) move (rank 7) and is no start cell.
+      const int ci = i - lane, cj = j - lane, ck = k - lane;
+      const int rk = rank_at(ci, cj, ck);
+      const bool diag = rk == 7 && ci >= 1 && cj >= 1 && ck >= 1 && !start(ci, cj, ck);
+      const unsigned nd = ~__ballot_sync(kFull, diag);
+      const int run = nd ? __ffs(nd) - 1 : 32;
+      if (run > cap - n) {  // longer than the rows: corrupt codes
+        bad = 1;
+        break;
+      }
+      if (lane < run) {
+        const int pos = cap - 1 - (n + lane);
+        row0[pos] = res[0][ci - iw];
+        row1[pos] = res[1][cj - jw];
+        row2[pos] = res[2][ck - kw];
+      }
+      i -= run;
+      j -= run;
+      k -= run;
+      n += run;
+      if (start(i, j, k)) {
+        done = 1;
+        break;
+      }
+      if (run == 32) continue;
+      // The cell after the run: outside the tube (stage the next one), or a single other move.
+      const int rank = __shfl_sync(kFull, rk, run);
+      if (rank < 0) break;
+      if (rank == 0 && local) {  // v = 0 won: the local alignment starts here
+        done = 1;
+        break;
+      }
+      // rank -> move (Eq. 1 listing order, rank 7 first)
+      const int di = (0xE8 >> rank) & 1, dj = (0xD4 >> rank) & 1, dk = (0xB2 >> rank) & 1;
+      if (rank == 0 || n >= cap || i < di || j < dj || k < dk) {
+        bad = 1;
+        break;
+      }
+      if (lane == 0) {
         const int pos = cap - 1 - n;
-        row0[pos] = di ? (uint8_t)S0[i - 1] : (uint8_t)255;
-        row1[pos] = dj ? (uint8_t)S1[j - 1] : (uint8_t)255;
-        row2[pos] = dk ? (uint8_t)S2[k - 1] : (uint8_t)255;
-        i -= di;
-        j -= dj;
-        k -= dk;
-        ++n;
-        done = start(i, j, k);
+        row0[pos] = di ? res[0][i - iw] : (uint8_t)255;
+        row1[pos] = dj ? res[1][j - jw] : (uint8_t)255;
+        row2[pos] = dk ? res[2][k - kw] : (uint8_t)255;
+      }
+      i -= di;
+      j -= dj;
+      k -= dk;
+      ++n;
+      if (start(i, j, k)) {
+        done = 1;
+        break;
       }
     }
-    __syncwarp();
-    i = __shfl_sync(kFull, i, 0);
-    j = __shfl_sync(kFull, j, 0);
-    k = __shfl_sync(kFull, k, 0);
-    n = __shfl_sync(kFull, n, 0);
-    bad = __shfl_sync(kFull, bad, 0);
-    done = __shfl_sync(kFull, done, 0);
+    __syncwarp();  // the next tube overwrites the shared buffers
   }
   if (lane == 0) {
     if (p.state) {
