@@ -24,7 +24,6 @@ constexpr int kPC = 8;             // lanes of a warp along k
 constexpr int kMaxAlphabet = 32;
 constexpr int kWarpsPerCta = 4;
 constexpr int kRing = 4;           // face-staging ring slots per warp (power of two)
-constexpr int kAhead = 2;          // steps between loading a face piece and using it
 
 // Alignment types of Sec. II. Semi-global: zero axes, score = best cell on a last slice;
 // local: zero axes and v = 0 in Eq. 1, score = best cell. Both are score-only on the device.

@@ -34,11 +34,13 @@ __device__ __forceinline__ int win_base(int x, int l) {
   return ((((x - (kTubeS - 1)) >> l) - 1) << l) - 1;
 }
 
+// The triplet's shape comes in registers (len: the three lengths; nK: column tasks along k;
+// nJR, nKC: lane rows / columns of the task grid), read once by the caller.
 template <int W>
 __device__ __forceinline__ void tube_load(uint32_t* win, uint8_t (*res)[kWin], int i0, int j0,
                                           int k0, int lj, int lk, const uint32_t* codes,
-                                          const TripDesc& d, const int8_t* const* S, int T,
-                                          int i_lo, int lane) {
+                                          const int (&len)[3], int nK, int nJR, int nKC,
+                                          const int8_t* const* S, int T, int i_lo, int lane) {
   // residue windows: res[0][m] = S0[i0 - kTubeS + m], res[1][m] = S1[win_base(j0) + m], ...
   uint8_t rv[3][kWin / 32];
   {
@@ -48,7 +50,7 @@ __device__ __forceinline__ void tube_load(uint32_t* win, uint8_t (*res)[kWin], i
 #pragma unroll
       for (int h = 0; h < kWin / 32; ++h) {
         const int x = base[q] + lane + 32 * h;
-        rv[q][h] = (x >= 0 && x < d.len[q]) ? (uint8_t)S[q][x] : (uint8_t)255;
+        rv[q][h] = (x >= 0 && x < len[q]) ? (uint8_t)S[q][x] : (uint8_t)255;
       }
   }
   constexpr int V = (W + 3) / 4;  // 16-byte vectors per record (W = 2 uses the low half)
@@ -61,10 +63,9 @@ __device__ __forceinline__ void tube_load(uint32_t* win, uint8_t (*res)[kWin], i
     const int ii = i0 - sx;
     const int gr = ((j0 - sx) >> lj) + rem / kTubeC - 1;
     const int gc = ((k0 - sx) >> lk) + rem % kTubeC - 1;
-    valid[u] = e < kTubeRecs && ii >= i_lo && gr >= 0 && gc >= 0 && gr < d.nJ * kPR &&
-               gc < d.nK * kPC;
+    valid[u] = e < kTubeRecs && ii >= i_lo && gr >= 0 && gc >= 0 && gr < nJR && gc < nKC;
     if (valid[u]) {
-      const int task = (gr / kPR) * d.nK + (gc / kPC);
+      const int task = (gr / kPR) * nK + (gc / kPC);
       const int lr = gr % kPR, lcc = gc % kPC;
       const uint32_t* src =
           codes + (((int64_t)task * T + (ii - i_lo + lr + lcc)) * 32 + (lr * kPC + lcc)) * W;
@@ -77,6 +78,9 @@ __device__ __forceinline__ void tube_load(uint32_t* win, uint8_t (*res)[kWin], i
       }
     }
   }
+  // All loads above are issued before any store below (the barrier keeps the compiler from
+  // pairing each load with its store, which would serialise the round trips).
+  __syncwarp();
 #pragma unroll
   for (int q = 0; q < 3; ++q)
 #pragma unroll
@@ -103,6 +107,8 @@ __global__ void __launch_bounds__(32) walk_kernel(const WalkParams p) {
   const int q = blockIdx.x;
   const TripDesc& d = p.desc[p.tb_trips[q]];
   const int a = d.len[0], b = d.len[1], c = d.len[2];
+  const int len[3] = {a, b, c};
+  const int nK = d.nK, nJR = d.nJ * kPR, nKC = d.nK * kPC;
   const int lj = __ffs(p.NJ) - 1, lk = __ffs(p.NK) - 1;  // tile sides are powers of two
   const int8_t* const S[3] = {p.seq + d.s_off[0], p.seq + d.s_off[1], p.seq + d.s_off[2]};
   const int cap = p.row_cap[q];
@@ -136,7 +142,7 @@ __global__ void __launch_bounds__(32) walk_kernel(const WalkParams p) {
   int done = start(i, j, k);
   while (!done && i >= i_lo && !bad) {
     const int i0 = i, j0 = j, k0 = k;
-    tube_load<W>(win, res, i0, j0, k0, lj, lk, codes, d, S, T, i_lo, lane);
+    tube_load<W>(win, res, i0, j0, k0, lj, lk, codes, len, nK, nJR, nKC, S, T, i_lo, lane);
     __syncwarp();
     // residue windows: S0[x - 1] is res[0][x - iw], and likewise for S1 and S2
     const int iw = i0 - kTubeS + 1, jw = win_base(j0, lj) + 1, kw = win_base(k0, lk) + 1;

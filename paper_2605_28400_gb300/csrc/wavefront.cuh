@@ -12,10 +12,10 @@
 //   j-records written by (J-1,K) and the k-records written by (J,K-1) (engine.h). A producer
 //   publishes how many steps it has completed every TI steps with a release store. The
 //   consumer's edge lanes need the records of step t; every lane loads one 16-byte piece of
-//   them from L2 kAhead steps early (after lane 0 has acquired the producer's progress, bounded
-//   wait) and parks it in a small per-warp shared-memory ring one step early. All lanes then
-//   read their halo from the ring and select it against the shuffled value, so the step loop
-//   has no lane-divergent branches in steady state.
+//   them from L2 one or two steps early (after lane 0 has acquired the producer's progress,
+//   bounded wait) and parks it in a small per-warp shared-memory ring. All lanes then read
+//   their halo from the ring and select it against the shuffled value; loads and stores that
+//   only some lanes make are predicated, so the step loop has no lane-divergent branches.
 //   Tasks come from one atomic queue in an order where every producer precedes its consumers,
 //   so the engine cannot deadlock even when not all warps are resident.
 //   TB = true additionally keeps traceback keys (8*M' + 7, engine.h) and streams one 4-bit code
@@ -90,6 +90,35 @@ __device__ __forceinline__ int mad_lo(int a, int b, int c) {
   int d;
   asm("mad.lo.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
   return d;
+}
+
+// Predicated 16-byte accesses of the per-step data movement: one instruction each, so lanes that
+// have nothing to load or store (no face piece, no record) take no branch in the step loop.
+// Load: *p if pr, else neg in every component.
+__device__ __forceinline__ int4 ld_cg_if(const int4* p, bool pr, int neg) {
+  int4 v;
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.b32 q, %5, 0;\n mov.b32 %0, %6;\n mov.b32 %1, %6;\n"
+      " mov.b32 %2, %6;\n mov.b32 %3, %6;\n @q ld.global.cg.v4.s32 {%0,%1,%2,%3}, [%4];\n}"
+      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+      : "l"(p), "r"((int)pr), "r"(neg));
+  return v;
+}
+__device__ __forceinline__ void st_shared_if(int4* p, int4 v, bool pr) {
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.b32 q, %5, 0;\n @q st.shared.v4.s32 [%0], {%1,%2,%3,%4};\n}"
+      ::"r"((unsigned)__cvta_generic_to_shared(p)), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w),
+      "r"((int)pr)
+      : "memory");
+}
+__device__ __forceinline__ void st_global_if(int4* p, int4 v, bool pr) {
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.b32 q, %5, 0;\n @q st.global.v4.s32 [%0], {%1,%2,%3,%4};\n}"
+      ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "r"((int)pr));
+}
+__device__ __forceinline__ void st_global_if(int* p, int v, bool pr) {
+  asm volatile("{\n .reg .pred q;\n setp.ne.b32 q, %2, 0;\n @q st.global.s32 [%0], %1;\n}"
+               ::"l"(p), "r"(v), "r"((int)pr));
 }
 
 }  // namespace
@@ -370,14 +399,20 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
     bool ok = true;
 
     // Face pieces of step u: each lane loads its 16-byte piece from L2 into registers at step
-    // u - kAhead (after lane 0 has seen the producers publish the steps that wrote them), parks
-    // it in ring slot u % kRing at step u - 1, and the edge lanes read the slot at step u. The
-    // load's latency is covered by a whole step of compute. A piece whose slice is outside
+    // u - kAh (after lane 0 has seen the producers publish the steps that wrote them), parks it
+    // in ring slot u % kRing at the start of step u - kAh + 1, and the edge lanes read the slot
+    // at step u. The load's latency is covered by the rest of the step that issued it (at
+    // least). A piece whose slice is outside
     // 0..a, or whose producer does not exist, is parked as -infinity: the piece of lane column
     // l covers exactly the slice s = u - l that edge lane (0, l) (or row l, for k-pieces) works
     // on at step u, so the edge lanes take the ring value as is.
     int4 pf = make_int4(NEG, NEG, NEG, NEG);
     int pf_u = -1;
+    // Lead of a piece's load over its use, in steps. Traceback keys serve single triplets whose
+    // time is the wavefront ramp, where each producer-consumer level lags by the lead: 1 step
+    // (the load then has the rest of one step to land). Score mode runs many levels at once
+    // and gives the load two steps.
+    constexpr int kAh = TB ? 1 : 2;
     auto fetch = [&](int u) {
       const int needJ = min(u + kPR, T), needK = min(u + kPC, T);
       if (cachedJ < needJ || cachedK < needK) {  // warp-uniform
@@ -394,12 +429,13 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
       }
       const int sl = u - cp_delta;
       pf_u = u;
-      if (ok && cp_kind != 0 && sl >= 0 && sl <= a && (cp_kind == 1 ? J > 0 : K > 0)) {
+      {
+        const bool have = ok && cp_kind != 0 && sl >= 0 && sl <= a && (cp_kind == 1 ? J > 0 : K > 0);
         const int* src = (cp_kind == 1) ? srcJ + (int64_t)sl * G::RJ + cp_col
                                         : srcK + (int64_t)sl * G::RK + cp_col;
-        pf = __ldcg(reinterpret_cast<const int4*>(src));
-      } else if (SLAB && p.plane_in && sl == -1 && cp_kind != 0 &&
-                 (cp_kind == 1 ? J > 0 : K > 0)) {
+        pf = ld_cg_if(reinterpret_cast<const int4*>(src), have, NEG);  // src is read only if have
+      }
+      if (SLAB && p.plane_in && sl == -1 && cp_kind != 0 && (cp_kind == 1 ? J > 0 : K > 0)) {
         // Slab launch, local slice -1: the producer's record of that slice is plane i0 - 1.
         const int* pl = p.plane_in;
         if (cp_kind == 1) {  // j-record slots cp_col..+3: row J*WJ-1, k = K*WK + slot - 4
@@ -410,18 +446,18 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
           const int64_t base = (int64_t)(J * WJ + cp_col) * PW + K * WK - 1;
           pf = make_int4(pl[base], pl[base + PW], pl[base + 2 * PW], pl[base + 3 * PW]);
         }
-      } else {
-        pf = make_int4(NEG, NEG, NEG, NEG);
       }
     };
     auto park = [&]() {
-      if (cp_kind != 0)
-        *reinterpret_cast<int4*>(ring + (pf_u & (kRing - 1)) * G::SLOT + cp_dst) = pf;
+      st_shared_if(reinterpret_cast<int4*>(ring + (pf_u & (kRing - 1)) * G::SLOT + cp_dst), pf,
+                   cp_kind != 0);
     };
 
     fetch(0);
-    park();
-    fetch(1);
+    if (kAh == 2) {
+      park();
+      fetch(1);
+    }
     // Residues of S0 by slice: in block B, lane q holds the residue of slice 32*B + q. Blocks are
     // loaded one block ahead and read by shuffle, so no global load sits on the per-step path.
     // Packed mode: the two triplets' residues in bits 0-7 and 8-15.
@@ -441,7 +477,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
                     int (&colCur)[NJ], const int (&colPrev)[NJ]) -> bool {
       const int s = t - r - lc;
       park();  // piece of step t + 1
-      if (t + kAhead < T) fetch(t + kAhead);
+      if (t + kAh < T) fetch(t + kAh);
       if (!ok) return false;
       if ((t & 31) == 0 && t > 0) {
         xprev = xcur;
@@ -748,21 +784,27 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
                   make_int4(P[pp][4 * q4], P[pp][4 * q4 + 1], P[pp][4 * q4 + 2],
                             P[pp][4 * q4 + 3]);
         }
-        if (r == kPR - 1 && has_out_j) {
+        {  // j-record: the last lane row's bottom tile rows (predicated, no branch)
+          const bool out_j = r == kPR - 1 && has_out_j;
           int* dst = dstJ + (int64_t)s * G::RJ;
-          if (lc == 0) dst[3] = colCur[NJ - 1];  // corner for the consumer's lane (0,0)
+          st_global_if(dst + 3, colCur[NJ - 1], out_j && lc == 0);  // corner for lane (0,0)
           int4* d4 = reinterpret_cast<int4*>(dst + 4 + lc * NK);
 #pragma unroll
           for (int q4 = 0; q4 < NK / 4; ++q4)
-            d4[q4] = make_int4(P[NJ - 1][4 * q4], P[NJ - 1][4 * q4 + 1], P[NJ - 1][4 * q4 + 2],
-                               P[NJ - 1][4 * q4 + 3]);
+            st_global_if(d4 + q4,
+                         make_int4(P[NJ - 1][4 * q4], P[NJ - 1][4 * q4 + 1],
+                                   P[NJ - 1][4 * q4 + 2], P[NJ - 1][4 * q4 + 3]),
+                         out_j);
         }
-        if (lc == kPC - 1 && has_out_k) {
+        {  // k-record: the last lane column's right tile columns
+          const bool out_k = lc == kPC - 1 && has_out_k;
           int4* d4 = reinterpret_cast<int4*>(dstK + (int64_t)s * G::RK + r * NJ);
 #pragma unroll
           for (int p4 = 0; p4 < NJ / 4; ++p4)
-            d4[p4] = make_int4(P[4 * p4][NK - 1], P[4 * p4 + 1][NK - 1], P[4 * p4 + 2][NK - 1],
-                               P[4 * p4 + 3][NK - 1]);
+            st_global_if(d4 + p4,
+                         make_int4(P[4 * p4][NK - 1], P[4 * p4 + 1][NK - 1],
+                                   P[4 * p4 + 2][NK - 1], P[4 * p4 + 3][NK - 1]),
+                         out_k);
         }
         if (AT == kSemiGlobal && (edgeJ || edgeK)) {
           // Cells of this slice on the last row j = b or the last column k = c, in the original
