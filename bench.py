@@ -498,6 +498,26 @@ def aux_measurements(B, torch, stream, flush, sms, clock_mhz, skip: str, cpu_leg
                      "unit": "TOPS (int32)" if packing == 1 else "TOPS (int16x2 lanes)",
                      "frac": ach_b / peak_b},
         "cells": w.cells}
+    # The same 4096 triplets with traceback: the traceback kernels and the walk at full occupancy
+    # (thousands of independent triplets), where the single-triplet line is bound by its ramp.
+    plan = B.trioseq_plan(w.scoring.alphabet, w.scoring.sub, w.scoring.gap)
+    tuned_tb = B.trioseq_plan_autotune(plan, strs, B.WITH_TRACEBACK)
+    bt = B.trioseq_batch_create(plan, strs, B.WITH_TRACEBACK)
+    sm, km, wk, sc_tb = time_batch(B, torch, bt, 3, 2, stream, flush, len(strs))
+    B.trioseq_batch_destroy(bt)
+    B.trioseq_plan_destroy(plan)
+    kt = statistics.mean(km)
+    ach_t = OPS_PER_CELL * w.cells / (kt / 1e3) / 1e12
+    peak_t = sms * INT32_LANES_PER_SM * clock_mhz * 1e6 / 1e12
+    out["batch4096_traceback"] = {
+        "workload": "the 4096-triplet batch with 4-bit traceback codes and one walk per triplet",
+        "gcups": w.cells / (statistics.mean(sm) / 1e3) / 1e9, "ms_per_step": statistics.mean(sm),
+        "kernel_ms": kt, "walk_ms": statistics.mean(wk), "tuned": tuned_tb,
+        "identical_scores_to_score_only": [int(x) for x in sc_tb] == [int(x) for x in sc_batched],
+        "roofline": {"bound": "alu", "achieved": ach_t, "peak": peak_t, "unit": "TOPS (int32)",
+                     "frac": ach_t / peak_t,
+                     "code_stream_gbs": CODE_BYTES_PER_CELL * w.cells / kt / 1e6},
+        "cells": w.cells}
     out["serving_stream"] = serving_measurement(B)
     out["dna8000_linear_space_traceback"] = linear_space_measurement(B, torch, stream)
     return out

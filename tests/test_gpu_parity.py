@@ -194,6 +194,38 @@ def test_config2_batch_4096_sampled():
         B.trioseq_plan_destroy(plan)
 
 
+def test_config2_batch_4096_traceback():
+    """The 4096-triplet batch with traceback: every score equals the score-only run's, every
+    alignment re-scores to its score and strips to its input triplet, and sampled alignments
+    equal the oracle's."""
+    w = synth.config2()
+    sc = w.scoring
+    plan = _plan(DNA)
+    try:
+        trip_strs = [strs(t, DNA) for t in w.triplets]
+        score_only = B.trioseq_align_batch(plan, trip_strs)
+        got = B.trioseq_align_batch(plan, trip_strs, B.WITH_TRACEBACK)
+        assert got.tolist() == score_only.tolist()
+        lut = np.full(256, 255, dtype=np.uint8)
+        for code, ch in enumerate(sc.alphabet):
+            lut[ord(ch)] = code
+        for i, t in enumerate(w.triplets):
+            rows = B.trioseq_traceback(plan, i)
+            codes = np.stack([lut[np.frombuffer(r.encode(), dtype=np.uint8)] for r in rows])
+            assert oracle.sp_score(codes, sc.sub, sc.gap) == int(got[i]), i
+            for q in range(3):
+                assert np.array_equal(codes[q][codes[q] != 255], t[q]), (i, q)
+            assert not (codes == 255).all(axis=0).any(), i  # no all-gap column
+        rng = np.random.default_rng(12)
+        idx = sorted(set(rng.choice(len(w.triplets), size=8, replace=False).tolist()) | {0, 4095})
+        for i in idx:
+            score, rows = oracle.align(*w.triplets[i], sc.sub, sc.gap, traceback=True)
+            assert int(got[i]) == score, i
+            assert B.trioseq_traceback(plan, i) == oracle_rows_str(rows, sc), i
+    finally:
+        B.trioseq_plan_destroy(plan)
+
+
 def test_config3_protein_4000_properties(prot_plan):
     w = synth.config3()
     t = w.triplets[0]
