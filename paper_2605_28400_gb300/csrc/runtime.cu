@@ -282,21 +282,59 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
   size_t pos = 0, face = 0, codes = 0, rows = 0;
   int64_t prog = 0;
   bt->cells = 0;
-  // 1. Per triplet: encode, range checks, output slots.
+  // 1a. Packed positions, then the residue codes (alphabet lookup). Large batches encode on
+  //     several host threads, each over a contiguous range of triplets.
+  for (size_t t = 0; t < n; t++)
+    for (int q = 0; q < 3; q++) {
+      bt->desc[t].s_off[q] = (int64_t)pos;
+      pos += align_up(trip[t].len[q], 16);
+    }
+  {
+    std::atomic<bool> bad{false};
+    const auto encode = [&](size_t t0, size_t t1) {
+      for (size_t t = t0; t < t1 && !bad.load(std::memory_order_relaxed); t++)
+        for (int q = 0; q < 3; q++) {
+          const unsigned char* src = reinterpret_cast<const unsigned char*>(trip[t].s[q]);
+          int8_t* dst = bt->seq.data() + bt->desc[t].s_off[q];
+          int16_t acc = 0;
+          for (uint32_t e = 0; e < trip[t].len[q]; e++) {
+            const int16_t code = plan->lut[src[e]];
+            acc |= code;  // negative iff some residue is outside the alphabet
+            dst[e] = (int8_t)code;
+          }
+          if (acc < 0) bad.store(true, std::memory_order_relaxed);
+        }
+    };
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const size_t nth = std::min<size_t>({(size_t)8, (size_t)hw, n, total / (1u << 19) + 1});
+    if (nth <= 1) {
+      encode(0, n);
+    } else {  // split the triplets into nth ranges of about equal residue counts
+      std::vector<std::thread> pool;
+      size_t t0 = 0;
+      for (size_t k = 1; k <= nth && t0 < n; k++) {
+        size_t t1 = t0;
+        const size_t goal = total * k / nth;
+        while (t1 < n && (k == nth || (size_t)bt->desc[t1].s_off[0] < goal)) t1++;
+        if (t1 == t0) continue;
+        try {
+          pool.emplace_back(encode, t0, t1);
+        } catch (...) {  // no thread: encode the range here
+          encode(t0, t1);
+        }
+        t0 = t1;
+      }
+      for (auto& th : pool) th.join();
+    }
+    if (bad.load()) return TRIOSEQ_EINVAL;
+  }
+  // 1b. Per triplet: range checks, output slots.
   for (size_t t = 0; t < n; t++) {
     TripDesc& d = bt->desc[t];
     int64_t sumlen = 0;
     for (int q = 0; q < 3; q++) {
       const uint32_t L = trip[t].len[q];
-      d.s_off[q] = (int64_t)pos;
       d.len[q] = d.glen[q] = (int32_t)L;
-      const unsigned char* src = reinterpret_cast<const unsigned char*>(trip[t].s[q]);
-      for (uint32_t e = 0; e < L; e++) {
-        const int16_t code = plan->lut[src[e]];
-        if (code < 0) return TRIOSEQ_EINVAL;
-        bt->seq[pos + e] = (int8_t)code;
-      }
-      pos += align_up(L, 16);
       sumlen += L;
     }
     // |M'| <= max|sigma''| * (a+b+c) (and, with zero axes or v = 0, <= 2|alpha| * (a+b+c));
