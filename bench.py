@@ -44,6 +44,29 @@ if ROOT not in sys.path:
 METRIC = "GCUPS (3D cells/s) and % of INT32 roofline; batched vs per-triplet; p50/p99 lat"
 OPS_PER_CELL = 13          # 7 adds + 6 max per cell (factored Eq. 1)
 INT32_LANES_PER_SM = 128   # int32 ops/clk/SM: 64 fused add+max (VIADDMNMX) issues per clock per SM
+# int32 operations per instruction of the forms that carry maxima. Maxima issue on the ALU pipe
+# only; plain adds can also go to the FMA pipe (the add forms are measured and reported, but the
+# max-plus roof is set by the forms with maxima).
+ALU_OPS_PER_FORM = {"max": 1, "add_max": 2, "max3": 2}
+
+
+def measured_alu(B) -> dict:
+    """Issue rates of the cell update's int32 instruction forms on this GPU (trioseq_alu_rate,
+    outside any timed region) and the int32 operations per SM per clock that the forms with
+    maxima sustain: the best of operations-per-instruction x rate over those forms."""
+    rates = {}
+    for op, name in enumerate(B.ALU_FORMS):
+        r, mhz = B.trioseq_alu_rate(op)
+        rates[name] = {"per_clk_per_sm": r, "sm_mhz": mhz}
+    lanes = max(ALU_OPS_PER_FORM[k] * rates[k]["per_clk_per_sm"] for k in ALU_OPS_PER_FORM)
+    return {"forms": rates, "int32_ops_per_clk_per_sm": lanes}
+
+
+def roof_lanes(alu: dict | None) -> float:
+    """int32 lanes per SM per clock for the roofline: the lower of nominal and measured."""
+    if not alu:
+        return float(INT32_LANES_PER_SM)
+    return min(float(INT32_LANES_PER_SM), alu["int32_ops_per_clk_per_sm"])
 CODE_BYTES_PER_CELL = 0.5  # packed 4-bit traceback code
 
 
@@ -400,7 +423,8 @@ def serving_measurement(B, n_req: int = 2000, load: float = 0.7, n_cal: int = 60
                    "clipped to [50, 2000]"}
 
 
-def aux_measurements(B, torch, stream, flush, sms, clock_mhz, skip: str, cpu_legs: bool = True):
+def aux_measurements(B, torch, stream, flush, sms, clock_mhz, skip: str, cpu_legs: bool = True,
+                     lanes: float = INT32_LANES_PER_SM):
     """Secondary lines of the metric: the traceback workload (related DNA triplet n~1000, score +
     4-bit codes + walk), the semi-global and local types on the n=4000 protein triplet, the
     4096-triplet batch in one persistent launch versus one launch per triplet, and the serving
@@ -419,7 +443,7 @@ def aux_measurements(B, torch, stream, flush, sms, clock_mhz, skip: str, cpu_leg
         sm, km, wk, sc = time_batch(B, torch, bt, 10, 3, stream, flush, 1)
         kmean = statistics.mean(km)
         ach = OPS_PER_CELL * w.cells / (kmean / 1e3) / 1e12
-        peak = sms * INT32_LANES_PER_SM * clock_mhz * 1e6 / 1e12
+        peak = sms * lanes * clock_mhz * 1e6 / 1e12
         entry = {"workload": f"{w.name}: {desc}",
                  "gcups": w.cells / (statistics.mean(sm) / 1e3) / 1e9,
                  "ms_per_step": statistics.mean(sm), "kernel_ms": kmean, "cells": w.cells,
@@ -445,7 +469,7 @@ def aux_measurements(B, torch, stream, flush, sms, clock_mhz, skip: str, cpu_leg
         sm, km, _, sc = time_batch(B, torch, bt, 5, 3, stream, flush, 1)
         kmean = statistics.mean(km)
         ach = ops * w.cells / (kmean / 1e3) / 1e12
-        peak = sms * INT32_LANES_PER_SM * clock_mhz * 1e6 / 1e12
+        peak = sms * lanes * clock_mhz * 1e6 / 1e12
         out[f"protein4000_{name}"] = {
             "workload": f"{w.name}: alignment type {name} (Sec. II), score only",
             "gcups": w.cells / (statistics.mean(sm) / 1e3) / 1e9, "kernel_ms": kmean,
@@ -465,7 +489,7 @@ def aux_measurements(B, torch, stream, flush, sms, clock_mhz, skip: str, cpu_leg
     batched = w.cells / (statistics.mean(sm) / 1e3) / 1e9
     kb = statistics.mean(km)
     ach_b = OPS_PER_CELL * w.cells / (kb / 1e3) / 1e12
-    peak_b = packing * sms * INT32_LANES_PER_SM * clock_mhz * 1e6 / 1e12
+    peak_b = packing * sms * lanes * clock_mhz * 1e6 / 1e12
     B.trioseq_batch_destroy(bt)
     singles = [B.trioseq_batch_create(plan, [s], B.SCORE_ONLY) for s in strs]
     for b in singles:  # untimed first run of each (captures its graph)
@@ -508,7 +532,7 @@ def aux_measurements(B, torch, stream, flush, sms, clock_mhz, skip: str, cpu_leg
     B.trioseq_plan_destroy(plan)
     kt = statistics.mean(km)
     ach_t = OPS_PER_CELL * w.cells / (kt / 1e3) / 1e12
-    peak_t = sms * INT32_LANES_PER_SM * clock_mhz * 1e6 / 1e12
+    peak_t = sms * lanes * clock_mhz * 1e6 / 1e12
     out["batch4096_traceback"] = {
         "workload": "the 4096-triplet batch with 4-bit traceback codes and one walk per triplet",
         "gcups": w.cells / (statistics.mean(sm) / 1e3) / 1e9, "ms_per_step": statistics.mean(sm),
@@ -642,19 +666,26 @@ def main():
     e2e_val = world * w.cells / (e2e_total / len(e2e_ms) / 1e3) / 1e9
 
     clock_mhz = clocks.get("sm_mhz") or 2070.0
+    try:
+        alu = measured_alu(B)
+    except Exception as exc:  # the nominal lane count stands; the line says why
+        alu = {"error": str(exc)}
+    lanes = roof_lanes(alu if "int32_ops_per_clk_per_sm" in alu else None)
     kmean = statistics.mean(kern_ms)
     achieved = OPS_PER_CELL * w.cells / (kmean / 1e3) / 1e12
     # packed int16x2 batches run two cells per instruction lane: the lane roof doubles
     packing = info.get("packing", 1)
-    peak = packing * sms * INT32_LANES_PER_SM * clock_mhz * 1e6 / 1e12
+    peak = packing * sms * lanes * clock_mhz * 1e6 / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak,
             "unit": "TOPS (int32)" if packing == 1 else "TOPS (int16x2 lanes)",
             "frac": achieved / peak,
             "traffic": measured_traffic(f"{args.workload}"),
             "kernel": "wavefront_kernel", "kernel_ms": kmean,
-            "peak_basis": f"{sms} SMs x {INT32_LANES_PER_SM} int32 ops/clk x median SM clock "
+            "peak_basis": f"{sms} SMs x {lanes:.1f} int32 ops/clk (the lower of the nominal "
+                          f"{INT32_LANES_PER_SM} and the measured rate) x median SM clock "
                           f"{clock_mhz:.0f} MHz sampled in the timed region"
-                          + (" x 2 (int16x2 packing)" if packing == 2 else "")}
+                          + (" x 2 (int16x2 packing)" if packing == 2 else ""),
+            "alu_measured": alu}
     if tb:
         roof["code_stream_gbs"] = CODE_BYTES_PER_CELL * w.cells / (kmean / 1e3) / 1e9
 
@@ -679,7 +710,7 @@ def main():
 
     if rank == 0 and not args.no_aux:
         line["aux"] = aux_measurements(B, torch, stream, flush, sms, clock_mhz, args.workload,
-                                       not args.no_cpu)
+                                       not args.no_cpu, lanes)
     if rank == 0 and not args.no_cpu:
         cb, _ = cpu_oracle_sample(w, 2.5e8, tb)
         line["cpu_baseline"] = cb

@@ -251,6 +251,22 @@ trioseq_status trioseq_poll(trioseq_server_t srv, uint64_t ticket, int32_t* scor
 /* Stop the server thread after finishing admitted work and release it. */
 trioseq_status trioseq_server_destroy(trioseq_server_t srv);
 
+/* ---- measurement ---- */
+
+/* trioseq_alu_rate — measured rate of one int32 instruction form on the current GPU. It backs the
+ * roofline of the cell recurrence (Eq. 1, Sec. II): the engine counts 13 int32 operations per
+ * cell (7 adds, 6 maxima) against SMs x 128 int32 lanes x SM clock, and issues them as the forms
+ * below. The paper has no counterpart; this call measures the hardware.
+ *   op             : 0 max(x, y); 1 max(y + b, x) (__viaddmax_s32, two operations);
+ *                    2 max(x, y, z) (__vimax3_s32, two operations); 3 x + y + b (two operations);
+ *                    4 y * one + x with a runtime one (the FMA-pipe add).
+ *   per_clk_per_sm : out, thread-level instructions of that form completed per SM clock per SM,
+ *                    with every SM fully occupied by independent recurrences.
+ *   sm_mhz         : out, the SM clock during the measurement (cycles / event time).
+ * Allocates a few MB of device memory for the duration of the call and launches two short
+ * kernels (~0.1 s). Errors: TRIOSEQ_EINVAL (op out of range, null output), TRIOSEQ_ECUDA. */
+trioseq_status trioseq_alu_rate(int32_t op, double* per_clk_per_sm, double* sm_mhz);
+
 /* ---- allocation-free entry point ---- */
 
 /* trioseq_align_noalloc — score one triplet without allocating any memory in the call.

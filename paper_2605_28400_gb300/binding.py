@@ -86,6 +86,8 @@ def load(build_if_missing: bool = True):
         "trioseq_batch_slabs": ([vp, i32p, i32p], i32),
         "trioseq_traceback_span": ([vp, sz, i32p, i32p], i32),
         "trioseq_batch_span": ([vp, sz, i32p, i32p], i32),
+        "trioseq_alu_rate": ([i32, ctypes.POINTER(ctypes.c_double),
+                              ctypes.POINTER(ctypes.c_double)], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -103,7 +105,7 @@ def exported_symbols() -> list[str]:
             "trioseq_plan_io_bytes", "trioseq_server_create", "trioseq_submit", "trioseq_poll",
             "trioseq_server_destroy", "trioseq_strerror", "trioseq_align_noalloc",
             "trioseq_plan_autotune", "trioseq_batch_packing", "trioseq_batch_slabs",
-            "trioseq_traceback_span", "trioseq_batch_span"]
+            "trioseq_traceback_span", "trioseq_batch_span", "trioseq_alu_rate"]
 
 
 def trioseq_plan_autotune(plan, sample, mode: int = SCORE_ONLY) -> dict:
@@ -345,6 +347,17 @@ def trioseq_poll(server, ticket: int, cap: int = 0):
 
 def trioseq_server_destroy(server):
     _check(load().trioseq_server_destroy(server), "trioseq_server_destroy")
+
+
+ALU_FORMS = ("max", "add_max", "max3", "add3", "mad_by_one")  # trioseq_alu_rate's op codes
+
+
+def trioseq_alu_rate(op: int) -> tuple[float, float]:
+    """(instructions per SM clock per SM, SM MHz) of int32 instruction form `op` (ALU_FORMS)."""
+    rate, mhz = ctypes.c_double(0), ctypes.c_double(0)
+    _check(load().trioseq_alu_rate(int(op), ctypes.byref(rate), ctypes.byref(mhz)),
+           "trioseq_alu_rate")
+    return rate.value, mhz.value
 
 
 def trioseq_align_noalloc(alphabet: str, sub, gap: int, d_s0: int, a: int, d_s1: int, b: int,

@@ -82,3 +82,10 @@ def test_reference_arm_rank0_prints_contract_line():
     assert line["higher_is_better"] is True
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_roofline_lanes_take_the_lower_of_nominal_and_measured():
+    import bench
+    assert bench.roof_lanes(None) == bench.INT32_LANES_PER_SM
+    assert bench.roof_lanes({"int32_ops_per_clk_per_sm": 127.2}) == 127.2
+    assert bench.roof_lanes({"int32_ops_per_clk_per_sm": 140.0}) == bench.INT32_LANES_PER_SM
