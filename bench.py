@@ -191,15 +191,26 @@ def triplet_strings(w):
 
 # ------------------------------------------------------------------------------------------
 def host_cpu() -> dict:
-    """CPU model and logical core count of the host running the oracle."""
-    model = ""
+    """CPU model, logical core count and clock (lscpu's max MHz, and the current MHz of CPU 0 from
+    cpufreq where the kernel exposes it) of the host running the oracle."""
+    model, max_mhz, cur_mhz = "", None, None
     try:  # lscpu names Arm cores (Neoverse-V2 on Grace); /proc/cpuinfo there does not
         out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
         for line in out.splitlines():
-            if line.lower().startswith("model name:"):
+            key = line.split(":", 1)[0].strip().lower()
+            if key == "model name" and not model:
                 model = line.split(":", 1)[1].strip()
-                break
+            elif key == "cpu max mhz":
+                try:
+                    max_mhz = float(line.split(":", 1)[1].strip().replace(",", "."))
+                except ValueError:
+                    pass
     except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/sys/devices/system/cpu/cpu0/cpufreq/scaling_cur_freq") as fh:
+            cur_mhz = int(fh.read().strip()) / 1000.0
+    except (OSError, ValueError):
         pass
     try:
         with open("/proc/cpuinfo") as fh:
@@ -212,7 +223,7 @@ def host_cpu() -> dict:
     if not model:
         import platform
         model = platform.processor() or platform.machine()
-    return {"cpu": model, "nproc": os.cpu_count()}
+    return {"cpu": model, "nproc": os.cpu_count(), "max_mhz": max_mhz, "cur_mhz": cur_mhz}
 
 
 def cpu_all_cores_sample(triplets, sc, target_s: float = 3.0):
