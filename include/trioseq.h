@@ -208,7 +208,8 @@ trioseq_status trioseq_batch_timing(trioseq_batch_t batch, float ms[2]);
 /* trioseq_plan_autotune — pick the kernel variant for a class of work by measuring it.
  * Runs the sample batch (host strings, n >= 1, mode as for trioseq_align_batch) once per
  * candidate — every instantiated register tile per lane (8x8, 4x8, 4x4 cells, i.e. column blocks
- * of 32x64, 16x64 and 16x32 cells per warp) times progress intervals of 4, 8, 16 and 32 steps —
+ * of 32x64, 16x64 and 16x32 cells per warp, and in traceback mode also 8x4, 32x32 cells) times
+ * progress intervals of 4, 8, 16 and 32 steps —
  * times two passes of each with CUDA events on the legacy default stream, and remembers the
  * fastest in the plan for batches of the same mode, the same single-or-batch kind, and the same
  * bit length of the longest sequence. Later batches of that class use it; other classes keep

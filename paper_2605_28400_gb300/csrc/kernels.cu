@@ -253,6 +253,9 @@ const void* pick(int nj, int nk, bool tb, int at, int pk, bool slab) {
   if (nj == 8 && nk == 8) return tb ? kptr<8, 8, true>() : kptr<8, 8, false>();
   if (nj == 4 && nk == 8) return tb ? kptr<4, 8, true>() : kptr<4, 8, false>();
   if (nj == 4 && nk == 4) return tb ? kptr<4, 4, true>() : kptr<4, 4, false>();
+  // 8x4 (32 x 32-cell tasks) for traceback keys only: single triplets whose time is the ramp
+  // cross fewer k-levels, whose lag is the larger one (8 lane columns of skew)
+  if (nj == 8 && nk == 4) return tb ? kptr<8, 4, true>() : nullptr;
   return nullptr;
 }
 

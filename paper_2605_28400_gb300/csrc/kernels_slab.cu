@@ -18,6 +18,7 @@ const void* wavefront_slab(int nj, int nk, bool tb) {
   if (nj == 8 && nk == 8) return tb ? sptr<8, 8, true>() : sptr<8, 8, false>();
   if (nj == 4 && nk == 8) return tb ? sptr<4, 8, true>() : sptr<4, 8, false>();
   if (nj == 4 && nk == 4) return tb ? sptr<4, 4, true>() : sptr<4, 4, false>();
+  if (nj == 8 && nk == 4) return tb ? sptr<8, 4, true>() : nullptr;  // traceback only
   return nullptr;
 }
 

@@ -17,6 +17,7 @@ const void* pick_type(int nj, int nk, bool tb) {
   if (nj == 8 && nk == 8) return tb ? vptr<8, 8, true, AT>() : vptr<8, 8, false, AT>();
   if (nj == 4 && nk == 8) return tb ? vptr<4, 8, true, AT>() : vptr<4, 8, false, AT>();
   if (nj == 4 && nk == 4) return tb ? vptr<4, 4, true, AT>() : vptr<4, 4, false, AT>();
+  if (nj == 8 && nk == 4) return tb ? vptr<8, 4, true, AT>() : nullptr;  // traceback only
   return nullptr;
 }
 

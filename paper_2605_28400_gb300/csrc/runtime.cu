@@ -1074,8 +1074,14 @@ trioseq_status trioseq_plan_autotune(trioseq_plan_t plan, const trioseq_triplet*
                                      int32_t* ti) {
   if (!plan || !sample || n == 0 || mode > TRIOSEQ_WITH_TRACEBACK) return TRIOSEQ_EINVAL;
   DeviceGuard g(plan->device);
-  static const Variant kTiles[] = {{8, 8}, {4, 8}, {4, 4}};
+  // candidate tiles per mode; 8x4 exists for traceback keys only
+  static const Variant kScoreTiles[] = {{8, 8}, {4, 8}, {4, 4}};
+  static const Variant kTbTiles[] = {{8, 8}, {4, 8}, {4, 4}, {8, 4}};
   static const int kTI[] = {4, 8, 16, 32};
+  const bool tb_mode = mode == TRIOSEQ_WITH_TRACEBACK;
+  const Variant* tiles = tb_mode ? kTbTiles : kScoreTiles;
+  const size_t ntiles = tb_mode ? sizeof(kTbTiles) / sizeof(kTbTiles[0])
+                                : sizeof(kScoreTiles) / sizeof(kScoreTiles[0]);
   uint32_t maxlen = 0;
   for (size_t t = 0; t < n; t++)
     for (int q = 0; q < 3; q++) maxlen = std::max(maxlen, sample[t].len[q]);
@@ -1090,7 +1096,8 @@ trioseq_status trioseq_plan_autotune(trioseq_plan_t plan, const trioseq_triplet*
   {
     Workspace ws;  // one workspace, grown to the largest candidate
     plan->tuning = true;
-    for (const Variant& v : kTiles) {
+    for (size_t vi = 0; vi < ntiles; vi++) {
+      const Variant& v = tiles[vi];
       for (int ti : kTI) {
         plan->forced = trioseq_plan_s::Tuned{v, ti};
         trioseq_batch_s bt;

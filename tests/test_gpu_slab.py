@@ -60,7 +60,7 @@ def run_one(plan, sc, t, mode):
 
 
 @pytest.mark.parametrize("slices", [1, 7, 64, 1000])
-@pytest.mark.parametrize("tile", ["4x4", "4x8", "8x8"])
+@pytest.mark.parametrize("tile", ["4x4", "4x8", "8x8", "8x4"])
 def test_traceback_slabs_match_oracle(slices, tile):
     w = synth.config2(seed=95, n=1, lo=150, hi=150)
     t = w.triplets[0]

@@ -136,7 +136,7 @@ def check_tb(plan, sc, kind, triplets):
     return got
 
 
-@pytest.mark.parametrize("tile", ["4x4", "4x8", "8x8"])
+@pytest.mark.parametrize("tile", ["4x4", "4x8", "8x8", "8x4"])
 @pytest.mark.parametrize("kinds", KINDS, ids=IDS)
 def test_traceback_exact_all_tiles(kinds, tile):
     flags, kind = kinds

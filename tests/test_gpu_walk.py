@@ -21,7 +21,7 @@ pytestmark = pytest.mark.gpu
 
 DNA = synth.dna_scoring()
 PROT = synth.protein_scoring(1003)
-TILES = ["4x4", "4x8", "8x8"]
+TILES = ["4x4", "4x8", "8x8", "8x4"]
 
 
 def _plan(sc, flags=0, tb_tile=None, slab_slices=None):
