@@ -607,6 +607,8 @@ def main():
     ap.add_argument("--workload", choices=sorted(workloads()), default="protein4000")
     ap.add_argument("--no-aux", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--alu-rate", action="store_true",
+                    help="print the measured int32 instruction-form rates (trioseq_alu_rate) and exit")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -615,6 +617,10 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.alu_rate:  # the roofline's denominator alone (one GPU, no workload)
+        from paper_2605_28400_gb300 import binding as B
+        print(json.dumps(measured_alu(B)))
         return
 
     import torch
