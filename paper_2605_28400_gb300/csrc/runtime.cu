@@ -136,6 +136,7 @@ struct trioseq_plan_s {
   std::unique_ptr<trioseq_batch_s> last;  // last align_batch (traceback rows kept here)
   int TI = 8;
   int64_t wait_ns = 2000000000LL;  // 2 s without progress = give up
+  bool test_wait_unset = false;    // test switch: first-wave warps wait on a flag nothing sets
   bool graphs = true;              // trioseq_batch_run replays a captured CUDA graph
   bool packed16 = true;            // pair score-only global triplets in int16 halves if they fit
   bool sig2_nonneg = false;        // every sigma'' >= 0: the biased packed mode applies
@@ -638,7 +639,14 @@ trioseq_status run(trioseq_batch_s* bt, cudaStream_t st) {
   p.wait_ns = plan->wait_ns;
   p.g2 = -2 * plan->gap;
   p.one = 1;
-  if (!bt->slab && plan->pace && bt->tasks.size() >= 2 * (size_t)bt->grid * kWarpsPerCta) {
+  if (plan->test_wait_unset && !bt->slab) {
+    // Test of the bounded waits: every first-wave task but queue task 0 waits on a word of the
+    // progress buffer that nothing writes (zeroed above), gives up after wait_ns, sets the error
+    // word and returns; the call then reports TRIOSEQ_ETIMEOUT.
+    p.pace_n = bt->grid * kWarpsPerCta;
+    p.pace_T = 1 << 20;
+    p.pace_flag = prog + bt->tasks.size() + 48;
+  } else if (!bt->slab && plan->pace && bt->tasks.size() >= 2 * (size_t)bt->grid * kWarpsPerCta) {
     // pace the first wave against the progress of queue task 0, the (0,0) block of its triplet
     const TripDesc& d0 = bt->desc[bt->tasks[0].trip];
     p.pace_n = bt->grid * kWarpsPerCta;
@@ -919,6 +927,8 @@ trioseq_status trioseq_plan(const trioseq_scoring* sc, uint32_t max_len_hint, ui
   plan->graphs = env_int("TRIOSEQ_GRAPHS", 1) != 0;
   plan->packed16 = env_int("TRIOSEQ_PACKED", 1) != 0;
   plan->pace = env_int("TRIOSEQ_PACE", 1) != 0;
+  plan->wait_ns = (int64_t)std::max(1, env_int("TRIOSEQ_WAIT_MS", 2000)) * 1000000LL;
+  plan->test_wait_unset = env_int("TRIOSEQ_TEST_WAIT_UNSET", 0) != 0;
   {
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
