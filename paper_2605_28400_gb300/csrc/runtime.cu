@@ -29,12 +29,33 @@
 #include <unordered_map>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "engine.h"
 #include "trioseq.h"
 
 using namespace trioseq;
 
 namespace {
+
+// NVTX range for the duration of a scope: plan, autotune, batch, run, traceback and server
+// launches show up by name in profilers that read NVTX (header-only NVTX 3; no cost without one).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// Host-side fault injection for tests: with TRIOSEQ_TEST_FAIL_ALLOC=N at trioseq_plan, the N-th
+// device allocation after it fails as if the device were out of memory.
+std::atomic<long> g_alloc_calls{0};
+std::atomic<long> g_alloc_fail_at{0};
+
+bool injected_alloc_failure() {
+  const long at = g_alloc_fail_at.load(std::memory_order_relaxed);
+  return at > 0 && g_alloc_calls.fetch_add(1, std::memory_order_relaxed) + 1 == at;
+}
 
 struct DevBuf {
   void* p = nullptr;
@@ -48,6 +69,7 @@ struct DevBuf {
   bool ensure(size_t bytes, cudaStream_t st = nullptr) {
     if (bytes <= cap && p) return true;
     const size_t want = std::max<size_t>(bytes, 256);
+    if (injected_alloc_failure()) return false;
     cudaError_t e;
     if (st) {
       if (p) cudaFreeAsync(p, st);
@@ -872,6 +894,7 @@ const char* trioseq_strerror(trioseq_status st) {
 trioseq_status trioseq_plan(const trioseq_scoring* sc, uint32_t max_len_hint, uint32_t flags,
                             trioseq_plan_t* out) {
   (void)max_len_hint;
+  NvtxRange range("trioseq_plan");
   if (!out) return TRIOSEQ_EINVAL;
   *out = nullptr;
   if (!sc || !sc->alphabet || !sc->sub || flags > TRIOSEQ_LOCAL) return TRIOSEQ_EINVAL;
@@ -929,6 +952,8 @@ trioseq_status trioseq_plan(const trioseq_scoring* sc, uint32_t max_len_hint, ui
   plan->pace = env_int("TRIOSEQ_PACE", 1) != 0;
   plan->wait_ns = (int64_t)std::max(1, env_int("TRIOSEQ_WAIT_MS", 2000)) * 1000000LL;
   plan->test_wait_unset = env_int("TRIOSEQ_TEST_WAIT_UNSET", 0) != 0;
+  g_alloc_calls.store(0);
+  g_alloc_fail_at.store(std::max(0, env_int("TRIOSEQ_TEST_FAIL_ALLOC", 0)));
   {
     size_t fr = 0, tot = 0;
     if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
@@ -957,6 +982,7 @@ trioseq_status trioseq_plan_destroy(trioseq_plan_t plan) {
 
 trioseq_status trioseq_align_batch(trioseq_plan_t plan, const trioseq_triplet* triplets, size_t n,
                                    uint32_t mode, int32_t* scores_out, void* stream) {
+  NvtxRange range("trioseq_align_batch");
   if (!plan || (n && !scores_out)) return TRIOSEQ_EINVAL;
   DeviceGuard g(plan->device);
   cudaStream_t st = (cudaStream_t)stream;
@@ -977,6 +1003,7 @@ trioseq_status trioseq_align_batch(trioseq_plan_t plan, const trioseq_triplet* t
 
 trioseq_status trioseq_traceback(trioseq_plan_t plan, size_t idx, char* row0, char* row1,
                                  char* row2, size_t cap, size_t* aln_len) {
+  NvtxRange range("trioseq_traceback");
   if (!plan || !plan->last) return TRIOSEQ_EINVAL;
   return copy_alignment(plan->last.get(), idx, row0, row1, row2, cap, aln_len);
 }
@@ -989,6 +1016,7 @@ trioseq_status trioseq_traceback_span(trioseq_plan_t plan, size_t idx, int32_t b
 
 trioseq_status trioseq_batch_create(trioseq_plan_t plan, const trioseq_triplet* triplets,
                                     size_t n, uint32_t mode, trioseq_batch_t* out) {
+  NvtxRange range("trioseq_batch_create");
   if (!plan || !out) return TRIOSEQ_EINVAL;
   *out = nullptr;
   DeviceGuard g(plan->device);
@@ -1005,6 +1033,7 @@ trioseq_status trioseq_batch_create(trioseq_plan_t plan, const trioseq_triplet* 
 }
 
 trioseq_status trioseq_batch_run(trioseq_batch_t bt, void* stream) {
+  NvtxRange range("trioseq_batch_run");
   if (!bt) return TRIOSEQ_EINVAL;
   DeviceGuard g(bt->plan->device);
   return bt->plan->graphs ? run_graph(bt, (cudaStream_t)stream) : run(bt, (cudaStream_t)stream);
@@ -1082,6 +1111,7 @@ trioseq_status trioseq_batch_timing(trioseq_batch_t bt, float ms[2]) {
 trioseq_status trioseq_plan_autotune(trioseq_plan_t plan, const trioseq_triplet* sample, size_t n,
                                      uint32_t mode, int32_t* tile_j, int32_t* tile_k,
                                      int32_t* ti) {
+  NvtxRange range("trioseq_plan_autotune");
   if (!plan || !sample || n == 0 || mode > TRIOSEQ_WITH_TRACEBACK) return TRIOSEQ_EINVAL;
   DeviceGuard g(plan->device);
   // candidate tiles per mode; 8x4 exists for traceback keys only
@@ -1231,7 +1261,7 @@ struct trioseq_server_s {
   std::vector<trioseq_plan_s*> plans;
   int device = 0;
   size_t slot_budget = 0;
-  size_t max_pending = (size_t)1 << 20;
+  size_t max_pending = (size_t)1 << 20;  // TRIOSEQ_SERVER_MAX_PENDING at creation
   size_t max_batch = 1024;
   std::thread th;
   std::mutex mu;
@@ -1264,6 +1294,7 @@ trioseq_status srv_launch(trioseq_server_s* S, SrvSlot& sl) {
   if (st != TRIOSEQ_OK) return st;
   bt->ws = &sl.ws;
   if ((st = upload(bt, sl.stream, true)) != TRIOSEQ_OK) return st;
+  NvtxRange range("trioseq_server_launch");
   if ((st = run(bt, sl.stream)) != TRIOSEQ_OK) return st;
   const bool tb = mode == TRIOSEQ_WITH_TRACEBACK;
   const size_t n = bt->n, ntb = bt->tb_trips.size();
@@ -1408,6 +1439,7 @@ trioseq_status trioseq_server_create(const trioseq_plan_t* plans, int32_t nplans
     hbm_budget = fr / 10 * 8;
   }
   S->slot_budget = std::max<size_t>(hbm_budget / trioseq_server_s::kSlots, 1 << 20);
+  S->max_pending = (size_t)std::max(0, env_int("TRIOSEQ_SERVER_MAX_PENDING", 1 << 20));
   for (auto& sl : S->slots) {
     if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess)
