@@ -703,6 +703,8 @@ def main():
                           f"{clock_mhz:.0f} MHz sampled in the timed region"
                           + (" x 2 (int16x2 packing)" if packing == 2 else ""),
             "alu_measured": alu}
+    if packing == 2:  # the metric's int32 roof, beside the roof of the int16x2 lanes used
+        roof["frac_of_int32_roof"] = achieved / (peak / 2)
     if tb:
         roof["code_stream_gbs"] = CODE_BYTES_PER_CELL * w.cells / (kmean / 1e3) / 1e9
 

@@ -20,7 +20,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libtrioseq.so")
 SOURCES = ["runtime.cu", "kernels.cu", "kernels_variants.cu", "kernels_packed.cu",
-           "kernels_slab.cu", "noalloc.cu", "alu_rate.cu"]
+           "kernels_slab.cu", "noalloc.cu", "alu_rate.cu", "kernels_vl.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 _lock = threading.Lock()
 
@@ -35,6 +35,7 @@ def nvcc() -> str:
 def _inputs():
     files = [os.path.join(CSRC, s) for s in SOURCES]
     files += [os.path.join(CSRC, "engine.h"), os.path.join(CSRC, "wavefront.cuh"),
+              os.path.join(CSRC, "wavefront_vl.cuh"),
               os.path.join(ROOT, "include", "trioseq.h")]
     return files
 

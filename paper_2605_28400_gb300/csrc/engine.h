@@ -150,6 +150,9 @@ int wavefront_occupancy(int nj, int nk, bool tb, int at, int pk, bool slab, size
 const void* wavefront_variant(int nj, int nk, int at, bool tb);
 // Kernel entry of a packed int16x2 (global, score) instantiation (kernels_packed.cu), or null.
 const void* wavefront_packed(int nj, int nk, int mode);
+// two cells of one triplet per register (wavefront_vl.cuh): nj x nk = 8 x 16 cells per lane
+const void* wavefront_vl(int nj, int nk);
+size_t wavefront_vl_smem_bytes(int nj, int nk, int KP);
 // Kernel entry of a slab-launch instantiation (kernels_slab.cu), or null.
 const void* wavefront_slab(int nj, int nk, bool tb);
 int launch_walk(const WalkParams& p, void* stream);

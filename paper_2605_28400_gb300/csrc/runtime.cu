@@ -383,8 +383,16 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
   //    max|sigma''| * (a+b+c + 3) < 2^14 on the grid's lengths.
   std::vector<std::pair<int32_t, int32_t>> units;  // (low-half triplet, high-half triplet or -1)
   bt->packed = 0;
+  // Two cells of one triplet per register (wavefront_vl.cuh), the 8x16 variant: score-only global
+  // alignment with every sigma'' >= 0 and max sigma'' <= 33 (the kernel's range argument).
+  const bool vl = NJ == 8 && NK == 16;
+  if (vl) {
+    if (tb || plan->atype != kGlobal || !plan->sig2_nonneg || plan->max_abs_sig2 > 33)
+      return TRIOSEQ_ECUDA;  // variant not available for this work (the autotuner skips it)
+    bt->packed = 3;
+  }
   const int pmode = plan->sig2_nonneg ? 2 : 1;
-  if (!tb && plan->atype == kGlobal && plan->packed16 && n >= 2 &&
+  if (!vl && !tb && plan->atype == kGlobal && plan->packed16 && n >= 2 &&
       wavefront_packed(NJ, NK, pmode) != nullptr) {
     std::vector<int32_t> order(n);
     for (size_t t = 0; t < n; t++) order[t] = (int32_t)t;
@@ -409,7 +417,7 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
       units.clear();
     }
   }
-  if (!bt->packed)
+  if (units.empty())  // one unit per triplet (no pairs formed)
     for (size_t t = 0; t < n; t++) units.emplace_back((int32_t)t, -1);
   // 3. Per unit: task grid, boundary records, progress flags, traceback codes and rows.
   for (const auto& un : units) {
@@ -422,7 +430,7 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
     const int a = d.glen[0], b = d.glen[1], c = d.glen[2];
     d.nJ = (b + 1 + WJ - 1) / WJ;
     d.nK = (c + 1 + WK - 1) / WK;
-    d.T = a + 1 + (kPR - 1) + (kPC - 1);
+    d.T = a + 1 + (kPR - 1) + (kPC - 1) + (vl ? kPC : 0);  // vl: 2*kPC virtual lane columns
     // boundary records of every column task: (a+1) x (WK+4) j-records, (a+1) x WJ k-records
     const size_t ntask = (size_t)d.nJ * (size_t)d.nK;
     d.oj_off = (int64_t)face;
@@ -455,6 +463,9 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
       rows += align_up((size_t)3 * cap, 16);
     }
   }
+  // The two-per-register kernel has no slab form: a triplet whose records exceed the slab budget
+  // takes the int32 kernels (reported as unavailable, so the autotuner moves on).
+  if (vl && 4 * face > plan->slab_budget) return TRIOSEQ_ECUDA;
   // 4. Slab mode: one global-type int32 triplet whose boundary records (and, with traceback,
   //    codes) would exceed the plan's budget at once, or any such triplet when a slab height is
   //    forced. The cube then runs slab by slab, each launch seeded from the plane the slab below
@@ -564,7 +575,8 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
   off = align_up(off + sizeof(int32_t) * std::max<size_t>(bt->row_cap.size(), 1), 256);
   bt->inputs_bytes = off;
   // launch shape
-  bt->smem = wavefront_smem_bytes(NJ, NK, plan->KP, bt->packed != 0);
+  bt->smem = bt->packed == 3 ? wavefront_vl_smem_bytes(NJ, NK, plan->KP)
+                             : wavefront_smem_bytes(NJ, NK, plan->KP, bt->packed != 0);
   int bpm = 0;
   if (wavefront_occupancy(NJ, NK, tb, plan->atype, bt->packed, bt->slab > 0, bt->smem, &bpm) !=
           0 ||
@@ -964,10 +976,17 @@ trioseq_status trioseq_plan(const trioseq_scoring* sc, uint32_t max_len_hint, ui
     plan->slab_budget = mb > 0 ? (size_t)mb << 20 : fr / 2;
     plan->slab_slices = std::max(0, env_int("TRIOSEQ_SLAB_SLICES", 0));
   }
-  const char* sv = std::getenv("TRIOSEQ_SCORE_TILE");
-  if (sv && std::strlen(sv) >= 3) plan->score_variant = Variant{sv[0] - '0', sv[2] - '0'};
-  const char* tv = std::getenv("TRIOSEQ_TB_TILE");
-  if (tv && std::strlen(tv) >= 3) plan->tb_variant = Variant{tv[0] - '0', tv[2] - '0'};
+  // "RxC": register tile rows x columns per lane
+  const auto parse_tile = [](const char* v, Variant* out) {
+    if (!v) return;
+    char* end = nullptr;
+    const long rj = std::strtol(v, &end, 10);
+    if (!end || *end != 'x') return;
+    const long ck = std::strtol(end + 1, nullptr, 10);
+    if (rj > 0 && rj <= 16 && ck > 0 && ck <= 32) *out = Variant{(int)rj, (int)ck};
+  };
+  parse_tile(std::getenv("TRIOSEQ_SCORE_TILE"), &plan->score_variant);
+  parse_tile(std::getenv("TRIOSEQ_TB_TILE"), &plan->tb_variant);
   *out = plan.release();
   return TRIOSEQ_OK;
 }
@@ -1115,7 +1134,7 @@ trioseq_status trioseq_plan_autotune(trioseq_plan_t plan, const trioseq_triplet*
   if (!plan || !sample || n == 0 || mode > TRIOSEQ_WITH_TRACEBACK) return TRIOSEQ_EINVAL;
   DeviceGuard g(plan->device);
   // candidate tiles per mode; 8x4 exists for traceback keys only
-  static const Variant kScoreTiles[] = {{8, 8}, {4, 8}, {4, 4}};
+  static const Variant kScoreTiles[] = {{8, 8}, {4, 8}, {4, 4}, {8, 16}};  // 8x16: two per register
   static const Variant kTbTiles[] = {{8, 8}, {4, 8}, {4, 4}, {8, 4}};
   static const int kTI[] = {4, 8, 16, 32};
   const bool tb_mode = mode == TRIOSEQ_WITH_TRACEBACK;

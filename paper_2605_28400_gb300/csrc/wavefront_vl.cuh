@@ -1,0 +1,472 @@
+// wavefront_vl.cuh — score-only global wavefront kernel with two cells of one triplet per
+// register ("virtual lanes"), for scoring schemes whose sigma'' are all >= 0.
+//
+// wavefront_vl_kernel<NJ, NH>: the column-task engine of wavefront.cuh (same queue, boundary
+// records, progress flags, staging ring and bounded waits; Eq. 1 in the shifted frame of engine.h),
+// with each lane's NJ x 2NH tile held as NJ x NH registers of two 16-bit halves:
+//  * Layout. The low half holds the left NH columns of the tile at slice s = t - r - 2*lc, the
+//    high half the right NH columns one slice behind (s - 1). The 4 x 8 lanes thus act as 4 x 16
+//    virtual lanes of NJ x NH tiles on the usual anti-diagonal skew, and every halo comes from a
+//    step already finished: rows and the corner by the same packed shuffles as a plain tile, the
+//    high half's left column from the low half's previous right column (one PRMT per row).
+//  * Arithmetic. The cell passes are those of the biased packed mode (engine.h): each half holds
+//    M' - B + 2^14 with -infinity = 0, the diagonal sum runs as two 32-bit multiply-adds on the
+//    FMA pipe, the maxima as unsigned 16x2 DPX add-max operations.
+//  * Range. With every sigma'' >= 0, M' is non-decreasing along each axis and adjacent cells differ
+//    by at most 2*max sigma'' (follow the optimal path to the farther cell back to where it enters
+//    the farther plane and copy its in-plane moves one plane lower: in-plane costs do not depend
+//    on the third coordinate). A warp's working set (19 slices of a 32 x 128 block plus halos, L1
+//    diameter <= 178) therefore spans at most 356*max sigma''. Each warp keeps one base B for
+//    its task, warp-uniform, so shuffled halos need no conversion; B is moved by the drift of
+//    lane 0's first cell whenever that exceeds 2048 (all halves rebased with a signed 16x2
+//    add-max against 0, which keeps -infinity at 0). The host admits the mode only for
+//    max sigma'' <= 33, so every half stays within [1, 2^16) with margin and no add wraps.
+//  * Records stay absolute int32 (converted on store and on staging), so tasks are decoupled and
+//    the record layout is the plain kernel's with WK = 8 lanes x 2NH columns.
+//  * Edges of a task's sweep: the high half of a lane is inactive while the low half computes
+//    slice 0 (it is reset to -infinity afterwards); the low half's extra slice a + 1 at the end is
+//    computed on virtual residues and never stored.
+#pragma once
+#include "wavefront.cuh"
+
+namespace trioseq {
+
+constexpr int kVlBias = 1 << 14;
+
+template <int NJ, int NH>
+struct VlGeom {
+  static constexpr int NK = 2 * NH;                  // cell columns per lane
+  static constexpr int WJ = kPR * NJ, WK = kPC * NK;
+  static constexpr int RJ = WK + 4, RK = WJ;          // record strides (ints)
+  static constexpr int PJ = WJ + 4, PK = WK + 4;      // padded profile rows
+  static constexpr int SEGL = NH + 4, SEGH = NH;      // staged j-record ints per lane column
+  static constexpr int SEGC = SEGL + SEGH;
+  static constexpr int SLOT = kPC * SEGC + kPR * NJ;  // ints per ring slot
+  static constexpr int PL = SEGL / 4, PH = SEGH / 4;  // 16-byte pieces per lane column
+  static constexpr int PKR = NJ / 4;                  // 16-byte pieces per lane row (k-records)
+  static constexpr int NPIECE = kPC * (PL + PH) + kPR * PKR;
+  static constexpr int NPL = (NPIECE + 31) / 32;      // pieces per lane
+};
+
+template <int NJ, int NH>
+__global__ void __launch_bounds__(kWarpsPerCta * 32, 2) wavefront_vl_kernel(const WaveParams p) {
+  using G = VlGeom<NJ, NH>;
+  static_assert(NJ % 4 == 0 && NH % 4 == 0, "tile sides must be multiples of 4");
+  constexpr int NK = G::NK, WJ = G::WJ, WK = G::WK;
+  constexpr int NEG = 0;  // -infinity in both halves
+  extern __shared__ int4 smem4[];
+  int* smem = reinterpret_cast<int*>(smem4);
+  const int KP = p.KP;
+  const int VIRT = KP - 1;
+  const int sigN = (KP * KP + 3) & ~3;
+  int* sig = smem;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int* profJ = smem + sigN + warp * (KP * (G::PJ + G::PK) + kRing * G::SLOT);
+  int* profK = profJ + KP * G::PJ;
+  int* ring = profK + KP * G::PK;
+  for (int e = threadIdx.x; e < KP * KP; e += blockDim.x) sig[e] = p.sig[e];
+  __syncthreads();
+  const int r = lane >> 3, lc = lane & 7;
+
+  // This lane's staging pieces: record kind (1 j, 2 k), slice delta, record slot, ring slot.
+  int cp_kind[G::NPL], cp_delta[G::NPL], cp_col[G::NPL], cp_dst[G::NPL];
+#pragma unroll
+  for (int m = 0; m < G::NPL; ++m) {
+    const int q = lane + 32 * m;
+    cp_kind[m] = 0;
+    cp_delta[m] = 0;
+    cp_col[m] = 0;
+    cp_dst[m] = 0;
+    if (q < kPC * (G::PL + G::PH)) {
+      const int l = q / (G::PL + G::PH), w = q % (G::PL + G::PH);
+      cp_kind[m] = 1;
+      if (w < G::PL) {  // low half of lane column l: slice u - 2l, record slots from l*NK
+        cp_delta[m] = 2 * l;
+        cp_col[m] = l * NK + 4 * w;
+        cp_dst[m] = l * G::SEGC + 4 * w;
+      } else {  // high half: slice u - 2l - 1, the right NH columns
+        const int w2 = w - G::PL;
+        cp_delta[m] = 2 * l + 1;
+        cp_col[m] = 4 + l * NK + NH + 4 * w2;
+        cp_dst[m] = l * G::SEGC + G::SEGL + 4 * w2;
+      }
+    } else if (q < G::NPIECE) {  // k-record of lane row rr (low half of virtual column 0)
+      const int q2 = q - kPC * (G::PL + G::PH);
+      const int rr = q2 / G::PKR, bb = q2 % G::PKR;
+      cp_kind[m] = 2;
+      cp_delta[m] = rr;
+      cp_col[m] = rr * NJ + 4 * bb;
+      cp_dst[m] = kPC * G::SEGC + rr * NJ + 4 * bb;
+    }
+  }
+
+  for (;;) {
+    int task = 0;
+    if (lane == 0) task = atomicAdd(p.queue, 1);
+    task = __shfl_sync(kFull, task, 0);
+    if (task >= p.ntasks) return;
+    if (task < p.pace_n && task > 0) {  // first-wave pacing, as in wavefront_kernel
+      const int need = (int)((long long)task * p.pace_T / p.pace_n);
+      bool okp = true;
+      int seen = 0;
+      if (lane == 0 && need > 0) okp = wait_flag(p.pace_flag, need, &seen, p.wait_ns);
+      if (!__shfl_sync(kFull, okp, 0)) {
+        if (lane == 0) atomicOr(p.err, 1);
+        return;
+      }
+    }
+    const Task tk = p.tasks[task];
+    const TripDesc& d = p.desc[tk.trip];
+    const int a = d.len[0], b = d.len[1], c = d.len[2];
+    const int nJ = d.nJ, nK = d.nK, T = d.T;
+    const int J = tk.J, K = tk.K;
+    const int8_t* S0 = p.seq + d.s_off[0];
+    const int8_t* S1 = p.seq + d.s_off[1];
+    const int8_t* S2 = p.seq + d.s_off[2];
+    const int j0 = J * WJ + r * NJ, k0 = K * WK + lc * NK;
+    const int me = J * nK + K;
+
+    // Profiles of this block: profJ[x][jl] = sigma''(x, y_(J*WJ+jl)), profK[x][kl] =
+    // sigma''(x, z_(K*WK+kl)); residue index 0 and beyond the end are VIRT.
+    __syncwarp();
+    for (int e = lane; e < KP * WJ; e += 32) {
+      const int x = e / WJ, jl = e - x * WJ, j = J * WJ + jl;
+      const int y = (j >= 1 && j <= b) ? (int)S1[j - 1] : VIRT;
+      profJ[x * G::PJ + jl] = sig[x * KP + y];
+    }
+    for (int e = lane; e < KP * WK; e += 32) {
+      const int x = e / WK, kl = e - x * WK, k = K * WK + kl;
+      const int z = (k >= 1 && k <= c) ? (int)S2[k - 1] : VIRT;
+      profK[x * G::PK + kl] = sig[x * KP + z];
+    }
+    // sigma''(y_j, z_k) for both halves (left and right NH columns), packed, for the whole task
+    int Cv[NJ][NH];
+    {
+      int yo[NJ];
+#pragma unroll
+      for (int pp = 0; pp < NJ; ++pp) {
+        const int j = j0 + pp;
+        yo[pp] = ((j >= 1 && j <= b) ? (int)S1[j - 1] : VIRT) * KP;
+      }
+#pragma unroll
+      for (int qq = 0; qq < NH; ++qq) {
+        const int kl = k0 + qq, kh = k0 + NH + qq;
+        const int zl = (kl >= 1 && kl <= c) ? (int)S2[kl - 1] : VIRT;
+        const int zh = (kh >= 1 && kh <= c) ? (int)S2[kh - 1] : VIRT;
+#pragma unroll
+        for (int pp = 0; pp < NJ; ++pp)
+          Cv[pp][qq] = (int)__byte_perm(sig[yo[pp] + zl], sig[yo[pp] + zh], 0x5410);
+      }
+    }
+    __syncwarp();
+
+    // Owner of the final cell (a, b, c): its lane, half and tile cell.
+    const int endK = c % WK;
+    const bool owns_end = (J == b / WJ) && (K == c / WK) && (r == (b % WJ) / NJ) &&
+                          (lc == endK / NK);
+    const int end_p = b % NJ, end_h = (endK % NK) >= NH, end_q = (endK % NK) % NH;
+
+    int P[NJ][NH];
+    int rowA[NH + 1], colA[NJ], rowB[NH + 1], colB[NJ];
+#pragma unroll
+    for (int pp = 0; pp < NJ; ++pp) {
+#pragma unroll
+      for (int qq = 0; qq < NH; ++qq) P[pp][qq] = NEG;
+      colA[pp] = NEG;
+      colB[pp] = NEG;
+    }
+#pragma unroll
+    for (int qq = 0; qq <= NH; ++qq) {
+      rowA[qq] = NEG;
+      rowB[qq] = NEG;
+    }
+
+    const int64_t recJ = (int64_t)(a + 1) * G::RJ, recK = (int64_t)(a + 1) * G::RK;
+    int* const faces = p.faces;
+    const int* srcJ = faces + d.oj_off + (int64_t)(me - nK) * recJ;  // producer (J-1, K)
+    const int* srcK = faces + d.ok_off + (int64_t)(me - 1) * recK;   // producer (J, K-1)
+    int* dstJ = faces + d.oj_off + (int64_t)me * recJ;
+    int* dstK = faces + d.ok_off + (int64_t)me * recK;
+    const bool has_out_j = (J + 1 < nJ), has_out_k = (K + 1 < nK);
+    const int* progJ = p.progress + d.prog_base + (me - nK);
+    const int* progK = p.progress + d.prog_base + (me - 1);
+    int* progMe = p.progress + d.prog_base + me;
+    int cachedJ = J > 0 ? 0 : 1 << 30, cachedK = K > 0 ? 0 : 1 << 30;  // warp-uniform
+    bool ok = true;
+
+    // Face pieces (absolute int32 records, kNeg where absent): loaded two steps ahead, parked one
+    // step ahead, read by the edge lanes and converted to the task's base there.
+    int4 pf[G::NPL];
+#pragma unroll
+    for (int m = 0; m < G::NPL; ++m) pf[m] = make_int4(kNeg, kNeg, kNeg, kNeg);
+    int pf_u = -1;
+    auto fetch = [&](int u) {
+      // k-records are written by the last virtual lane column (2*kPC - 1 steps of skew)
+      const int needJ = min(u + kPR, T), needK = min(u + 2 * kPC, T);
+      if (cachedJ < needJ || cachedK < needK) {  // warp-uniform
+        bool okl = true;
+        int cj = cachedJ, ck = cachedK;
+        if (lane == 0) {
+          if (cj < needJ) okl = wait_flag(progJ, needJ, &cj, p.wait_ns);
+          if (okl && ck < needK) okl = wait_flag(progK, needK, &ck, p.wait_ns);
+        }
+        ok = __shfl_sync(kFull, okl, 0);
+        cachedJ = __shfl_sync(kFull, cj, 0);
+        cachedK = __shfl_sync(kFull, ck, 0);
+        __syncwarp();
+      }
+      pf_u = u;
+#pragma unroll
+      for (int m = 0; m < G::NPL; ++m) {
+        const int sl = u - cp_delta[m];
+        const bool have = ok && cp_kind[m] != 0 && sl >= 0 && sl <= a &&
+                          (cp_kind[m] == 1 ? J > 0 : K > 0);
+        const int* src = (cp_kind[m] == 1) ? srcJ + (int64_t)sl * G::RJ + cp_col[m]
+                                           : srcK + (int64_t)sl * G::RK + cp_col[m];
+        pf[m] = ld_cg_if(reinterpret_cast<const int4*>(src), have, kNeg);
+      }
+    };
+    auto park = [&]() {
+#pragma unroll
+      for (int m = 0; m < G::NPL; ++m)
+        st_shared_if(reinterpret_cast<int4*>(ring + (pf_u & (kRing - 1)) * G::SLOT + cp_dst[m]),
+                     pf[m], cp_kind[m] != 0);
+    };
+
+    fetch(0);
+    // The task's base: the largest record value its first slice borders (0 without producers);
+    // every cell of the working set lies within the range argument of it.
+    int Bt = 0;
+    {
+      int mx = kNeg;
+#pragma unroll
+      for (int m = 0; m < G::NPL; ++m)
+        mx = max(mx, max(max(pf[m].x, pf[m].y), max(pf[m].z, pf[m].w)));
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(kFull, mx, off));
+      Bt = mx > kNeg / 2 ? mx : 0;
+    }
+    int nb = kVlBias - Bt;  // absolute M' -> biased half: max(v + nb, 0)
+    // M'[-1][-1][-1] = 0 feeds the origin through the (1,1,1) move (low half of lane 0).
+    if (J == 0 && K == 0 && lane == 0) rowB[0] = kVlBias - Bt;
+    park();
+    fetch(1);
+
+    auto xblock = [&](int base) -> int {
+      const int sl = base + lane;
+      return (sl >= 1 && sl <= a) ? (int)__ldg(S0 + sl - 1) : VIRT;
+    };
+    int xprev = VIRT, xcur = xblock(0), xnext = xblock(32);
+    int xlo_prev = VIRT;  // residue of slice s - 1: the high half's
+
+    int pub_in = p.TI;
+    auto step = [&](const int t, int (&rowCur)[NH + 1], const int (&rowPrev)[NH + 1],
+                    int (&colCur)[NJ], const int (&colPrev)[NJ]) -> bool {
+      const int s = t - r - 2 * lc;
+      park();
+      if (t + 2 < T) fetch(t + 2);
+      if (!ok) return false;
+      if ((t & 31) == 0 && t > 0) {
+        xprev = xcur;
+        xcur = xnext;
+        xnext = xblock(t + 32);
+      }
+      // this lane's slice s lies in [t - 17, t]: in the current or the previous block
+      const int xa = __shfl_sync(kFull, xcur, s & 31);
+      const int xb = __shfl_sync(kFull, xprev, s & 31);
+      const int xl = (s >= (t & ~31)) ? xa : xb;  // low half: slice s
+      const int xh = xlo_prev;                    // high half: slice s - 1
+      xlo_prev = xl;
+      __syncwarp();
+      {
+        const int* sl = ring + (t & (kRing - 1)) * G::SLOT;
+        const int* rs = sl + lc * G::SEGC;          // low half: corner + NH columns, slice s
+        const int* rh = rs + G::SEGL;               // high half: NH columns, slice s - 1
+        const int* cs = sl + kPC * G::SEGC + r * NJ;  // k-record rows, slice s
+        // row halo: lane above (packed shuffle), or the staged j-record (first lane row)
+        const int corner_send = colPrev[NJ - 1];
+#pragma unroll
+        for (int qq = 0; qq <= NH; ++qq) {
+          const int send = qq == 0 ? corner_send : P[NJ - 1][qq - 1];
+          const int v = __shfl_up_sync(kFull, send, kPC);
+          const unsigned lo = (unsigned)max(rs[3 + qq] + nb, 0);
+          // the high half's corner (j0-1, k0+NH-1) at slice s-1 is the low half's last row
+          // halo of the previous step
+          const unsigned hi = qq == 0 ? ((unsigned)rowPrev[NH] & 0xffffu)
+                                      : (unsigned)max(rh[qq - 1] + nb, 0);
+          rowCur[qq] = (r == 0) ? (int)__byte_perm(lo, hi, 0x5410) : v;
+        }
+        // column halo: low half from the left lane's high half (or the staged k-record in the
+        // first lane column), high half from this lane's low half; both from the previous step
+#pragma unroll
+        for (int pp = 0; pp < NJ; ++pp) {
+          const int mine = P[pp][NH - 1];
+          const int v = __shfl_up_sync(kFull, mine, 1);
+          const unsigned ring_lo = (unsigned)max(cs[pp] + nb, 0);
+          colCur[pp] = (lc == 0) ? (int)__byte_perm(ring_lo, (unsigned)mine, 0x5410)
+                                 : (int)__byte_perm((unsigned)v, (unsigned)mine, 0x5432);
+        }
+      }
+
+      const bool active = s >= 0 && s <= a + 1;
+      if (active) {
+        int A[NJ], Bq[NH];
+        {
+          const int4* pl = reinterpret_cast<const int4*>(profJ + xl * G::PJ + r * NJ);
+          const int4* ph = reinterpret_cast<const int4*>(profJ + xh * G::PJ + r * NJ);
+#pragma unroll
+          for (int p4 = 0; p4 < NJ / 4; ++p4) {
+            const int4 u = pl[p4], v = ph[p4];
+            A[4 * p4] = (int)__byte_perm(u.x, v.x, 0x5410);
+            A[4 * p4 + 1] = (int)__byte_perm(u.y, v.y, 0x5410);
+            A[4 * p4 + 2] = (int)__byte_perm(u.z, v.z, 0x5410);
+            A[4 * p4 + 3] = (int)__byte_perm(u.w, v.w, 0x5410);
+          }
+          const int4* ql = reinterpret_cast<const int4*>(profK + xl * G::PK + lc * NK);
+          const int4* qh = reinterpret_cast<const int4*>(profK + xh * G::PK + lc * NK + NH);
+#pragma unroll
+          for (int q4 = 0; q4 < NH / 4; ++q4) {
+            const int4 u = ql[q4], v = qh[q4];
+            Bq[4 * q4] = (int)__byte_perm(u.x, v.x, 0x5410);
+            Bq[4 * q4 + 1] = (int)__byte_perm(u.y, v.y, 0x5410);
+            Bq[4 * q4 + 2] = (int)__byte_perm(u.z, v.z, 0x5410);
+            Bq[4 * q4 + 3] = (int)__byte_perm(u.w, v.w, 0x5410);
+          }
+        }
+        // Two passes in place, as in the biased packed mode of wavefront_kernel.
+        auto pass1 = [&](const int pp, const int qq) {
+          const int Pd = (pp == 0) ? rowPrev[qq] : (qq == 0 ? colPrev[pp - 1] : P[pp - 1][qq - 1]);
+          const int Pxy = (pp == 0) ? rowPrev[qq + 1] : P[pp - 1][qq];
+          const int Pxz = (qq == 0) ? colPrev[pp] : P[pp][qq - 1];
+          const int Sx = P[pp][qq];
+          const unsigned x2 = (unsigned)mad_lo(Bq[qq], p.one, mad_lo(A[pp], p.one, Pd));
+          unsigned e = __viaddmax_u16x2((unsigned)Pxy, (unsigned)A[pp], (unsigned)Sx);
+          e = __viaddmax_u16x2((unsigned)Pxz, (unsigned)Bq[qq], e);
+          P[pp][qq] = (int)__viaddmax_u16x2(x2, (unsigned)Cv[pp][qq], e);
+        };
+        auto pass2 = [&](const int pp, const int qq) {
+          const int Myz = (pp == 0) ? rowCur[qq] : (qq == 0 ? colCur[pp - 1] : P[pp - 1][qq - 1]);
+          const int Sy = (pp == 0) ? rowCur[qq + 1] : P[pp - 1][qq];
+          const int Sz = (qq == 0) ? colCur[pp] : P[pp][qq - 1];
+          const unsigned q =
+              __viaddmax_u16x2((unsigned)Myz, (unsigned)Cv[pp][qq], (unsigned)P[pp][qq]);
+          P[pp][qq] = (int)__vimax3_u16x2(q, (unsigned)Sy, (unsigned)Sz);
+        };
+#pragma unroll
+        for (int dg = NJ + NH - 2; dg >= 0; --dg) {
+#pragma unroll
+          for (int pp = NJ - 1; pp >= 0; --pp) {
+            const int qq = dg - pp;
+            if (qq >= 0 && qq < NH) pass1(pp, qq);
+          }
+        }
+#pragma unroll
+        for (int dg = 0; dg < NJ + NH - 1; ++dg) {
+#pragma unroll
+          for (int pp = 0; pp < NJ; ++pp) {
+            const int qq = dg - pp;
+            if (qq >= 0 && qq < NH) pass2(pp, qq);
+          }
+        }
+        if (s == 0) {  // the high half was at slice -1: -infinity there, and in its halos
+#pragma unroll
+          for (int pp = 0; pp < NJ; ++pp) {
+#pragma unroll
+            for (int qq = 0; qq < NH; ++qq) P[pp][qq] &= 0xffff;
+            colCur[pp] &= 0xffff;
+          }
+#pragma unroll
+          for (int qq = 0; qq <= NH; ++qq) rowCur[qq] &= 0xffff;
+        }
+      }
+      if (--pub_in == 0) {
+        pub_in = p.TI;
+        __syncwarp();
+        if (lane == 0) st_release(progMe, t);
+      }
+      if (active) {
+        const int ub = Bt - kVlBias;  // biased half -> absolute M'
+        const bool lo_in = s <= a, hi_in = s >= 1;
+        {  // j-record: the last lane row's bottom tile row; low half at s, high half at s - 1
+          const bool out_j = r == kPR - 1 && has_out_j;
+          int* dl = dstJ + (int64_t)s * G::RJ;
+          int* dh = dstJ + (int64_t)(s - 1) * G::RJ;
+          // the corner: -infinity (0) on the k = 0 face goes out as the absolute sentinel;
+          // every other stored half is a computed cell, always finite
+          const int cb = (int)((unsigned)colCur[NJ - 1] & 0xffffu);
+          st_global_if(dl + 3, cb == 0 ? kNeg : cb + ub, out_j && lo_in && lc == 0);
+#pragma unroll
+          for (int q4 = 0; q4 < NH / 4; ++q4) {
+            int lo[4], hi[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const unsigned v = (unsigned)P[NJ - 1][4 * q4 + e];
+              lo[e] = (int)(v & 0xffffu) + ub;
+              hi[e] = (int)(v >> 16) + ub;
+            }
+            st_global_if(reinterpret_cast<int4*>(dl + 4 + lc * NK) + q4,
+                         make_int4(lo[0], lo[1], lo[2], lo[3]), out_j && lo_in);
+            st_global_if(reinterpret_cast<int4*>(dh + 4 + lc * NK + NH) + q4,
+                         make_int4(hi[0], hi[1], hi[2], hi[3]), out_j && hi_in);
+          }
+        }
+        {  // k-record: the block's last column is the last lane column's high half, slice s - 1
+          const bool out_k = lc == kPC - 1 && has_out_k && hi_in;
+          int* dk = dstK + (int64_t)(s - 1) * G::RK + r * NJ;
+#pragma unroll
+          for (int p4 = 0; p4 < NJ / 4; ++p4) {
+            int v[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) v[e] = (int)((unsigned)P[4 * p4 + e][NH - 1] >> 16) + ub;
+            st_global_if(reinterpret_cast<int4*>(dk) + p4, make_int4(v[0], v[1], v[2], v[3]),
+                         out_k);
+          }
+        }
+        if (owns_end && (end_h ? s - 1 == a : s == a)) {
+          unsigned v = 0;
+#pragma unroll
+          for (int pp = 0; pp < NJ; ++pp)
+#pragma unroll
+            for (int qq = 0; qq < NH; ++qq)
+              if (pp == end_p && qq == end_q) v = (unsigned)P[pp][qq];
+          const int h16 = end_h ? (int)(v >> 16) : (int)(v & 0xffffu);
+          p.scores[d.out_idx] = h16 + ub + d.score_base;
+        }
+      }
+      return true;
+    };
+    // Rebase the task when lane 0's first cell drifts 2048 from the bias (warp-uniform; after an
+    // odd step, whose current halos are in rowB / colB).
+    auto rebase = [&]() {
+      const int ref = __shfl_sync(kFull, (int)((unsigned)P[0][0] & 0xffffu), 0);
+      const int dlt = ref - kVlBias;
+      if (ref != 0 && (dlt >= 2048 || dlt <= -2048)) {
+        const unsigned m = (unsigned)((-dlt) & 0xffff) * 0x10001u;  // -dlt in both halves
+#pragma unroll
+        for (int pp = 0; pp < NJ; ++pp) {
+#pragma unroll
+          for (int qq = 0; qq < NH; ++qq)
+            P[pp][qq] = (int)__viaddmax_s16x2((unsigned)P[pp][qq], m, 0u);
+          colB[pp] = (int)__viaddmax_s16x2((unsigned)colB[pp], m, 0u);
+        }
+#pragma unroll
+        for (int qq = 0; qq <= NH; ++qq) rowB[qq] = (int)__viaddmax_s16x2((unsigned)rowB[qq], m, 0u);
+        Bt += dlt;
+        nb = kVlBias - Bt;
+      }
+    };
+    for (int t = 0; t < T; t += 2) {
+      if (!step(t, rowA, rowB, colA, colB)) break;
+      if (t + 1 < T && !step(t + 1, rowB, rowA, colB, colA)) break;
+      rebase();
+    }
+    __syncwarp();
+    if (ok && lane == 0) st_release(progMe, T);
+    if (!ok) {
+      if (lane == 0) atomicOr(p.err, 1);
+      return;
+    }
+  }
+}
+
+}  // namespace trioseq

@@ -1,0 +1,155 @@
+"""GPU parity of the two-cells-per-register score kernel (wavefront_vl.cuh, tile 8x16) against the
+CPU oracle, bit for bit.
+
+The kernel holds two column halves of one lane tile as the 16-bit halves of each register, the
+high half one slice behind, against a per-task base that moves as the values grow. Cases: every
+shape up to 5^3, ragged multi-block shapes for DNA and protein (several column tasks, tails in
+both halves, empty sequences), related batches, medium triplets whose values force many
+rebases, and the full-size workloads against the int32 kernel, which is itself checked against
+the oracle elsewhere.
+"""
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2605_28400_gb300 import binding as B
+from paper_2605_28400_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+DNA = synth.dna_scoring()
+PROT = synth.protein_scoring(1003)
+
+
+def _plan(sc, tile="8x16"):
+    old = os.environ.get("TRIOSEQ_SCORE_TILE")
+    os.environ["TRIOSEQ_SCORE_TILE"] = tile
+    try:
+        return B.trioseq_plan(sc.alphabet, sc.sub, sc.gap)
+    finally:
+        if old is None:
+            os.environ.pop("TRIOSEQ_SCORE_TILE", None)
+        else:
+            os.environ["TRIOSEQ_SCORE_TILE"] = old
+
+
+def strs(trip, sc):
+    return [synth.to_str(s, sc.alphabet) for s in trip]
+
+
+def rand_trip(rng, shape, K):
+    return tuple(rng.integers(0, K, size=n).astype(np.uint8) for n in shape)
+
+
+def check(plan, sc, trips):
+    got = B.trioseq_align_batch(plan, [strs(t, sc) for t in trips])
+    want = oracle.align_many(trips, sc.sub, sc.gap)
+    assert got.tolist() == want.tolist()
+
+
+def test_vl_is_selected_for_nonnegative_schemes():
+    plan = _plan(DNA)
+    try:
+        bt = B.trioseq_batch_create(plan, [["ACGT" * 20, "ACG" * 20, "AGT" * 20]])
+        try:
+            info = B.trioseq_batch_info(bt)
+            assert info["tile"] == (8, 16) and info["packing"] == 2
+        finally:
+            B.trioseq_batch_destroy(bt)
+    finally:
+        B.trioseq_plan_destroy(plan)
+
+
+def test_vl_all_tiny_shapes_one_batch():
+    rng = np.random.default_rng(51)
+    trips = [rand_trip(rng, s, 4) for s in itertools.product(range(6), repeat=3)]
+    plan = _plan(DNA)
+    try:
+        check(plan, DNA, trips)
+    finally:
+        B.trioseq_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("sc", [DNA, PROT], ids=["dna", "protein"])
+def test_vl_ragged_multi_block(sc):
+    rng = np.random.default_rng(52)
+    shapes = [(37, 70, 130), (129, 33, 65), (0, 100, 100), (100, 0, 77), (64, 64, 0),
+              (200, 1, 250), (5, 260, 3), (31, 32, 63), (33, 65, 129), (17, 127, 128),
+              (40, 135, 257), (1, 1, 1), (0, 0, 0)]
+    trips = [rand_trip(rng, s, len(sc.alphabet)) for s in shapes]
+    plan = _plan(sc)
+    try:
+        check(plan, sc, trips)
+        for t in trips[:4]:  # alone as well as in the batch
+            check(plan, sc, [t])
+    finally:
+        B.trioseq_plan_destroy(plan)
+
+
+def test_vl_related_batch_and_rebasing():
+    w = synth.config2(seed=98, n=24, lo=40, hi=300)
+    big = synth.config1(seed=99, L=600).triplets  # values grow past many rebase thresholds
+    prot = synth.config3(seed=97, L=420)
+    plan = _plan(DNA)
+    try:
+        check(plan, DNA, w.triplets + big)
+    finally:
+        B.trioseq_plan_destroy(plan)
+    plan = _plan(prot.scoring)
+    try:
+        check(plan, prot.scoring, prot.triplets)
+    finally:
+        B.trioseq_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("which", ["config1", "config3"])
+def test_vl_full_size_equals_int32(which):
+    w = synth.config1() if which == "config1" else synth.config3()
+    s = [strs(t, w.scoring) for t in w.triplets]
+    ref = _plan(w.scoring, "8x8")
+    vl = _plan(w.scoring)
+    try:
+        want = B.trioseq_align_batch(ref, s)
+        got = B.trioseq_align_batch(vl, s)
+        assert got.tolist() == want.tolist()
+    finally:
+        B.trioseq_plan_destroy(vl)
+        B.trioseq_plan_destroy(ref)
+
+
+def test_vl_unavailable_cases():
+    """Schemes with a negative sigma'' and the semi-global / local types cannot take the
+    two-per-register kernel: forcing its tile reports the variant as unavailable (the autotuner
+    then skips it). Traceback keeps its own tile and stays exact on the same plan."""
+    neg = np.full((4, 4), -10, dtype=np.int8)  # sigma'' = -10 + 4 < 0 off the diagonal
+    np.fill_diagonal(neg, 2)
+    old = os.environ.get("TRIOSEQ_SCORE_TILE")
+    os.environ["TRIOSEQ_SCORE_TILE"] = "8x16"
+    try:
+        plan = B.trioseq_plan("ACGT", neg, -2)
+        semi = B.trioseq_plan(DNA.alphabet, DNA.sub, DNA.gap, B.SEMIGLOBAL)
+    finally:
+        if old is None:
+            os.environ.pop("TRIOSEQ_SCORE_TILE", None)
+        else:
+            os.environ["TRIOSEQ_SCORE_TILE"] = old
+    try:
+        for pl in (plan, semi):
+            with pytest.raises(B.TrioseqError) as e:
+                B.trioseq_align_batch(pl, [["ACGT", "ACG", "AGT"]])
+            assert e.value.status == B.ECUDA
+    finally:
+        B.trioseq_plan_destroy(semi)
+        B.trioseq_plan_destroy(plan)
+    plan = _plan(DNA)
+    try:
+        t = tuple(np.array([DNA.alphabet.index(ch) for ch in x], dtype=np.uint8)
+                  for x in ("ACGTTGCA", "ACGTGCA", "AGTTGCA"))
+        got = B.trioseq_align_batch(plan, [strs(t, DNA)], B.WITH_TRACEBACK)
+        score, rows = oracle.align(*t, DNA.sub, DNA.gap, traceback=True)
+        assert int(got[0]) == score
+    finally:
+        B.trioseq_plan_destroy(plan)
