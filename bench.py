@@ -163,7 +163,7 @@ class ClockSampler:
 
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    for f in ("kernels.cu", "wavefront.cuh", "engine.h"):
+    for f in ("kernels.cu", "wavefront.cuh", "engine.h", "wavefront_vl.cuh", "kernels_vl.cu"):
         with open(os.path.join(ROOT, "paper_2605_28400_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
