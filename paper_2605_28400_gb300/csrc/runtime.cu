@@ -286,6 +286,24 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
       }
     }
   }
+  // Two cells of one triplet per register (wavefront_vl.cuh), the 8x16 variant: score-only global
+  // alignment with every sigma'' >= 0, max sigma'' <= 33 (the kernel's range argument), and
+  // boundary records within the slab budget (it has no slab form). Outside the autotuner's own
+  // candidate runs, work it cannot take runs on the int32 8x8 kernel instead.
+  if (bt->var.nj == 8 && bt->var.nk == 16) {
+    bool ok_vl = !tb && plan->atype == kGlobal && plan->sig2_nonneg && plan->max_abs_sig2 <= 33;
+    if (ok_vl) {
+      double rec = 0;  // int32 boundary records of all triplets: (a+1) x tasks x (132 + 32)
+      for (size_t t = 0; t < n; t++)
+        rec += (trip[t].len[0] + 1.0) * ((trip[t].len[1] + 32) / 32) *
+               ((trip[t].len[2] + 128) / 128) * (4.0 * (128 + 4 + 32));
+      ok_vl = rec <= (double)plan->slab_budget;
+    }
+    if (!ok_vl) {
+      if (plan->tuning) return TRIOSEQ_ECUDA;  // the autotuner skips the candidate
+      bt->var = Variant{8, 8};
+    }
+  }
   const int NJ = bt->var.nj, NK = bt->var.nk;
   const int WJ = kPR * NJ, WK = kPC * NK, W = NJ * NK / 8;
   // encode + pack (16-byte aligned sequences)
@@ -383,14 +401,8 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
   //    max|sigma''| * (a+b+c + 3) < 2^14 on the grid's lengths.
   std::vector<std::pair<int32_t, int32_t>> units;  // (low-half triplet, high-half triplet or -1)
   bt->packed = 0;
-  // Two cells of one triplet per register (wavefront_vl.cuh), the 8x16 variant: score-only global
-  // alignment with every sigma'' >= 0 and max sigma'' <= 33 (the kernel's range argument).
-  const bool vl = NJ == 8 && NK == 16;
-  if (vl) {
-    if (tb || plan->atype != kGlobal || !plan->sig2_nonneg || plan->max_abs_sig2 > 33)
-      return TRIOSEQ_ECUDA;  // variant not available for this work (the autotuner skips it)
-    bt->packed = 3;
-  }
+  const bool vl = NJ == 8 && NK == 16;  // admitted above
+  if (vl) bt->packed = 3;
   const int pmode = plan->sig2_nonneg ? 2 : 1;
   if (!vl && !tb && plan->atype == kGlobal && plan->packed16 && n >= 2 &&
       wavefront_packed(NJ, NK, pmode) != nullptr) {
@@ -463,9 +475,6 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
       rows += align_up((size_t)3 * cap, 16);
     }
   }
-  // The two-per-register kernel has no slab form: a triplet whose records exceed the slab budget
-  // takes the int32 kernels (reported as unavailable, so the autotuner moves on).
-  if (vl && 4 * face > plan->slab_budget) return TRIOSEQ_ECUDA;
   // 4. Slab mode: one global-type int32 triplet whose boundary records (and, with traceback,
   //    codes) would exceed the plan's budget at once, or any such triplet when a slab height is
   //    forced. The cube then runs slab by slab, each launch seeded from the plane the slab below

@@ -120,16 +120,28 @@ def test_vl_full_size_equals_int32(which):
         B.trioseq_plan_destroy(ref)
 
 
-def test_vl_unavailable_cases():
-    """Schemes with a negative sigma'' and the semi-global / local types cannot take the
-    two-per-register kernel: forcing its tile reports the variant as unavailable (the autotuner
-    then skips it). Traceback keeps its own tile and stays exact on the same plan."""
+def test_vl_unavailable_cases_fall_back_to_int32():
+    """Schemes with a negative sigma'' and the semi-global type cannot take the two-per-register
+    kernel: a plan with its tile forced runs them on the int32 8x8 kernel, exactly. Traceback
+    keeps its own tile."""
     neg = np.full((4, 4), -10, dtype=np.int8)  # sigma'' = -10 + 4 < 0 off the diagonal
     np.fill_diagonal(neg, 2)
+    neg_sc = type("Sc", (), {"alphabet": "ACGT", "sub": neg, "gap": -2})
+    rng = np.random.default_rng(53)
+    trips = [rand_trip(rng, s, 4) for s in ((40, 70, 150), (130, 33, 64))]
+    plan = _plan(neg_sc)
+    try:
+        check(plan, neg_sc, trips)
+        bt = B.trioseq_batch_create(plan, [strs(t, neg_sc) for t in trips])
+        try:
+            assert B.trioseq_batch_info(bt)["tile"] == (8, 8)
+        finally:
+            B.trioseq_batch_destroy(bt)
+    finally:
+        B.trioseq_plan_destroy(plan)
     old = os.environ.get("TRIOSEQ_SCORE_TILE")
     os.environ["TRIOSEQ_SCORE_TILE"] = "8x16"
     try:
-        plan = B.trioseq_plan("ACGT", neg, -2)
         semi = B.trioseq_plan(DNA.alphabet, DNA.sub, DNA.gap, B.SEMIGLOBAL)
     finally:
         if old is None:
@@ -137,13 +149,11 @@ def test_vl_unavailable_cases():
         else:
             os.environ["TRIOSEQ_SCORE_TILE"] = old
     try:
-        for pl in (plan, semi):
-            with pytest.raises(B.TrioseqError) as e:
-                B.trioseq_align_batch(pl, [["ACGT", "ACG", "AGT"]])
-            assert e.value.status == B.ECUDA
+        got = B.trioseq_align_batch(semi, [strs(t, DNA) for t in trips])
+        want = [oracle.align_type(*t, DNA.sub, DNA.gap, oracle.SEMIGLOBAL) for t in trips]
+        assert got.tolist() == want
     finally:
         B.trioseq_plan_destroy(semi)
-        B.trioseq_plan_destroy(plan)
     plan = _plan(DNA)
     try:
         t = tuple(np.array([DNA.alphabet.index(ch) for ch in x], dtype=np.uint8)
