@@ -207,11 +207,18 @@ def host_cpu() -> dict:
                     pass
     except (OSError, subprocess.SubprocessError):
         pass
+    cpufreq = "/sys/devices/system/cpu/cpu0/cpufreq/"
     try:
-        with open("/sys/devices/system/cpu/cpu0/cpufreq/scaling_cur_freq") as fh:
+        with open(cpufreq + "scaling_cur_freq") as fh:
             cur_mhz = int(fh.read().strip()) / 1000.0
     except (OSError, ValueError):
         pass
+    if max_mhz is None:
+        try:
+            with open(cpufreq + "cpuinfo_max_freq") as fh:
+                max_mhz = int(fh.read().strip()) / 1000.0
+        except (OSError, ValueError):
+            pass
     try:
         with open("/proc/cpuinfo") as fh:
             for line in fh:
