@@ -169,15 +169,29 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def measured_traffic(key: str):
+def kernel_of(info: dict, n_triplets: int):
+    """(tile label, kernel name) of a batch. A packed one-triplet batch runs two column halves
+    of the triplet per register (wavefront_vl_kernel<8, half width>, tile label with a 'v');
+    a packed batch of several triplets runs two triplets per register."""
+    tj, tk = info["tile"]
+    packing = info.get("packing", 1)
+    if packing == 2 and n_triplets == 1:
+        return f"{tj}x{tk}v", f"wavefront_vl_kernel<{tj},{tk // 2}>"
+    if packing == 2:
+        return f"{tj}x{tk}", f"wavefront_kernel<{tj},{tk}> (two triplets per register)"
+    return f"{tj}x{tk}", f"wavefront_kernel<{tj},{tk}>"
+
+
+def measured_traffic(key: str, tile: str):
     """DRAM bytes per launch of the wavefront kernel from the committed ncu summary, or None
-    when the kernel source changed since the counters were taken."""
+    when the kernel source changed since the counters were taken or the batch runs another
+    tile than the one measured."""
     path = os.path.join(ROOT, "profiles", "wavefront_traffic.json")
     try:
         with open(path) as fh:
             d = json.load(fh)
         e = d.get(key)
-        if e and e.get("kernel_hash") == kernel_source_hash():
+        if e and e.get("kernel_hash") == kernel_source_hash() and e.get("tile") == tile:
             return e.get("dram_bytes_per_launch")
     except (OSError, ValueError):
         pass
@@ -459,16 +473,21 @@ def aux_measurements(B, torch, stream, flush, sms, clock_mhz, skip: str, cpu_leg
         tuned = B.trioseq_plan_autotune(plan, triplet_strings(w), mode)
         bt = B.trioseq_batch_create(plan, triplet_strings(w), mode)
         sm, km, wk, sc = time_batch(B, torch, bt, 10, 3, stream, flush, 1)
+        binfo = B.trioseq_batch_info(bt)
+        tile, kname = kernel_of(binfo, len(w.triplets))
+        packing = binfo.get("packing", 1)
         kmean = statistics.mean(km)
         ach = OPS_PER_CELL * w.cells / (kmean / 1e3) / 1e12
-        peak = sms * lanes * clock_mhz * 1e6 / 1e12
+        peak = packing * sms * lanes * clock_mhz * 1e6 / 1e12
         entry = {"workload": f"{w.name}: {desc}",
                  "gcups": w.cells / (statistics.mean(sm) / 1e3) / 1e9,
                  "ms_per_step": statistics.mean(sm), "kernel_ms": kmean, "cells": w.cells,
                  "score": int(sc[0]), "tuned": tuned,
+                 "tile": tile,
                  "roofline": {"bound": "alu", "achieved": ach, "peak": peak,
-                              "unit": "TOPS (int32)", "frac": ach / peak,
-                              "traffic": measured_traffic(key)}}
+                              "unit": "TOPS (int32)" if packing == 1 else "TOPS (int16x2 lanes)",
+                              "frac": ach / peak, "kernel": kname,
+                              "traffic": measured_traffic(key, tile)}}
         if w.traceback:
             entry["walk_ms"] = statistics.mean(wk)
             entry["roofline"]["code_stream_gbs"] = CODE_BYTES_PER_CELL * w.cells / kmean / 1e6
@@ -699,12 +718,13 @@ def main():
     achieved = OPS_PER_CELL * w.cells / (kmean / 1e3) / 1e12
     # packed int16x2 batches run two cells per instruction lane: the lane roof doubles
     packing = info.get("packing", 1)
+    tile, kname = kernel_of(info, len(strs))
     peak = packing * sms * lanes * clock_mhz * 1e6 / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": peak,
             "unit": "TOPS (int32)" if packing == 1 else "TOPS (int16x2 lanes)",
             "frac": achieved / peak,
-            "traffic": measured_traffic(f"{args.workload}"),
-            "kernel": "wavefront_kernel", "kernel_ms": kmean,
+            "traffic": measured_traffic(args.workload, tile),
+            "kernel": kname, "kernel_ms": kmean,
             "peak_basis": f"{sms} SMs x {lanes:.1f} int32 ops/clk (the lower of the nominal "
                           f"{INT32_LANES_PER_SM} and the measured rate) x median SM clock "
                           f"{clock_mhz:.0f} MHz sampled in the timed region"
@@ -721,7 +741,8 @@ def main():
             "data": "synthetic",
             "config": {"workload": f"{w.name}: {desc}", "cells_per_step": w.cells,
                        "triplets": len(strs), "mode": "score+traceback" if tb else "score",
-                       "column_tasks": info["tasks"], "tile": f"{info['tile'][0]}x{info['tile'][1]}",
+                       "column_tasks": info["tasks"],
+                       "tile": tile,
                        "progress_interval": tuned["ti"], "autotuned": True,
                        "l2": "256 MiB flush between timed steps (outside the events)",
                        "parallelism": "replicas" if world > 1 else "single GPU"},

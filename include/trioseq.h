@@ -174,9 +174,11 @@ trioseq_status trioseq_batch_span(trioseq_batch_t batch, size_t idx, int32_t beg
 trioseq_status trioseq_batch_info(trioseq_batch_t batch, size_t* n, uint64_t* cells,
                                   uint64_t* tasks, int32_t* tile_j, int32_t* tile_k);
 
-/* trioseq_batch_packing — *per_word = how many triplets share each register of the batch's
- * kernel: 2 in the packed int16x2 mode, else 1. The packed mode is the integer counterpart of
- * the paper's FP16x2 arithmetic (Sec. IV-B). A score-only global batch of two or more triplets
+/* trioseq_batch_packing — *per_word = how many DP cells share each register of the batch's
+ * kernel: 2 in the packed int16x2 modes, else 1. Two packed modes are the integer counterpart
+ * of the paper's FP16x2 arithmetic (Sec. IV-B): two triplets per register, or two column halves
+ * of one triplet per register (a one-triplet batch whose score tile is 8x16 or "8x8v", see
+ * trioseq_plan_autotune). A score-only global batch of two or more triplets
  * is packed when every pair fits: the batch pairs triplets of the same column-task grid class,
  * and each pair's grid needs max|sigma''| * (a+b+c+3) < 2^14 on its maximal lengths. Otherwise,
  * or with TRIOSEQ_PACKED=0 set before trioseq_plan, every triplet gets its own int32 tasks.
@@ -208,7 +210,9 @@ trioseq_status trioseq_batch_timing(trioseq_batch_t batch, float ms[2]);
 /* trioseq_plan_autotune — pick the kernel variant for a class of work by measuring it.
  * Runs the sample batch (host strings, n >= 1, mode as for trioseq_align_batch) once per
  * candidate — every instantiated register tile per lane (8x8, 4x8, 4x4 cells, i.e. column blocks
- * of 32x64, 16x64 and 16x32 cells per warp, and in traceback mode also 8x4, 32x32 cells) times
+ * of 32x64, 16x64 and 16x32 cells per warp, and in traceback mode also 8x4, 32x32 cells; in
+ * score-only global mode with every sigma'' in [0, 33] also the two-cells-per-register tiles
+ * 8x16 and 8x8v, 32x128 and 32x64 cells per warp) times
  * progress intervals of 4, 8, 16 and 32 steps —
  * times two passes of each with CUDA events on the legacy default stream, and remembers the
  * fastest in the plan for batches of the same mode, the same single-or-batch kind, and the same

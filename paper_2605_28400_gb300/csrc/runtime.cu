@@ -136,8 +136,11 @@ struct Workspace {
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Register tile per lane: nj x nk cells; vl = 1 for the two-cells-per-register kernel
+// (wavefront_vl.cuh), whose lane tile is two nj x nk/2 column halves.
 struct Variant {
   int nj, nk;
+  int vl = 0;
 };
 
 }  // namespace
@@ -286,17 +289,19 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
       }
     }
   }
-  // Two cells of one triplet per register (wavefront_vl.cuh), the 8x16 variant: score-only global
-  // alignment with every sigma'' >= 0, max sigma'' <= 33 (the kernel's range argument), and
-  // boundary records within the slab budget (it has no slab form). Outside the autotuner's own
-  // candidate runs, work it cannot take runs on the int32 8x8 kernel instead.
-  if (bt->var.nj == 8 && bt->var.nk == 16) {
-    bool ok_vl = !tb && plan->atype == kGlobal && plan->sig2_nonneg && plan->max_abs_sig2 <= 33;
+  // Two cells of one triplet per register (wavefront_vl.cuh), variants 8x16 and 8x8v: score-only
+  // global alignment with every sigma'' >= 0, max sigma'' <= 33 (the kernel's range argument),
+  // and boundary records within the slab budget (it has no slab form). Outside the autotuner's
+  // own candidate runs, work it cannot take runs on the int32 8x8 kernel instead.
+  if (bt->var.vl) {
+    bool ok_vl = !tb && plan->atype == kGlobal && plan->sig2_nonneg && plan->max_abs_sig2 <= 33 &&
+                 wavefront_vl(bt->var.nj, bt->var.nk) != nullptr;
     if (ok_vl) {
-      double rec = 0;  // int32 boundary records of all triplets: (a+1) x tasks x (132 + 32)
+      const int wj = kPR * bt->var.nj, wk = kPC * bt->var.nk;
+      double rec = 0;  // int32 boundary records of all triplets: (a+1) x tasks x (WK+4 + WJ)
       for (size_t t = 0; t < n; t++)
-        rec += (trip[t].len[0] + 1.0) * ((trip[t].len[1] + 32) / 32) *
-               ((trip[t].len[2] + 128) / 128) * (4.0 * (128 + 4 + 32));
+        rec += (trip[t].len[0] + 1.0) * ((trip[t].len[1] + wj) / wj) *
+               ((trip[t].len[2] + wk) / wk) * (4.0 * (wk + 4 + wj));
       ok_vl = rec <= (double)plan->slab_budget;
     }
     if (!ok_vl) {
@@ -401,7 +406,7 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
   //    max|sigma''| * (a+b+c + 3) < 2^14 on the grid's lengths.
   std::vector<std::pair<int32_t, int32_t>> units;  // (low-half triplet, high-half triplet or -1)
   bt->packed = 0;
-  const bool vl = NJ == 8 && NK == 16;  // admitted above
+  const bool vl = bt->var.vl != 0;  // admitted above
   if (vl) bt->packed = 3;
   const int pmode = plan->sig2_nonneg ? 2 : 1;
   if (!vl && !tb && plan->atype == kGlobal && plan->packed16 && n >= 2 &&
@@ -991,8 +996,11 @@ trioseq_status trioseq_plan(const trioseq_scoring* sc, uint32_t max_len_hint, ui
     char* end = nullptr;
     const long rj = std::strtol(v, &end, 10);
     if (!end || *end != 'x') return;
-    const long ck = std::strtol(end + 1, nullptr, 10);
-    if (rj > 0 && rj <= 16 && ck > 0 && ck <= 32) *out = Variant{(int)rj, (int)ck};
+    char* end2 = nullptr;
+    const long ck = std::strtol(end + 1, &end2, 10);
+    // "8x16" and a trailing 'v' ("8x8v") select the two-cells-per-register kernel
+    const int two = (ck == 16 || (end2 && *end2 == 'v')) ? 1 : 0;
+    if (rj > 0 && rj <= 16 && ck > 0 && ck <= 32) *out = Variant{(int)rj, (int)ck, two};
   };
   parse_tile(std::getenv("TRIOSEQ_SCORE_TILE"), &plan->score_variant);
   parse_tile(std::getenv("TRIOSEQ_TB_TILE"), &plan->tb_variant);
@@ -1143,7 +1151,8 @@ trioseq_status trioseq_plan_autotune(trioseq_plan_t plan, const trioseq_triplet*
   if (!plan || !sample || n == 0 || mode > TRIOSEQ_WITH_TRACEBACK) return TRIOSEQ_EINVAL;
   DeviceGuard g(plan->device);
   // candidate tiles per mode; 8x4 exists for traceback keys only
-  static const Variant kScoreTiles[] = {{8, 8}, {4, 8}, {4, 4}, {8, 16}};  // 8x16: two per register
+  // 8x16 and 8x8 with vl: two cells of one triplet per register
+  static const Variant kScoreTiles[] = {{8, 8}, {4, 8}, {4, 4}, {8, 16, 1}, {8, 8, 1}};
   static const Variant kTbTiles[] = {{8, 8}, {4, 8}, {4, 4}, {8, 4}};
   static const int kTI[] = {4, 8, 16, 32};
   const bool tb_mode = mode == TRIOSEQ_WITH_TRACEBACK;

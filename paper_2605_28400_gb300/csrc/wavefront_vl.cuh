@@ -15,12 +15,13 @@
 //  * Range. With every sigma'' >= 0, M' is non-decreasing along each axis and adjacent cells differ
 //    by at most 2*max sigma'' (follow the optimal path to the farther cell back to where it enters
 //    the farther plane and copy its in-plane moves one plane lower: in-plane costs do not depend
-//    on the third coordinate). A warp's working set (19 slices of a 32 x 128 block plus halos, L1
-//    diameter <= 178) therefore spans at most 356*max sigma''. Each warp keeps one base B for
-//    its task, warp-uniform, so shuffled halos need no conversion; B is moved by the drift of
-//    lane 0's first cell whenever that exceeds 2048 (all halves rebased with a signed 16x2
-//    add-max against 0, which keeps -infinity at 0). The host admits the mode only for
-//    max sigma'' <= 33, so every half stays within [1, 2^16) with margin and no add wraps.
+//    on the third coordinate). A warp's working set (19 slices of a 32 x 16NH block plus halos,
+//    L1 diameter <= 178 for NH = 8, 114 for NH = 4) therefore spans at most 356*max sigma''.
+//    Each warp keeps one base B for its task, warp-uniform, so shuffled halos need no
+//    conversion; B is moved by the drift of lane 0's first cell whenever that exceeds 2048 (all
+//    halves rebased with a signed 16x2 add-max against 0, which keeps -infinity at 0). The host
+//    admits the mode only for max sigma'' <= 33, so every half stays within [1, 2^16) with margin
+//    and no add wraps.
 //  * Records stay absolute int32 (converted on store and on staging), so tasks are decoupled and
 //    the record layout is the plain kernel's with WK = 8 lanes x 2NH columns.
 //  * Edges of a task's sweep: the high half of a lane is inactive while the low half computes
@@ -49,7 +50,8 @@ struct VlGeom {
 };
 
 template <int NJ, int NH>
-__global__ void __launch_bounds__(kWarpsPerCta * 32, 2) wavefront_vl_kernel(const WaveParams p) {
+__global__ void __launch_bounds__(kWarpsPerCta * 32, (NH >= 8 ? 2 : 3))
+    wavefront_vl_kernel(const WaveParams p) {
   using G = VlGeom<NJ, NH>;
   static_assert(NJ % 4 == 0 && NH % 4 == 0, "tile sides must be multiples of 4");
   constexpr int NK = G::NK, WJ = G::WJ, WK = G::WK;

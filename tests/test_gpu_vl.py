@@ -22,6 +22,8 @@ pytestmark = pytest.mark.gpu
 
 DNA = synth.dna_scoring()
 PROT = synth.protein_scoring(1003)
+# the two instantiations: 8 x (8+8) cells per lane (32 x 128 tasks) and 8 x (4+4) (32 x 64 tasks)
+VL_TILES = ["8x16", "8x8v"]
 
 
 def _plan(sc, tile="8x16"):
@@ -50,37 +52,41 @@ def check(plan, sc, trips):
     assert got.tolist() == want.tolist()
 
 
-def test_vl_is_selected_for_nonnegative_schemes():
-    plan = _plan(DNA)
+@pytest.mark.parametrize("tile", VL_TILES)
+def test_vl_is_selected_for_nonnegative_schemes(tile):
+    plan = _plan(DNA, tile)
     try:
         bt = B.trioseq_batch_create(plan, [["ACGT" * 20, "ACG" * 20, "AGT" * 20]])
         try:
             info = B.trioseq_batch_info(bt)
-            assert info["tile"] == (8, 16) and info["packing"] == 2
+            assert info["tile"] == ((8, 16) if tile == "8x16" else (8, 8))
+            assert info["packing"] == 2
         finally:
             B.trioseq_batch_destroy(bt)
     finally:
         B.trioseq_plan_destroy(plan)
 
 
-def test_vl_all_tiny_shapes_one_batch():
+@pytest.mark.parametrize("tile", VL_TILES)
+def test_vl_all_tiny_shapes_one_batch(tile):
     rng = np.random.default_rng(51)
     trips = [rand_trip(rng, s, 4) for s in itertools.product(range(6), repeat=3)]
-    plan = _plan(DNA)
+    plan = _plan(DNA, tile)
     try:
         check(plan, DNA, trips)
     finally:
         B.trioseq_plan_destroy(plan)
 
 
+@pytest.mark.parametrize("tile", VL_TILES)
 @pytest.mark.parametrize("sc", [DNA, PROT], ids=["dna", "protein"])
-def test_vl_ragged_multi_block(sc):
+def test_vl_ragged_multi_block(sc, tile):
     rng = np.random.default_rng(52)
     shapes = [(37, 70, 130), (129, 33, 65), (0, 100, 100), (100, 0, 77), (64, 64, 0),
               (200, 1, 250), (5, 260, 3), (31, 32, 63), (33, 65, 129), (17, 127, 128),
               (40, 135, 257), (1, 1, 1), (0, 0, 0)]
     trips = [rand_trip(rng, s, len(sc.alphabet)) for s in shapes]
-    plan = _plan(sc)
+    plan = _plan(sc, tile)
     try:
         check(plan, sc, trips)
         for t in trips[:4]:  # alone as well as in the batch
@@ -89,28 +95,30 @@ def test_vl_ragged_multi_block(sc):
         B.trioseq_plan_destroy(plan)
 
 
-def test_vl_related_batch_and_rebasing():
+@pytest.mark.parametrize("tile", VL_TILES)
+def test_vl_related_batch_and_rebasing(tile):
     w = synth.config2(seed=98, n=24, lo=40, hi=300)
     big = synth.config1(seed=99, L=600).triplets  # values grow past many rebase thresholds
     prot = synth.config3(seed=97, L=420)
-    plan = _plan(DNA)
+    plan = _plan(DNA, tile)
     try:
         check(plan, DNA, w.triplets + big)
     finally:
         B.trioseq_plan_destroy(plan)
-    plan = _plan(prot.scoring)
+    plan = _plan(prot.scoring, tile)
     try:
         check(plan, prot.scoring, prot.triplets)
     finally:
         B.trioseq_plan_destroy(plan)
 
 
+@pytest.mark.parametrize("tile", VL_TILES)
 @pytest.mark.parametrize("which", ["config1", "config3"])
-def test_vl_full_size_equals_int32(which):
+def test_vl_full_size_equals_int32(which, tile):
     w = synth.config1() if which == "config1" else synth.config3()
     s = [strs(t, w.scoring) for t in w.triplets]
     ref = _plan(w.scoring, "8x8")
-    vl = _plan(w.scoring)
+    vl = _plan(w.scoring, tile)
     try:
         want = B.trioseq_align_batch(ref, s)
         got = B.trioseq_align_batch(vl, s)

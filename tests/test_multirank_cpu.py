@@ -89,3 +89,26 @@ def test_roofline_lanes_take_the_lower_of_nominal_and_measured():
     assert bench.roof_lanes(None) == bench.INT32_LANES_PER_SM
     assert bench.roof_lanes({"int32_ops_per_clk_per_sm": 127.2}) == 127.2
     assert bench.roof_lanes({"int32_ops_per_clk_per_sm": 140.0}) == bench.INT32_LANES_PER_SM
+
+
+def test_kernel_label_and_tile_checked_traffic(tmp_path, monkeypatch):
+    import json
+
+    import bench
+    assert bench.kernel_of({"tile": (8, 16), "packing": 2}, 1) == \
+        ("8x16v", "wavefront_vl_kernel<8,8>")
+    assert bench.kernel_of({"tile": (8, 8), "packing": 2}, 1)[0] == "8x8v"
+    assert bench.kernel_of({"tile": (8, 8), "packing": 2}, 5)[0] == "8x8"
+    assert bench.kernel_of({"tile": (8, 4), "packing": 1}, 1) == ("8x4", "wavefront_kernel<8,4>")
+    # traffic is reported only for the measured tile and the current kernel source
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "wavefront_traffic.json").write_text(json.dumps({"w": {
+        "kernel_hash": "h0", "tile": "8x8v", "dram_bytes_per_launch": 123}}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "h0")
+    assert bench.measured_traffic("w", "8x8v") == 123
+    assert bench.measured_traffic("w", "8x16v") is None
+    assert bench.measured_traffic("other", "8x8v") is None
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "h1")  # source changed since
+    assert bench.measured_traffic("w", "8x8v") is None
