@@ -161,9 +161,14 @@ class ClockSampler:
                 "samples": len(inside), "note": note}
 
 
-def kernel_source_hash() -> str:
+def kernel_source_hash(tile: str) -> str:
+    """Hash of the sources a tile's wavefront kernel is compiled from: the two-cells-per-register
+    kernel (tile label ending in 'v') or the int32 / two-triplets kernel family."""
+    common = ("wavefront.cuh", "engine.h")
+    own = (("wavefront_vl.cuh", "kernels_vl.cu") if tile.endswith("v")
+           else ("kernels.cu", "kernels_packed.cu", "kernels_slab.cu", "kernels_variants.cu"))
     h = hashlib.sha256()
-    for f in ("kernels.cu", "wavefront.cuh", "engine.h", "wavefront_vl.cuh", "kernels_vl.cu"):
+    for f in common + own:
         with open(os.path.join(ROOT, "paper_2605_28400_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -191,7 +196,7 @@ def measured_traffic(key: str, tile: str):
         with open(path) as fh:
             d = json.load(fh)
         e = d.get(key)
-        if e and e.get("kernel_hash") == kernel_source_hash() and e.get("tile") == tile:
+        if e and e.get("kernel_hash") == kernel_source_hash(tile) and e.get("tile") == tile:
             return e.get("dram_bytes_per_launch")
     except (OSError, ValueError):
         pass

@@ -106,9 +106,9 @@ def test_kernel_label_and_tile_checked_traffic(tmp_path, monkeypatch):
     (prof / "wavefront_traffic.json").write_text(json.dumps({"w": {
         "kernel_hash": "h0", "tile": "8x8v", "dram_bytes_per_launch": 123}}))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "h0")
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda tile: "h0")
     assert bench.measured_traffic("w", "8x8v") == 123
     assert bench.measured_traffic("w", "8x16v") is None
     assert bench.measured_traffic("other", "8x8v") is None
-    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "h1")  # source changed since
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda tile: "h1")  # source changed since
     assert bench.measured_traffic("w", "8x8v") is None
