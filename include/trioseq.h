@@ -170,7 +170,9 @@ trioseq_status trioseq_batch_span(trioseq_batch_t batch, size_t idx, int32_t beg
 
 /* Work statistics of a batch: number of triplets, the paper's cell count
  * (sum of |S0|*|S1|*|S2|, the TCUPS numerator), the number of column tasks in the queue, and the
- * kernel variant chosen (tile rows x tile cols per lane). Any out pointer may be null. */
+ * kernel variant chosen (tile rows x tile cols per lane; the two-cells-per-register tiles count
+ * both halves, so 8x8v reads 8 x 8, told apart from the int32 8x8 by trioseq_batch_packing).
+ * Any out pointer may be null. */
 trioseq_status trioseq_batch_info(trioseq_batch_t batch, size_t* n, uint64_t* cells,
                                   uint64_t* tasks, int32_t* tile_j, int32_t* tile_k);
 
