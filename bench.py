@@ -22,8 +22,12 @@ roofline: the wavefront kernel's int32 work (13 algorithmic ops per cell: 7 adds
         sampled during the timed region.
 cpu_baseline / --impl reference: the C++ oracle (single core) on a bounded prefix sample.
 
-Under torchrun (N > 1) every rank aligns its own replica of the workload (triplets are
-independent; no collective on the data path) and the slowest rank's time is reported.
+Under torchrun (N > 1) the slowest rank's time is reported and `value` is the whole job's cells
+over it (weak scaling; no collective on the data path). A batch workload (batch4096) becomes
+N x 4096 triplets of the same recipe, sharded over the ranks by the dynamic partition of
+Sec. V-D (trioseq_partition: least cumulative cells first), each rank computing the same
+partition from the lengths. A single-triplet workload runs one replica per rank. The aux lines
+and the CPU baseline are taken at N = 1 only.
 """
 from __future__ import annotations
 
@@ -172,6 +176,29 @@ def kernel_source_hash(tile: str) -> str:
         with open(os.path.join(ROOT, "paper_2605_28400_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def global_workload(key: str, world: int):
+    """The whole job's batch when a multi-triplet workload runs on `world` ranks: `world` times
+    the single-GPU batch (same recipe and seed), so each rank's share stays about the same size
+    (weak scaling). None for single-triplet workloads, which run as replicas."""
+    from paper_2605_28400_gb300 import synth
+    if key == "batch4096":
+        return synth.config2(n=4096 * world)
+    return None
+
+
+def shard_workload(w, world: int, rank: int, B):
+    """This rank's share of a batch under the dynamic partition of Sec. V-D (each triplet to the
+    rank with the least cumulative cells so far). Every rank computes the same partition from
+    the same lengths, so there is no collective. Returns (share, cells of every rank)."""
+    from paper_2605_28400_gb300 import synth
+    lens = [[len(s) for s in t] for t in w.triplets]
+    rank_of, cells = B.trioseq_partition(lens, world, B.PART_DYNAMIC)
+    mine = [t for t, r in zip(w.triplets, rank_of) if r == rank]
+    share = synth.Workload(f"{w.name}, rank {rank} of {world}", w.scoring, mine, w.traceback,
+                           dict(w.meta))
+    return share, [int(c) for c in cells]
 
 
 def kernel_of(info: dict, n_triplets: int):
@@ -664,7 +691,16 @@ def main():
     from paper_2605_28400_gb300 import binding as B
     B.load()
     make, desc = workloads()[args.workload]
-    w = make()
+    wg = global_workload(args.workload, world) if world > 1 else None
+    if wg is not None:  # a batch: shard its triplets over the ranks (Sec. V-D)
+        w, rank_cells = shard_workload(wg, world, rank, B)
+        cells_total = wg.cells
+        parallelism = f"dp{world}: triplets sharded by the dynamic partition (Sec. V-D)"
+    else:  # one triplet, or one GPU: every rank aligns its own replica
+        w = make()
+        rank_cells = [w.cells] * world
+        cells_total = world * w.cells
+        parallelism = f"dp{world}: replicas" if world > 1 else "single GPU"
     tb = w.traceback
     mode = B.WITH_TRACEBACK if tb else B.SCORE_ONLY
     strs = triplet_strings(w)
@@ -696,7 +732,7 @@ def main():
 
     total_ms = max_over_ranks(sum(step_ms), dist, "cuda")
     ms_step = total_ms / args.steps
-    value = world * w.cells / (ms_step / 1e3) / 1e9
+    value = cells_total / (ms_step / 1e3) / 1e9
 
     # e2e through the public C call on host strings
     e2e_ms = []
@@ -711,7 +747,7 @@ def main():
     h2d, d2h = B.trioseq_plan_io_bytes(plan)
     assert s2.tolist() == scores.tolist(), "e2e and device-resident scores differ"
     e2e_total = max_over_ranks(sum(e2e_ms), dist, "cuda")
-    e2e_val = world * w.cells / (e2e_total / len(e2e_ms) / 1e3) / 1e9
+    e2e_val = cells_total / (e2e_total / len(e2e_ms) / 1e3) / 1e9
 
     clock_mhz = clocks.get("sm_mhz") or 2070.0
     try:
@@ -744,13 +780,15 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
-            "config": {"workload": f"{w.name}: {desc}", "cells_per_step": w.cells,
-                       "triplets": len(strs), "mode": "score+traceback" if tb else "score",
+            "config": {"workload": f"{(wg or w).name}: {desc}", "cells_per_step": cells_total,
+                       "cells_per_rank": rank_cells,
+                       "triplets": len(wg.triplets) if wg else world * len(strs),
+                       "mode": "score+traceback" if tb else "score",
                        "column_tasks": info["tasks"],
                        "tile": tile,
                        "progress_interval": tuned["ti"], "autotuned": True,
                        "l2": "256 MiB flush between timed steps (outside the events)",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+                       "parallelism": parallelism},
             "roofline": roof,
             "e2e": {"value": e2e_val, "unit": "GCUPS", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h), "ms_per_step": statistics.mean(e2e_ms)},
@@ -760,10 +798,11 @@ def main():
     B.trioseq_batch_destroy(bt)
     B.trioseq_plan_destroy(plan)
 
-    if rank == 0 and not args.no_aux:
+    # aux lines and the CPU baseline: one GPU only (at N > 1 the other GPUs would idle meanwhile)
+    if rank == 0 and world == 1 and not args.no_aux:
         line["aux"] = aux_measurements(B, torch, stream, flush, sms, clock_mhz, args.workload,
                                        not args.no_cpu, lanes)
-    if rank == 0 and not args.no_cpu:
+    if rank == 0 and world == 1 and not args.no_cpu:
         cb, _ = cpu_oracle_sample(w, 2.5e8, tb)
         line["cpu_baseline"] = cb
     sampler.stop()

@@ -258,6 +258,30 @@ trioseq_status trioseq_poll(trioseq_server_t srv, uint64_t ticket, int32_t* scor
 /* Stop the server thread after finishing admitted work and release it. */
 trioseq_status trioseq_server_destroy(trioseq_server_t srv);
 
+/* ---- multi-GPU work partitioning (host only) ---- */
+
+enum { TRIOSEQ_PART_BLOCKED = 0, TRIOSEQ_PART_INTERLEAVED = 1, TRIOSEQ_PART_DYNAMIC = 2 };
+
+/* trioseq_partition — assign each triplet of a set to one of nranks ranks (one rank per GPU, each
+ * aligning its share with its own plan), by the three schemes of Sec. V-D:
+ *   TRIOSEQ_PART_BLOCKED     : contiguous chunks in dataset order; rank r gets triplets
+ *                              floor(r*n/nranks) .. floor((r+1)*n/nranks) - 1 (the paper gives
+ *                              no chunk rule; sizes differ by at most one);
+ *   TRIOSEQ_PART_INTERLEAVED : round robin, triplet t to rank t mod nranks;
+ *   TRIOSEQ_PART_DYNAMIC     : in dataset order, each triplet to the rank with the least
+ *                              cumulative cell count so far (ties: lowest rank).
+ * A triplet's work is the paper's cell count |S0|*|S1|*|S2|.
+ *   lens           : host array of 3n lengths, triplet t at lens[3t .. 3t+2] (caller-owned).
+ *   rank_of        : out, host array of n ranks in [0, nranks) (caller-owned).
+ *   cells_per_rank : out, host array of nranks cumulative cell counts; may be null.
+ * Pure host computation: needs no GPU and no plan, allocates O(nranks) host memory, writes no
+ * output on error. There is no collective: every rank computes the same partition from the
+ * same lengths and keeps its own triplets.
+ * Errors: EINVAL (nranks < 1, unknown scheme, null lens or rank_of with n > 0), EOVERFLOW (the
+ * set's total cell count exceeds 2^64 - 1). */
+trioseq_status trioseq_partition(const uint32_t* lens, size_t n, int32_t nranks, int32_t scheme,
+                                 int32_t* rank_of, uint64_t* cells_per_rank);
+
 /* ---- measurement ---- */
 
 /* trioseq_alu_rate — measured rate of one int32 instruction form on the current GPU. It backs the

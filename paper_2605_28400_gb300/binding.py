@@ -16,6 +16,7 @@ from . import build as _build
 OK, EINVAL, ENOMEM, EAGAIN, EOVERFLOW, ETIMEOUT, ECUDA, ENOTIMPL, ESCRATCH = range(9)
 SCORE_ONLY, WITH_TRACEBACK = 0, 1
 GLOBAL, SEMIGLOBAL, LOCAL = 0, 1, 2  # alignment types of Sec. II (trioseq_plan flags)
+PART_BLOCKED, PART_INTERLEAVED, PART_DYNAMIC = 0, 1, 2  # trioseq_partition schemes (Sec. V-D)
 
 
 class TrioseqError(RuntimeError):
@@ -88,6 +89,8 @@ def load(build_if_missing: bool = True):
         "trioseq_batch_span": ([vp, sz, i32p, i32p], i32),
         "trioseq_alu_rate": ([i32, ctypes.POINTER(ctypes.c_double),
                               ctypes.POINTER(ctypes.c_double)], i32),
+        "trioseq_partition": ([ctypes.POINTER(ctypes.c_uint32), sz, i32, i32, i32p,
+                               ctypes.POINTER(ctypes.c_uint64)], i32),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -105,7 +108,24 @@ def exported_symbols() -> list[str]:
             "trioseq_plan_io_bytes", "trioseq_server_create", "trioseq_submit", "trioseq_poll",
             "trioseq_server_destroy", "trioseq_strerror", "trioseq_align_noalloc",
             "trioseq_plan_autotune", "trioseq_batch_packing", "trioseq_batch_slabs",
-            "trioseq_traceback_span", "trioseq_batch_span", "trioseq_alu_rate"]
+            "trioseq_traceback_span", "trioseq_batch_span", "trioseq_alu_rate",
+            "trioseq_partition"]
+
+
+def trioseq_partition(lens, nranks: int, scheme: int = None):
+    """Ranks of a triplet set under a Sec. V-D scheme (default dynamic), from an (n, 3) array of
+    lengths. Returns (rank_of as an int32 array of n, cells per rank as a uint64 array)."""
+    scheme = PART_DYNAMIC if scheme is None else scheme
+    lens = np.ascontiguousarray(np.asarray(lens, dtype=np.uint32).reshape(-1, 3))
+    n = lens.shape[0]
+    rank_of = np.zeros(n, dtype=np.int32)
+    load_ = np.zeros(max(int(nranks), 0), dtype=np.uint64)
+    _check(load().trioseq_partition(
+        lens.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), n, int(nranks), int(scheme),
+        rank_of.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+        load_.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)) if load_.size else None),
+        "trioseq_partition")
+    return rank_of, load_
 
 
 def trioseq_plan_autotune(plan, sample, mode: int = SCORE_ONLY) -> dict:

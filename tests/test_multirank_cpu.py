@@ -1,7 +1,8 @@
 """Multi-rank logic of the benchmark, on CPU with gloo (world size 2).
 
-The path shards over independent triplets, so N ranks run N replicas with no collective on the
-data path; the only cross-rank step is taking the slowest rank's time. The reference arm runs on
+The path shards over independent triplets with no collective on the data path: a batch is split
+over the ranks by the dynamic partition of Sec. V-D, a single triplet runs as one replica per
+rank, and the only cross-rank step is taking the slowest rank's time. The reference arm runs on
 rank 0 only and the other ranks exit cleanly without output.
 """
 import os
@@ -112,3 +113,57 @@ def test_kernel_label_and_tile_checked_traffic(tmp_path, monkeypatch):
     assert bench.measured_traffic("other", "8x8v") is None
     monkeypatch.setattr(bench, "kernel_source_hash", lambda tile: "h1")  # source changed since
     assert bench.measured_traffic("w", "8x8v") is None
+
+
+def _shard_worker(rank, world, port, out_q):
+    import torch.distributed as dist
+
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    from paper_2605_28400_gb300 import binding as B
+    from paper_2605_28400_gb300 import synth
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        w = synth.config2(seed=77, n=24, lo=4, hi=30)
+        share, cells = bench.shard_workload(w, world, rank, B)
+        scores = oracle.align_many(share.triplets, w.scoring.sub, w.scoring.gap).tolist()
+        mine = [[int(len(s)) for s in t] + [sc] for t, sc in zip(share.triplets, scores)]
+        gathered = [None] * world  # the test's own check; the bench has no collective
+        dist.all_gather_object(gathered, (mine, share.cells, cells))
+        out_q.put((rank, gathered))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_sharded_batch_gloo_world2():
+    """Two CPU ranks shard a batch by the dynamic partition (bench.shard_workload), each aligns
+    its share with the oracle: every triplet is aligned exactly once, the union of the shares'
+    results equals the whole batch aligned in one process, and every rank agrees on the loads."""
+    pytest.importorskip("torch")
+    import torch.multiprocessing as mp
+
+    import oracle
+    from paper_2605_28400_gb300 import synth
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_shard_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=180)
+        assert p.exitcode == 0
+    got = dict(q.get(timeout=10) for _ in range(2))
+    assert got[0] == got[1]
+    shares = got[0]
+    w = synth.config2(seed=77, n=24, lo=4, hi=30)
+    whole = oracle.align_many(w.triplets, w.scoring.sub, w.scoring.gap).tolist()
+    want = sorted([int(len(s)) for s in t] + [sc] for t, sc in zip(w.triplets, whole))
+    assert sorted(row for mine, _, _ in shares for row in mine) == want
+    assert [c for _, c, _ in shares] == shares[0][2]  # each share's cells = its rank's load
+    assert sum(shares[0][2]) == w.cells
+    assert all(len(mine) > 0 for mine, _, _ in shares)
