@@ -803,7 +803,7 @@ def main():
         line["aux"] = aux_measurements(B, torch, stream, flush, sms, clock_mhz, args.workload,
                                        not args.no_cpu, lanes)
     if rank == 0 and world == 1 and not args.no_cpu:
-        cb, _ = cpu_oracle_sample(w, 2.5e8, tb)
+        cb, _ = cpu_oracle_sample(w, 1e9, tb)  # ~15 s of one host core
         line["cpu_baseline"] = cb
     sampler.stop()
     if rank == 0:
