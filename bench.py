@@ -25,8 +25,8 @@ cpu_baseline / --impl reference: the C++ oracle (single core) on a bounded prefi
 Under torchrun (N > 1) the slowest rank's time is reported and `value` is the whole job's cells
 over it (weak scaling; no collective on the data path). A batch workload (batch4096) becomes
 N x 4096 triplets of the same recipe, sharded over the ranks by the dynamic partition of
-Sec. V-D (trioseq_partition: least cumulative cells first), each rank computing the same
-partition from the lengths. A single-triplet workload runs one replica per rank. The aux lines
+Sec. V-D taken largest triplet first (trioseq_partition: least cumulative cells first), each
+rank computing the same partition from the lengths. A single-triplet workload runs one replica per rank. The aux lines
 and the CPU baseline are taken at N = 1 only.
 """
 from __future__ import annotations
@@ -190,11 +190,12 @@ def global_workload(key: str, world: int):
 
 def shard_workload(w, world: int, rank: int, B):
     """This rank's share of a batch under the dynamic partition of Sec. V-D (each triplet to the
-    rank with the least cumulative cells so far). Every rank computes the same partition from
-    the same lengths, so there is no collective. Returns (share, cells of every rank)."""
+    rank with the least cumulative cells so far), taken largest triplet first. Every rank
+    computes the same partition from the same lengths, so there is no collective. Returns
+    (share, cells of every rank)."""
     from paper_2605_28400_gb300 import synth
     lens = [[len(s) for s in t] for t in w.triplets]
-    rank_of, cells = B.trioseq_partition(lens, world, B.PART_DYNAMIC)
+    rank_of, cells = B.trioseq_partition(lens, world, B.PART_LARGEST_FIRST)
     mine = [t for t, r in zip(w.triplets, rank_of) if r == rank]
     share = synth.Workload(f"{w.name}, rank {rank} of {world}", w.scoring, mine, w.traceback,
                            dict(w.meta))
@@ -695,7 +696,8 @@ def main():
     if wg is not None:  # a batch: shard its triplets over the ranks (Sec. V-D)
         w, rank_cells = shard_workload(wg, world, rank, B)
         cells_total = wg.cells
-        parallelism = f"dp{world}: triplets sharded by the dynamic partition (Sec. V-D)"
+        parallelism = (f"dp{world}: triplets sharded by the dynamic partition (Sec. V-D), "
+                       "largest first")
     else:  # one triplet, or one GPU: every rank aligns its own replica
         w = make()
         rank_cells = [w.cells] * world

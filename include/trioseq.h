@@ -260,7 +260,8 @@ trioseq_status trioseq_server_destroy(trioseq_server_t srv);
 
 /* ---- multi-GPU work partitioning (host only) ---- */
 
-enum { TRIOSEQ_PART_BLOCKED = 0, TRIOSEQ_PART_INTERLEAVED = 1, TRIOSEQ_PART_DYNAMIC = 2 };
+enum { TRIOSEQ_PART_BLOCKED = 0, TRIOSEQ_PART_INTERLEAVED = 1, TRIOSEQ_PART_DYNAMIC = 2,
+       TRIOSEQ_PART_LARGEST_FIRST = 3 };
 
 /* trioseq_partition — assign each triplet of a set to one of nranks ranks (one rank per GPU, each
  * aligning its share with its own plan), by the three schemes of Sec. V-D:
@@ -270,6 +271,10 @@ enum { TRIOSEQ_PART_BLOCKED = 0, TRIOSEQ_PART_INTERLEAVED = 1, TRIOSEQ_PART_DYNA
  *   TRIOSEQ_PART_INTERLEAVED : round robin, triplet t to rank t mod nranks;
  *   TRIOSEQ_PART_DYNAMIC     : in dataset order, each triplet to the rank with the least
  *                              cumulative cell count so far (ties: lowest rank).
+ *   TRIOSEQ_PART_LARGEST_FIRST : the dynamic rule applied to the triplets in order of
+ *                              decreasing cell count, ties in dataset order (LPT list
+ *                              scheduling; not in the paper). Its largest load is at most
+ *                              4/3 - 1/(3 nranks) times the optimum.
  * A triplet's work is the paper's cell count |S0|*|S1|*|S2|.
  *   lens           : host array of 3n lengths, triplet t at lens[3t .. 3t+2] (caller-owned).
  *   rank_of        : out, host array of n ranks in [0, nranks) (caller-owned).

@@ -16,7 +16,8 @@ from . import build as _build
 OK, EINVAL, ENOMEM, EAGAIN, EOVERFLOW, ETIMEOUT, ECUDA, ENOTIMPL, ESCRATCH = range(9)
 SCORE_ONLY, WITH_TRACEBACK = 0, 1
 GLOBAL, SEMIGLOBAL, LOCAL = 0, 1, 2  # alignment types of Sec. II (trioseq_plan flags)
-PART_BLOCKED, PART_INTERLEAVED, PART_DYNAMIC = 0, 1, 2  # trioseq_partition schemes (Sec. V-D)
+# trioseq_partition schemes: the three of Sec. V-D, and the dynamic rule taken largest first
+PART_BLOCKED, PART_INTERLEAVED, PART_DYNAMIC, PART_LARGEST_FIRST = 0, 1, 2, 3
 
 
 class TrioseqError(RuntimeError):

@@ -7,7 +7,11 @@
 //    cell count is the least so far (the amount of computation is the paper's cell count,
 //    |S0|*|S1|*|S2|, Sec. V-A). Ties go to the lowest rank.
 // The paper gives no chunk rule for blocked: chunk r here is [floor(r*n/N), floor((r+1)*n/N)),
-// so chunk sizes differ by at most one.
+// so chunk sizes differ by at most one. A fourth scheme, largest first, applies the dynamic rule
+// to the triplets in order of decreasing cell count (ties in dataset order): Graham's LPT list
+// scheduling, whose largest load is at most 4/3 - 1/(3N) times the optimum; in dataset order a
+// few large triplets arriving last can leave one rank far above the rest.
+#include <algorithm>
 #include <cstdint>
 #include <queue>
 #include <utility>
@@ -20,7 +24,7 @@ extern "C" trioseq_status trioseq_partition(const uint32_t* lens, size_t n, int3
                                             uint64_t* cells_per_rank) {
   if (nranks < 1 || (n && (!lens || !rank_of))) return TRIOSEQ_EINVAL;
   if (scheme != TRIOSEQ_PART_BLOCKED && scheme != TRIOSEQ_PART_INTERLEAVED &&
-      scheme != TRIOSEQ_PART_DYNAMIC)
+      scheme != TRIOSEQ_PART_DYNAMIC && scheme != TRIOSEQ_PART_LARGEST_FIRST)
     return TRIOSEQ_EINVAL;
   // the whole set's cell count must fit 64 bits, so every rank's load does too
   unsigned __int128 total = 0;
@@ -46,11 +50,17 @@ extern "C" trioseq_status trioseq_partition(const uint32_t* lens, size_t n, int3
       load[t % N] += cells(t);
     }
   } else {
+    // the order triplets are taken in: dataset order, or decreasing cells (stable)
+    std::vector<size_t> order(n);
+    for (size_t t = 0; t < n; t++) order[t] = t;
+    if (scheme == TRIOSEQ_PART_LARGEST_FIRST)
+      std::stable_sort(order.begin(), order.end(),
+                       [&](size_t x, size_t y) { return cells(x) > cells(y); });
     // least cumulative cells first, then the lowest rank: a min-heap on (load, rank)
     using Entry = std::pair<uint64_t, int32_t>;
     std::priority_queue<Entry, std::vector<Entry>, std::greater<Entry>> heap;
     for (int32_t r = 0; r < nranks; r++) heap.push({0, r});
-    for (size_t t = 0; t < n; t++) {
+    for (size_t t : order) {
       Entry e = heap.top();
       heap.pop();
       rank_of[t] = e.second;

@@ -4,8 +4,12 @@ Checked: blocked and interleaved against their definitions, plus contiguity and 
 dynamic by replaying its rule (each triplet goes to a least-loaded rank, lowest first), by Graham's
 bound for greedy list scheduling (max load <= mean load + the largest triplet), and by the
 paper's two synthetic dataset shapes, each ideal for one static scheme and poor for the other,
-on which dynamic stays balanced; argument errors and the 64-bit overflow check.
+on which dynamic stays balanced; largest first by replaying it on the sorted order and by
+Graham's LPT bound (4/3 - 1/(3N) times the optimum, found by brute force on small sets); argument
+errors and the 64-bit overflow check.
 """
+import itertools
+
 import numpy as np
 import pytest
 
@@ -91,7 +95,7 @@ def test_dataset_shapes_of_sec_v_d():
 
 def test_errors():
     lens = rand_lens(6, 4)
-    for nranks, scheme in ((0, 0), (-1, 2), (2, 3), (2, -1)):
+    for nranks, scheme in ((0, 0), (-1, 2), (2, 4), (2, -1)):
         with pytest.raises(B.TrioseqError) as e:
             B.trioseq_partition(lens, nranks, scheme)
         assert e.value.status == B.EINVAL
@@ -105,3 +109,40 @@ def test_errors():
     with pytest.raises(B.TrioseqError) as e:
         B.trioseq_partition(np.vstack([ok, ok]), 2)
     assert e.value.status == B.EOVERFLOW
+
+
+@pytest.mark.parametrize("seed,n,N", [(11, 40, 3), (12, 4096, 8), (13, 9, 4)])
+def test_largest_first_is_dynamic_on_decreasing_cells(seed, n, N):
+    lens = rand_lens(seed, n)
+    c = cells(lens)
+    order = sorted(range(n), key=lambda t: -c[t])  # stable: ties keep dataset order
+    got, load = B.trioseq_partition(lens, N, B.PART_LARGEST_FIRST)
+    ranks, want_load = replay_dynamic(c[order], N)
+    want = [0] * n
+    for t, r in zip(order, ranks):
+        want[t] = r
+    assert got.tolist() == want and load.tolist() == want_load
+
+
+def test_largest_first_within_graham_lpt_bound_of_optimum():
+    rng = np.random.default_rng(14)
+    for trial in range(40):
+        n, N = int(rng.integers(1, 9)), int(rng.integers(2, 4))
+        lens = rng.integers(1, 12, size=(n, 3))
+        c = cells(lens)
+        opt = min(max(sum(int(c[t]) for t in range(n) if a[t] == r) for r in range(N))
+                  for a in itertools.product(range(N), repeat=n))
+        got = int(B.trioseq_partition(lens, N, B.PART_LARGEST_FIRST)[1].max())
+        assert opt <= got <= (4 / 3 - 1 / (3 * N)) * opt + 1e-9
+
+
+def test_heavy_tailed_set_balances_better_largest_first():
+    """Lengths lognormal(ln 300, 0.8) clipped to [50, 2000] (the serving mix): in dataset order a
+    few very large triplets late in the set unbalance the dynamic scheme; largest first does not."""
+    rng = np.random.default_rng(2024)
+    lens = np.clip(np.exp(rng.normal(np.log(300), 0.8, size=(4096, 3))), 50, 2000).astype(int)
+    for N in (8, 64):
+        dyn = B.trioseq_partition(lens, N, B.PART_DYNAMIC)[1]
+        lpt = B.trioseq_partition(lens, N, B.PART_LARGEST_FIRST)[1]
+        assert lpt.max() <= dyn.max()
+        assert imbalance(lpt) < 1.02
