@@ -440,7 +440,37 @@ def _serve(B, srv, reqs, strs, rate, cap):
     return t_sub, t_done, results, tickets
 
 
-def serving_measurement(B, n_req: int = 2000, load: float = 0.7, n_cal: int = 600):
+def cpu_all_cores_mix(reqs, dna, prot, target_s: float = 3.0):
+    """The oracle on every host core over the serving mix, replayed in arrival order: a prefix of
+    the requests sized for about target_s seconds, each scoring scheme's requests as one
+    multi-threaded batch (scores only; the oracle has no batched traceback)."""
+    import oracle
+    n_cores = os.cpu_count() or 1
+    vol = [len(r["triplet"][0]) * len(r["triplet"][1]) * len(r["triplet"][2]) for r in reqs]
+    probe = [r["triplet"] for r in reqs[:8] if not r["protein"]][:4]
+    t0 = time.perf_counter()
+    oracle.align_many(probe, dna.sub, dna.gap)
+    per_cell = (time.perf_counter() - t0) / max(1, sum(
+        len(a) * len(b) * len(c) for a, b, c in probe))
+    budget = target_s * n_cores / per_cell
+    n, tot = 0, 0
+    while n < len(reqs) and tot < budget:
+        tot += vol[n]
+        n += 1
+    groups = [[r["triplet"] for r in reqs[:n] if r["protein"] == p] for p in (False, True)]
+    t0 = time.perf_counter()
+    for trips, sc in zip(groups, (dna, prot)):
+        if trips:
+            oracle.align_many(trips, sc.sub, sc.gap, threads=n_cores)
+    dt = time.perf_counter() - t0
+    return {"value": tot / dt / 1e9, "unit": "GCUPS", "cores": n_cores, "kind": "oracle",
+            "sample": f"first {n} requests of the mix in arrival order ({len(groups[0])} DNA, "
+                      f"{len(groups[1])} protein; {tot} cells, scores only, {dt:.1f} s)",
+            "host": host_cpu()}
+
+
+def serving_measurement(B, n_req: int = 2000, load: float = 0.7, n_cal: int = 600,
+                        cpu_legs: bool = True):
     """Serving stream: mixed DNA/protein requests (20% traceback). The server's capacity on this
     mix is measured first with a closed-loop burst (n_cal requests submitted at once); the stream
     then arrives with Poisson gaps at `load` x that capacity. Latency = submit to the poll that
@@ -484,6 +514,7 @@ def serving_measurement(B, n_req: int = 2000, load: float = 0.7, n_cal: int = 60
             "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))], "max_ms": lat[-1],
             "aggregate_gcups": sum(cells) / span / 1e9, "span_s": span,
             "identical_to_alone_sample": bool(same),
+            "cpu_all_cores": cpu_all_cores_mix(reqs, dna, prot) if cpu_legs else None,
             "mix": "70% DNA / 30% protein, 20% traceback, ancestor lognormal(ln 300, 0.8) "
                    "clipped to [50, 2000]"}
 
@@ -612,7 +643,7 @@ def aux_measurements(B, torch, stream, flush, sms, clock_mhz, skip: str, cpu_leg
                      "frac": ach_t / peak_t,
                      "code_stream_gbs": CODE_BYTES_PER_CELL * w.cells / kt / 1e6},
         "cells": w.cells}
-    out["serving_stream"] = serving_measurement(B)
+    out["serving_stream"] = serving_measurement(B, cpu_legs=cpu_legs)
     out["dna8000_linear_space_traceback"] = linear_space_measurement(B, torch, stream)
     return out
 

@@ -167,3 +167,14 @@ def test_sharded_batch_gloo_world2():
     assert [c for _, c, _ in shares] == shares[0][2]  # each share's cells = its rank's load
     assert sum(shares[0][2]) == w.cells
     assert all(len(mine) > 0 for mine, _, _ in shares)
+
+
+def test_all_core_oracle_replay_of_the_serving_mix():
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2605_28400_gb300 import synth
+
+    dna, prot, reqs = synth.config4(n=40, hi=120)
+    got = bench.cpu_all_cores_mix(reqs, dna, prot, target_s=0.05)
+    assert got["kind"] == "oracle" and got["value"] > 0 and got["cores"] >= 1
+    assert "requests of the mix" in got["sample"]
