@@ -20,7 +20,10 @@
  * With it the emitted alignment is unique, so results are reproducible bit for bit.
  *
  * Conventions for every call:
- *  - Every call returns a trioseq_status and never aborts the process.
+ *  - Every call returns a trioseq_status and never aborts the process: no C++ exception crosses
+ *    the C boundary, and a failed host allocation returns TRIOSEQ_ENOMEM. For tests, setting
+ *    TRIOSEQ_TEST_HOST_BAD_ALLOC=1 in the environment before the first call makes every call
+ *    except trioseq_strerror fail that way, before it touches its arguments or the GPU.
  *  - The caller owns all inputs and outputs; the library copies what it needs before returning
  *    (host inputs) or reads device inputs only inside the call's stream order.
  *  - Handles are opaque and released by the matching *_destroy call.
@@ -282,7 +285,8 @@ enum { TRIOSEQ_PART_BLOCKED = 0, TRIOSEQ_PART_INTERLEAVED = 1, TRIOSEQ_PART_DYNA
  * Pure host computation: needs no GPU and no plan, allocates O(nranks) host memory, writes no
  * output on error. There is no collective: every rank computes the same partition from the
  * same lengths and keeps its own triplets.
- * Errors: EINVAL (nranks < 1, unknown scheme, null lens or rank_of with n > 0), EOVERFLOW (the
+ * Errors: EINVAL (nranks < 1 or > 2^20, unknown scheme, null lens or rank_of with n > 0),
+ * ENOMEM (host allocation), EOVERFLOW (the
  * set's total cell count exceeds 2^64 - 1). */
 trioseq_status trioseq_partition(const uint32_t* lens, size_t n, int32_t nranks, int32_t scheme,
                                  int32_t* rank_of, uint64_t* cells_per_rank);

@@ -35,6 +35,7 @@ def nvcc() -> str:
 def _inputs():
     files = [os.path.join(CSRC, s) for s in SOURCES]
     files += [os.path.join(CSRC, "engine.h"), os.path.join(CSRC, "wavefront.cuh"),
+              os.path.join(CSRC, "guard.h"),
               os.path.join(CSRC, "wavefront_vl.cuh"),
               os.path.join(ROOT, "include", "trioseq.h")]
     return files

@@ -16,6 +16,9 @@
 #include <vector>
 
 #include "trioseq.h"
+#include "guard.h"
+
+using trioseq::no_throw;
 
 namespace {
 
@@ -83,85 +86,90 @@ int occupancy() {
 }  // namespace
 
 extern "C" trioseq_status trioseq_alu_rate(int32_t op, double* per_clk_per_sm, double* sm_mhz) {
-  if (op < 0 || op > 4 || !per_clk_per_sm || !sm_mhz) return TRIOSEQ_EINVAL;
-  int dev = 0, sms = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess ||
-      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-    cudaGetLastError();
-    return TRIOSEQ_ECUDA;
-  }
-  // one wave: every SM holds its resident maximum of blocks for the whole run
-  const int per_sm = op == 0 ? occupancy<0>() : op == 1 ? occupancy<1>() : op == 2 ? occupancy<2>()
-                     : op == 3 ? occupancy<3>() : occupancy<4>();
-  if (per_sm <= 0) {
-    cudaGetLastError();
-    return TRIOSEQ_ECUDA;
-  }
-  const int grid = sms * per_sm;
-  const int iters = 1 << 14;
-  int* sink = nullptr;
-  long long* stamps = nullptr;
-  cudaStream_t st = nullptr;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  trioseq_status status = TRIOSEQ_ECUDA;
-  std::vector<long long> stm(3 * (size_t)grid);
-  float ms = 0.f;
-  const auto run = [&](cudaStream_t s) -> cudaError_t {
-    switch (op) {
-      case 0: return launch<0>(grid, iters, sink, stamps, s);
-      case 1: return launch<1>(grid, iters, sink, stamps, s);
-      case 2: return launch<2>(grid, iters, sink, stamps, s);
-      case 3: return launch<3>(grid, iters, sink, stamps, s);
-      default: return launch<4>(grid, iters, sink, stamps, s);
+  return no_throw([&]() -> trioseq_status {
+    if (op < 0 || op > 4 || !per_clk_per_sm || !sm_mhz) return TRIOSEQ_EINVAL;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      return TRIOSEQ_ECUDA;
     }
-  };
-  do {
-    if (cudaMalloc(&sink, sizeof(int) * (size_t)grid * kThreads) != cudaSuccess ||
-        cudaMalloc(&stamps, sizeof(long long) * 3 * (size_t)grid) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
-      break;
-    if (run(st) != cudaSuccess) break;  // warm-up (clocks up, code loaded)
-    if (cudaEventRecord(e0, st) != cudaSuccess || run(st) != cudaSuccess ||
-        cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-        cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess ||
-        cudaMemcpy(stm.data(), stamps, sizeof(long long) * 3 * (size_t)grid,
-                   cudaMemcpyDeviceToHost) != cudaSuccess)
-      break;
-    // per SM: blocks it ran, first start, last end (its own clock)
-    std::vector<long long> first(1024, -1), last(1024, -1), nblk(1024, 0);
-    bool bad = false;
-    for (int g = 0; g < grid && !bad; g++) {
-      const long long sm = stm[3 * (size_t)g], t0 = stm[3 * (size_t)g + 1],
-                      t1 = stm[3 * (size_t)g + 2];
-      if (sm < 0 || sm >= 1024) {
-        bad = true;
+    // one wave: every SM holds its resident maximum of blocks for the whole run
+    const int per_sm = op == 0   ? occupancy<0>()
+                       : op == 1 ? occupancy<1>()
+                       : op == 2 ? occupancy<2>()
+                       : op == 3 ? occupancy<3>()
+                                 : occupancy<4>();
+    if (per_sm <= 0) {
+      cudaGetLastError();
+      return TRIOSEQ_ECUDA;
+    }
+    const int grid = sms * per_sm;
+    const int iters = 1 << 14;
+    int* sink = nullptr;
+    long long* stamps = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    trioseq_status status = TRIOSEQ_ECUDA;
+    std::vector<long long> stm(3 * (size_t)grid);
+    float ms = 0.f;
+    const auto run = [&](cudaStream_t s) -> cudaError_t {
+      switch (op) {
+        case 0: return launch<0>(grid, iters, sink, stamps, s);
+        case 1: return launch<1>(grid, iters, sink, stamps, s);
+        case 2: return launch<2>(grid, iters, sink, stamps, s);
+        case 3: return launch<3>(grid, iters, sink, stamps, s);
+        default: return launch<4>(grid, iters, sink, stamps, s);
+      }
+    };
+    do {
+      if (cudaMalloc(&sink, sizeof(int) * (size_t)grid * kThreads) != cudaSuccess ||
+          cudaMalloc(&stamps, sizeof(long long) * 3 * (size_t)grid) != cudaSuccess ||
+          cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         break;
+      if (run(st) != cudaSuccess) break;  // warm-up (clocks up, code loaded)
+      if (cudaEventRecord(e0, st) != cudaSuccess || run(st) != cudaSuccess ||
+          cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess ||
+          cudaMemcpy(stm.data(), stamps, sizeof(long long) * 3 * (size_t)grid,
+                     cudaMemcpyDeviceToHost) != cudaSuccess)
+        break;
+      // per SM: blocks it ran, first start, last end (its own clock)
+      std::vector<long long> first(1024, -1), last(1024, -1), nblk(1024, 0);
+      bool bad = false;
+      for (int g = 0; g < grid && !bad; g++) {
+        const long long sm = stm[3 * (size_t)g], t0 = stm[3 * (size_t)g + 1],
+                        t1 = stm[3 * (size_t)g + 2];
+        if (sm < 0 || sm >= 1024) {
+          bad = true;
+          break;
+        }
+        first[sm] = first[sm] < 0 ? t0 : std::min(first[sm], t0);
+        last[sm] = std::max(last[sm], t1);
+        nblk[sm]++;
       }
-      first[sm] = first[sm] < 0 ? t0 : std::min(first[sm], t0);
-      last[sm] = std::max(last[sm], t1);
-      nblk[sm]++;
-    }
-    if (bad) break;
-    std::vector<double> rates, spans;
-    for (int sm = 0; sm < 1024; sm++)
-      if (nblk[sm] > 0 && last[sm] > first[sm]) {
-        const double span = (double)(last[sm] - first[sm]);
-        rates.push_back((double)nblk[sm] * kThreads * (double)iters * kChains / span);
-        spans.push_back(span);
-      }
-    if (rates.empty()) break;
-    std::sort(rates.begin(), rates.end());
-    *per_clk_per_sm = rates[rates.size() / 2];  // median over SMs
-    const double max_span = *std::max_element(spans.begin(), spans.end());
-    *sm_mhz = ms > 0 ? max_span / ((double)ms * 1e3) : 0.0;
-    status = TRIOSEQ_OK;
-  } while (false);
-  if (status != TRIOSEQ_OK) cudaGetLastError();
-  if (e0) cudaEventDestroy(e0);
-  if (e1) cudaEventDestroy(e1);
-  if (st) cudaStreamDestroy(st);
-  if (stamps) cudaFree(stamps);
-  if (sink) cudaFree(sink);
-  return status;
+      if (bad) break;
+      std::vector<double> rates, spans;
+      for (int sm = 0; sm < 1024; sm++)
+        if (nblk[sm] > 0 && last[sm] > first[sm]) {
+          const double span = (double)(last[sm] - first[sm]);
+          rates.push_back((double)nblk[sm] * kThreads * (double)iters * kChains / span);
+          spans.push_back(span);
+        }
+      if (rates.empty()) break;
+      std::sort(rates.begin(), rates.end());
+      *per_clk_per_sm = rates[rates.size() / 2];  // median over SMs
+      const double max_span = *std::max_element(spans.begin(), spans.end());
+      *sm_mhz = ms > 0 ? max_span / ((double)ms * 1e3) : 0.0;
+      status = TRIOSEQ_OK;
+    } while (false);
+    if (status != TRIOSEQ_OK) cudaGetLastError();
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    if (stamps) cudaFree(stamps);
+    if (sink) cudaFree(sink);
+    return status;
+  });
 }

@@ -32,6 +32,7 @@
 #include <nvtx3/nvToolsExt.h>
 
 #include "engine.h"
+#include "guard.h"
 #include "trioseq.h"
 
 using namespace trioseq;
@@ -919,319 +920,357 @@ const char* trioseq_strerror(trioseq_status st) {
 
 trioseq_status trioseq_plan(const trioseq_scoring* sc, uint32_t max_len_hint, uint32_t flags,
                             trioseq_plan_t* out) {
-  (void)max_len_hint;
-  NvtxRange range("trioseq_plan");
-  if (!out) return TRIOSEQ_EINVAL;
-  *out = nullptr;
-  if (!sc || !sc->alphabet || !sc->sub || flags > TRIOSEQ_LOCAL) return TRIOSEQ_EINVAL;
-  const int K = sc->alphabet_size;
-  if (K < 1 || K > kMaxAlphabet || sc->gap > 0 || sc->gap < -127) return TRIOSEQ_EINVAL;
-  std::unique_ptr<trioseq_plan_s> plan(new (std::nothrow) trioseq_plan_s());
-  if (!plan) return TRIOSEQ_ENOMEM;
-  for (int i = 0; i < 256; i++) plan->lut[i] = -1;
-  for (int i = 0; i < K; i++) {
-    const unsigned char ch = (unsigned char)sc->alphabet[i];
-    if (plan->lut[ch] >= 0) return TRIOSEQ_EINVAL;  // duplicate residue
-    plan->lut[ch] = (int16_t)i;
-    plan->alphabet[i] = (char)ch;
-  }
-  for (int i = 0; i < K; i++)
-    for (int j = 0; j < K; j++)
-      if (sc->sub[i * K + j] != sc->sub[j * K + i]) return TRIOSEQ_EINVAL;
-  plan->K = K;
-  plan->KP = K + 1;
-  plan->gap = sc->gap;
-  plan->atype = (int)flags;
-  plan->sub.assign(sc->sub, sc->sub + K * K);
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) {
-    cudaGetLastError();
-    return TRIOSEQ_ECUDA;
-  }
-  plan->device = dev;
-  if (cudaDeviceGetAttribute(&plan->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
-    cudaGetLastError();
-    return TRIOSEQ_ECUDA;
-  }
-  const int KP = K + 1;
-  std::vector<int32_t> s2((size_t)KP * KP, 0), s8((size_t)KP * KP, 0);
-  int32_t mx = 0, mn = 0;
-  for (int i = 0; i < K; i++)
-    for (int j = 0; j < K; j++) {
-      const int32_t v = (int32_t)sc->sub[i * K + j] - 2 * sc->gap;  // sigma'' = sigma - 2 alpha
-      s2[(size_t)i * KP + j] = v;
-      s8[(size_t)i * KP + j] = 8 * v;
-      mx = std::max(mx, std::abs(v));
-      mn = std::min(mn, v);
+  return no_throw([&]() -> trioseq_status {
+    (void)max_len_hint;
+    NvtxRange range("trioseq_plan");
+    if (!out) return TRIOSEQ_EINVAL;
+    *out = nullptr;
+    if (!sc || !sc->alphabet || !sc->sub || flags > TRIOSEQ_LOCAL) return TRIOSEQ_EINVAL;
+    const int K = sc->alphabet_size;
+    if (K < 1 || K > kMaxAlphabet || sc->gap > 0 || sc->gap < -127) return TRIOSEQ_EINVAL;
+    std::unique_ptr<trioseq_plan_s> plan(new (std::nothrow) trioseq_plan_s());
+    if (!plan) return TRIOSEQ_ENOMEM;
+    for (int i = 0; i < 256; i++) plan->lut[i] = -1;
+    for (int i = 0; i < K; i++) {
+      const unsigned char ch = (unsigned char)sc->alphabet[i];
+      if (plan->lut[ch] >= 0) return TRIOSEQ_EINVAL;  // duplicate residue
+      plan->lut[ch] = (int16_t)i;
+      plan->alphabet[i] = (char)ch;
     }
-  plan->max_abs_sig2 = std::max(mx, 1);
-  plan->sig2_nonneg = mn >= 0;
-  if (!plan->sig_score.ensure(s2.size() * 4) || !plan->sig_tb.ensure(s8.size() * 4))
-    return TRIOSEQ_ENOMEM;
-  if (cudaMemcpy(plan->sig_score.p, s2.data(), s2.size() * 4, cudaMemcpyHostToDevice) !=
-          cudaSuccess ||
-      cudaMemcpy(plan->sig_tb.p, s8.data(), s8.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
-    return cuda_status(cudaGetLastError());
-  plan->TI = std::max(1, env_int("TRIOSEQ_TI", 8));
-  plan->graphs = env_int("TRIOSEQ_GRAPHS", 1) != 0;
-  plan->packed16 = env_int("TRIOSEQ_PACKED", 1) != 0;
-  plan->pace = env_int("TRIOSEQ_PACE", 1) != 0;
-  plan->wait_ns = (int64_t)std::max(1, env_int("TRIOSEQ_WAIT_MS", 2000)) * 1000000LL;
-  plan->test_wait_unset = env_int("TRIOSEQ_TEST_WAIT_UNSET", 0) != 0;
-  g_alloc_calls.store(0);
-  g_alloc_fail_at.store(std::max(0, env_int("TRIOSEQ_TEST_FAIL_ALLOC", 0)));
-  {
-    size_t fr = 0, tot = 0;
-    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+    for (int i = 0; i < K; i++)
+      for (int j = 0; j < K; j++)
+        if (sc->sub[i * K + j] != sc->sub[j * K + i]) return TRIOSEQ_EINVAL;
+    plan->K = K;
+    plan->KP = K + 1;
+    plan->gap = sc->gap;
+    plan->atype = (int)flags;
+    plan->sub.assign(sc->sub, sc->sub + K * K);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
       cudaGetLastError();
-      fr = 0;
+      return TRIOSEQ_ECUDA;
     }
-    const int mb = env_int("TRIOSEQ_SLAB_BUDGET_MB", 0);
-    plan->slab_budget = mb > 0 ? (size_t)mb << 20 : fr / 2;
-    plan->slab_slices = std::max(0, env_int("TRIOSEQ_SLAB_SLICES", 0));
-  }
-  // "RxC": register tile rows x columns per lane
-  const auto parse_tile = [](const char* v, Variant* out) {
-    if (!v) return;
-    char* end = nullptr;
-    const long rj = std::strtol(v, &end, 10);
-    if (!end || *end != 'x') return;
-    char* end2 = nullptr;
-    const long ck = std::strtol(end + 1, &end2, 10);
-    // "8x16" and a trailing 'v' ("8x8v") select the two-cells-per-register kernel
-    const int two = (ck == 16 || (end2 && *end2 == 'v')) ? 1 : 0;
-    if (rj > 0 && rj <= 16 && ck > 0 && ck <= 32) *out = Variant{(int)rj, (int)ck, two};
-  };
-  parse_tile(std::getenv("TRIOSEQ_SCORE_TILE"), &plan->score_variant);
-  parse_tile(std::getenv("TRIOSEQ_TB_TILE"), &plan->tb_variant);
-  *out = plan.release();
-  return TRIOSEQ_OK;
+    plan->device = dev;
+    if (cudaDeviceGetAttribute(&plan->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      return TRIOSEQ_ECUDA;
+    }
+    const int KP = K + 1;
+    std::vector<int32_t> s2((size_t)KP * KP, 0), s8((size_t)KP * KP, 0);
+    int32_t mx = 0, mn = 0;
+    for (int i = 0; i < K; i++)
+      for (int j = 0; j < K; j++) {
+        const int32_t v = (int32_t)sc->sub[i * K + j] - 2 * sc->gap;  // sigma'' = sigma - 2 alpha
+        s2[(size_t)i * KP + j] = v;
+        s8[(size_t)i * KP + j] = 8 * v;
+        mx = std::max(mx, std::abs(v));
+        mn = std::min(mn, v);
+      }
+    plan->max_abs_sig2 = std::max(mx, 1);
+    plan->sig2_nonneg = mn >= 0;
+    if (!plan->sig_score.ensure(s2.size() * 4) || !plan->sig_tb.ensure(s8.size() * 4))
+      return TRIOSEQ_ENOMEM;
+    if (cudaMemcpy(plan->sig_score.p, s2.data(), s2.size() * 4, cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(plan->sig_tb.p, s8.data(), s8.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+      return cuda_status(cudaGetLastError());
+    plan->TI = std::max(1, env_int("TRIOSEQ_TI", 8));
+    plan->graphs = env_int("TRIOSEQ_GRAPHS", 1) != 0;
+    plan->packed16 = env_int("TRIOSEQ_PACKED", 1) != 0;
+    plan->pace = env_int("TRIOSEQ_PACE", 1) != 0;
+    plan->wait_ns = (int64_t)std::max(1, env_int("TRIOSEQ_WAIT_MS", 2000)) * 1000000LL;
+    plan->test_wait_unset = env_int("TRIOSEQ_TEST_WAIT_UNSET", 0) != 0;
+    g_alloc_calls.store(0);
+    g_alloc_fail_at.store(std::max(0, env_int("TRIOSEQ_TEST_FAIL_ALLOC", 0)));
+    {
+      size_t fr = 0, tot = 0;
+      if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+        cudaGetLastError();
+        fr = 0;
+      }
+      const int mb = env_int("TRIOSEQ_SLAB_BUDGET_MB", 0);
+      plan->slab_budget = mb > 0 ? (size_t)mb << 20 : fr / 2;
+      plan->slab_slices = std::max(0, env_int("TRIOSEQ_SLAB_SLICES", 0));
+    }
+    // "RxC": register tile rows x columns per lane
+    const auto parse_tile = [](const char* v, Variant* out) {
+      if (!v) return;
+      char* end = nullptr;
+      const long rj = std::strtol(v, &end, 10);
+      if (!end || *end != 'x') return;
+      char* end2 = nullptr;
+      const long ck = std::strtol(end + 1, &end2, 10);
+      // "8x16" and a trailing 'v' ("8x8v") select the two-cells-per-register kernel
+      const int two = (ck == 16 || (end2 && *end2 == 'v')) ? 1 : 0;
+      if (rj > 0 && rj <= 16 && ck > 0 && ck <= 32) *out = Variant{(int)rj, (int)ck, two};
+    };
+    parse_tile(std::getenv("TRIOSEQ_SCORE_TILE"), &plan->score_variant);
+    parse_tile(std::getenv("TRIOSEQ_TB_TILE"), &plan->tb_variant);
+    *out = plan.release();
+    return TRIOSEQ_OK;
+  });
 }
 
 trioseq_status trioseq_plan_destroy(trioseq_plan_t plan) {
-  if (!plan) return TRIOSEQ_OK;
-  DeviceGuard g(plan->device);
-  cudaDeviceSynchronize();
-  delete plan;
-  return TRIOSEQ_OK;
+  return no_throw([&]() -> trioseq_status {
+    if (!plan) return TRIOSEQ_OK;
+    DeviceGuard g(plan->device);
+    cudaDeviceSynchronize();
+    delete plan;
+    return TRIOSEQ_OK;
+  });
 }
 
 trioseq_status trioseq_align_batch(trioseq_plan_t plan, const trioseq_triplet* triplets, size_t n,
                                    uint32_t mode, int32_t* scores_out, void* stream) {
-  NvtxRange range("trioseq_align_batch");
-  if (!plan || (n && !scores_out)) return TRIOSEQ_EINVAL;
-  DeviceGuard g(plan->device);
-  cudaStream_t st = (cudaStream_t)stream;
-  std::unique_ptr<trioseq_batch_s> bt(new (std::nothrow) trioseq_batch_s());
-  if (!bt) return TRIOSEQ_ENOMEM;
-  plan->last.reset();
-  trioseq_status s = build_batch(plan, triplets, n, mode, bt.get());
-  if (s != TRIOSEQ_OK) return s;
-  bt->ws = &plan->ws;
-  if ((s = upload(bt.get(), st, true)) != TRIOSEQ_OK) return s;
-  if ((s = run(bt.get(), st)) != TRIOSEQ_OK) return s;
-  if ((s = fetch(bt.get(), st, scores_out)) != TRIOSEQ_OK) return s;
-  bt->seq.clear();
-  bt->seq.shrink_to_fit();
-  plan->last = std::move(bt);
-  return TRIOSEQ_OK;
+  return no_throw([&]() -> trioseq_status {
+    NvtxRange range("trioseq_align_batch");
+    if (!plan || (n && !scores_out)) return TRIOSEQ_EINVAL;
+    DeviceGuard g(plan->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    std::unique_ptr<trioseq_batch_s> bt(new (std::nothrow) trioseq_batch_s());
+    if (!bt) return TRIOSEQ_ENOMEM;
+    plan->last.reset();
+    trioseq_status s = build_batch(plan, triplets, n, mode, bt.get());
+    if (s != TRIOSEQ_OK) return s;
+    bt->ws = &plan->ws;
+    if ((s = upload(bt.get(), st, true)) != TRIOSEQ_OK) return s;
+    if ((s = run(bt.get(), st)) != TRIOSEQ_OK) return s;
+    if ((s = fetch(bt.get(), st, scores_out)) != TRIOSEQ_OK) return s;
+    bt->seq.clear();
+    bt->seq.shrink_to_fit();
+    plan->last = std::move(bt);
+    return TRIOSEQ_OK;
+  });
 }
 
 trioseq_status trioseq_traceback(trioseq_plan_t plan, size_t idx, char* row0, char* row1,
                                  char* row2, size_t cap, size_t* aln_len) {
-  NvtxRange range("trioseq_traceback");
-  if (!plan || !plan->last) return TRIOSEQ_EINVAL;
-  return copy_alignment(plan->last.get(), idx, row0, row1, row2, cap, aln_len);
+  return no_throw([&]() -> trioseq_status {
+    NvtxRange range("trioseq_traceback");
+    if (!plan || !plan->last) return TRIOSEQ_EINVAL;
+    return copy_alignment(plan->last.get(), idx, row0, row1, row2, cap, aln_len);
+  });
 }
 
 trioseq_status trioseq_traceback_span(trioseq_plan_t plan, size_t idx, int32_t begin[3],
                                       int32_t end[3]) {
-  if (!plan || !plan->last) return TRIOSEQ_EINVAL;
-  return copy_span(plan->last.get(), idx, begin, end);
+  return no_throw([&]() -> trioseq_status {
+    if (!plan || !plan->last) return TRIOSEQ_EINVAL;
+    return copy_span(plan->last.get(), idx, begin, end);
+  });
 }
 
 trioseq_status trioseq_batch_create(trioseq_plan_t plan, const trioseq_triplet* triplets,
                                     size_t n, uint32_t mode, trioseq_batch_t* out) {
-  NvtxRange range("trioseq_batch_create");
-  if (!plan || !out) return TRIOSEQ_EINVAL;
-  *out = nullptr;
-  DeviceGuard g(plan->device);
-  std::unique_ptr<trioseq_batch_s> bt(new (std::nothrow) trioseq_batch_s());
-  if (!bt) return TRIOSEQ_ENOMEM;
-  trioseq_status s = build_batch(plan, triplets, n, mode, bt.get());
-  if (s != TRIOSEQ_OK) return s;
-  bt->own_ws.reset(new (std::nothrow) Workspace());
-  if (!bt->own_ws) return TRIOSEQ_ENOMEM;
-  bt->ws = bt->own_ws.get();
-  if ((s = upload(bt.get(), nullptr, false)) != TRIOSEQ_OK) return s;
-  *out = bt.release();
-  return TRIOSEQ_OK;
+  return no_throw([&]() -> trioseq_status {
+    NvtxRange range("trioseq_batch_create");
+    if (!plan || !out) return TRIOSEQ_EINVAL;
+    *out = nullptr;
+    DeviceGuard g(plan->device);
+    std::unique_ptr<trioseq_batch_s> bt(new (std::nothrow) trioseq_batch_s());
+    if (!bt) return TRIOSEQ_ENOMEM;
+    trioseq_status s = build_batch(plan, triplets, n, mode, bt.get());
+    if (s != TRIOSEQ_OK) return s;
+    bt->own_ws.reset(new (std::nothrow) Workspace());
+    if (!bt->own_ws) return TRIOSEQ_ENOMEM;
+    bt->ws = bt->own_ws.get();
+    if ((s = upload(bt.get(), nullptr, false)) != TRIOSEQ_OK) return s;
+    *out = bt.release();
+    return TRIOSEQ_OK;
+  });
 }
 
 trioseq_status trioseq_batch_run(trioseq_batch_t bt, void* stream) {
-  NvtxRange range("trioseq_batch_run");
-  if (!bt) return TRIOSEQ_EINVAL;
-  DeviceGuard g(bt->plan->device);
-  return bt->plan->graphs ? run_graph(bt, (cudaStream_t)stream) : run(bt, (cudaStream_t)stream);
+  return no_throw([&]() -> trioseq_status {
+    NvtxRange range("trioseq_batch_run");
+    if (!bt) return TRIOSEQ_EINVAL;
+    DeviceGuard g(bt->plan->device);
+    return bt->plan->graphs ? run_graph(bt, (cudaStream_t)stream) : run(bt, (cudaStream_t)stream);
+  });
 }
 
 trioseq_status trioseq_batch_scores(trioseq_batch_t bt, void* stream, int32_t* scores_out) {
-  if (!bt || (bt->n && !scores_out)) return TRIOSEQ_EINVAL;
-  DeviceGuard g(bt->plan->device);
-  return fetch(bt, (cudaStream_t)stream, scores_out);
+  return no_throw([&]() -> trioseq_status {
+    if (!bt || (bt->n && !scores_out)) return TRIOSEQ_EINVAL;
+    DeviceGuard g(bt->plan->device);
+    return fetch(bt, (cudaStream_t)stream, scores_out);
+  });
 }
 
 trioseq_status trioseq_batch_device_scores(trioseq_batch_t bt, int32_t** d_scores) {
-  if (!bt || !d_scores) return TRIOSEQ_EINVAL;
-  *d_scores = bt->ws->scores.as<int32_t>();
-  return TRIOSEQ_OK;
+  return no_throw([&]() -> trioseq_status {
+    if (!bt || !d_scores) return TRIOSEQ_EINVAL;
+    *d_scores = bt->ws->scores.as<int32_t>();
+    return TRIOSEQ_OK;
+  });
 }
 
 trioseq_status trioseq_batch_alignment(trioseq_batch_t bt, size_t idx, char* row0, char* row1,
                                        char* row2, size_t cap, size_t* aln_len) {
-  return copy_alignment(bt, idx, row0, row1, row2, cap, aln_len);
+  return no_throw([&]() -> trioseq_status {
+    return copy_alignment(bt, idx, row0, row1, row2, cap, aln_len);
+  });
 }
 
 trioseq_status trioseq_batch_span(trioseq_batch_t bt, size_t idx, int32_t begin[3],
                                   int32_t end[3]) {
-  return copy_span(bt, idx, begin, end);
+  return no_throw([&]() -> trioseq_status {
+    return copy_span(bt, idx, begin, end);
+  });
 }
 
 trioseq_status trioseq_batch_info(trioseq_batch_t bt, size_t* n, uint64_t* cells, uint64_t* tasks,
                                   int32_t* tile_j, int32_t* tile_k) {
-  if (!bt) return TRIOSEQ_EINVAL;
-  if (n) *n = bt->n;
-  if (cells) *cells = bt->cells;
-  if (tasks) *tasks = bt->tasks.size();
-  if (tile_j) *tile_j = bt->var.nj;
-  if (tile_k) *tile_k = bt->var.nk;
-  return TRIOSEQ_OK;
+  return no_throw([&]() -> trioseq_status {
+    if (!bt) return TRIOSEQ_EINVAL;
+    if (n) *n = bt->n;
+    if (cells) *cells = bt->cells;
+    if (tasks) *tasks = bt->tasks.size();
+    if (tile_j) *tile_j = bt->var.nj;
+    if (tile_k) *tile_k = bt->var.nk;
+    return TRIOSEQ_OK;
+  });
 }
 
 trioseq_status trioseq_batch_slabs(trioseq_batch_t bt, int32_t* slices, int32_t* slabs) {
-  if (!bt || !slices || !slabs) return TRIOSEQ_EINVAL;
-  *slices = bt->slab;
-  *slabs = bt->nslab;
-  return TRIOSEQ_OK;
+  return no_throw([&]() -> trioseq_status {
+    if (!bt || !slices || !slabs) return TRIOSEQ_EINVAL;
+    *slices = bt->slab;
+    *slabs = bt->nslab;
+    return TRIOSEQ_OK;
+  });
 }
 
 trioseq_status trioseq_batch_packing(trioseq_batch_t bt, int32_t* per_word) {
-  if (!bt || !per_word) return TRIOSEQ_EINVAL;
-  *per_word = bt->packed ? 2 : 1;
-  return TRIOSEQ_OK;
+  return no_throw([&]() -> trioseq_status {
+    if (!bt || !per_word) return TRIOSEQ_EINVAL;
+    *per_word = bt->packed ? 2 : 1;
+    return TRIOSEQ_OK;
+  });
 }
 
 trioseq_status trioseq_batch_profile(trioseq_batch_t bt, int32_t enable) {
-  if (!bt) return TRIOSEQ_EINVAL;
-  DeviceGuard g(bt->plan->device);
-  if (enable)
-    for (auto& e : bt->ev)
-      if (!e && cudaEventCreate(&e) != cudaSuccess) return cuda_status(cudaGetLastError());
-  bt->profile = enable != 0;
-  bt->timed = false;
-  return TRIOSEQ_OK;
+  return no_throw([&]() -> trioseq_status {
+    if (!bt) return TRIOSEQ_EINVAL;
+    DeviceGuard g(bt->plan->device);
+    if (enable)
+      for (auto& e : bt->ev)
+        if (!e && cudaEventCreate(&e) != cudaSuccess) return cuda_status(cudaGetLastError());
+    bt->profile = enable != 0;
+    bt->timed = false;
+    return TRIOSEQ_OK;
+  });
 }
 
 trioseq_status trioseq_batch_timing(trioseq_batch_t bt, float ms[2]) {
-  if (!bt || !ms || !bt->profile || !bt->timed) return TRIOSEQ_EINVAL;
-  DeviceGuard g(bt->plan->device);
-  float a = 0.f, b = 0.f;
-  if (cudaEventElapsedTime(&a, bt->ev[0], bt->ev[1]) != cudaSuccess ||
-      cudaEventElapsedTime(&b, bt->ev[1], bt->ev[2]) != cudaSuccess)
-    return cuda_status(cudaGetLastError());
-  ms[0] = a;
-  ms[1] = b;
-  return TRIOSEQ_OK;
+  return no_throw([&]() -> trioseq_status {
+    if (!bt || !ms || !bt->profile || !bt->timed) return TRIOSEQ_EINVAL;
+    DeviceGuard g(bt->plan->device);
+    float a = 0.f, b = 0.f;
+    if (cudaEventElapsedTime(&a, bt->ev[0], bt->ev[1]) != cudaSuccess ||
+        cudaEventElapsedTime(&b, bt->ev[1], bt->ev[2]) != cudaSuccess)
+      return cuda_status(cudaGetLastError());
+    ms[0] = a;
+    ms[1] = b;
+    return TRIOSEQ_OK;
+  });
 }
 
 trioseq_status trioseq_plan_autotune(trioseq_plan_t plan, const trioseq_triplet* sample, size_t n,
                                      uint32_t mode, int32_t* tile_j, int32_t* tile_k,
                                      int32_t* ti) {
-  NvtxRange range("trioseq_plan_autotune");
-  if (!plan || !sample || n == 0 || mode > TRIOSEQ_WITH_TRACEBACK) return TRIOSEQ_EINVAL;
-  DeviceGuard g(plan->device);
-  // candidate tiles per mode; 8x4 exists for traceback keys only
-  // 8x16 and 8x8 with vl: two cells of one triplet per register
-  static const Variant kScoreTiles[] = {{8, 8}, {4, 8}, {4, 4}, {8, 16, 1}, {8, 8, 1}};
-  static const Variant kTbTiles[] = {{8, 8}, {4, 8}, {4, 4}, {8, 4}};
-  static const int kTI[] = {4, 8, 16, 32};
-  const bool tb_mode = mode == TRIOSEQ_WITH_TRACEBACK;
-  const Variant* tiles = tb_mode ? kTbTiles : kScoreTiles;
-  const size_t ntiles = tb_mode ? sizeof(kTbTiles) / sizeof(kTbTiles[0])
-                                : sizeof(kScoreTiles) / sizeof(kScoreTiles[0]);
-  uint32_t maxlen = 0;
-  for (size_t t = 0; t < n; t++)
-    for (int q = 0; q < 3; q++) maxlen = std::max(maxlen, sample[t].len[q]);
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
-    return cuda_status(cudaGetLastError());
-  trioseq_status result = TRIOSEQ_OK;
-  float best = 3.0e38f;
-  trioseq_plan_s::Tuned bestv{mode == TRIOSEQ_WITH_TRACEBACK ? plan->tb_variant
-                                                             : plan->score_variant,
-                              plan->TI};
-  {
-    Workspace ws;  // one workspace, grown to the largest candidate
-    plan->tuning = true;
-    for (size_t vi = 0; vi < ntiles; vi++) {
-      const Variant& v = tiles[vi];
-      for (int ti : kTI) {
-        plan->forced = trioseq_plan_s::Tuned{v, ti};
-        trioseq_batch_s bt;
-        trioseq_status s = build_batch(plan, sample, n, mode, &bt);
-        if (s == TRIOSEQ_ECUDA) continue;  // variant cannot be resident with this alphabet
-        if (s != TRIOSEQ_OK) {
-          result = s;
-          break;
+  return no_throw([&]() -> trioseq_status {
+    NvtxRange range("trioseq_plan_autotune");
+    if (!plan || !sample || n == 0 || mode > TRIOSEQ_WITH_TRACEBACK) return TRIOSEQ_EINVAL;
+    DeviceGuard g(plan->device);
+    // candidate tiles per mode; 8x4 exists for traceback keys only
+    // 8x16 and 8x8 with vl: two cells of one triplet per register
+    static const Variant kScoreTiles[] = {{8, 8}, {4, 8}, {4, 4}, {8, 16, 1}, {8, 8, 1}};
+    static const Variant kTbTiles[] = {{8, 8}, {4, 8}, {4, 4}, {8, 4}};
+    static const int kTI[] = {4, 8, 16, 32};
+    const bool tb_mode = mode == TRIOSEQ_WITH_TRACEBACK;
+    const Variant* tiles = tb_mode ? kTbTiles : kScoreTiles;
+    const size_t ntiles = tb_mode ? sizeof(kTbTiles) / sizeof(kTbTiles[0])
+                                  : sizeof(kScoreTiles) / sizeof(kScoreTiles[0]);
+    uint32_t maxlen = 0;
+    for (size_t t = 0; t < n; t++)
+      for (int q = 0; q < 3; q++) maxlen = std::max(maxlen, sample[t].len[q]);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+      return cuda_status(cudaGetLastError());
+    trioseq_status result = TRIOSEQ_OK;
+    float best = 3.0e38f;
+    trioseq_plan_s::Tuned bestv{mode == TRIOSEQ_WITH_TRACEBACK ? plan->tb_variant
+                                                               : plan->score_variant,
+                                plan->TI};
+    {
+      Workspace ws;  // one workspace, grown to the largest candidate
+      plan->tuning = true;
+      for (size_t vi = 0; vi < ntiles; vi++) {
+        const Variant& v = tiles[vi];
+        for (int ti : kTI) {
+          plan->forced = trioseq_plan_s::Tuned{v, ti};
+          trioseq_batch_s bt;
+          trioseq_status s = build_batch(plan, sample, n, mode, &bt);
+          if (s == TRIOSEQ_ECUDA) continue;  // variant cannot be resident with this alphabet
+          if (s != TRIOSEQ_OK) {
+            result = s;
+            break;
+          }
+          bt.ws = &ws;
+          if ((s = upload(&bt, nullptr, false)) != TRIOSEQ_OK ||
+              (s = run(&bt, nullptr)) != TRIOSEQ_OK ||
+              (s = fetch(&bt, nullptr, nullptr)) != TRIOSEQ_OK) {
+            result = s;
+            break;
+          }
+          float ms = 0.f;
+          cudaEventRecord(e0, nullptr);
+          for (int rep = 0; rep < 2 && s == TRIOSEQ_OK; rep++) s = run(&bt, nullptr);
+          cudaEventRecord(e1, nullptr);
+          if (s == TRIOSEQ_OK) s = fetch(&bt, nullptr, nullptr);
+          if (s != TRIOSEQ_OK || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            result = s != TRIOSEQ_OK ? s : cuda_status(cudaGetLastError());
+            break;
+          }
+          if (ms < best) {
+            best = ms;
+            bestv = trioseq_plan_s::Tuned{v, ti};
+          }
         }
-        bt.ws = &ws;
-        if ((s = upload(&bt, nullptr, false)) != TRIOSEQ_OK ||
-            (s = run(&bt, nullptr)) != TRIOSEQ_OK ||
-            (s = fetch(&bt, nullptr, nullptr)) != TRIOSEQ_OK) {
-          result = s;
-          break;
-        }
-        float ms = 0.f;
-        cudaEventRecord(e0, nullptr);
-        for (int rep = 0; rep < 2 && s == TRIOSEQ_OK; rep++) s = run(&bt, nullptr);
-        cudaEventRecord(e1, nullptr);
-        if (s == TRIOSEQ_OK) s = fetch(&bt, nullptr, nullptr);
-        if (s != TRIOSEQ_OK || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
-          result = s != TRIOSEQ_OK ? s : cuda_status(cudaGetLastError());
-          break;
-        }
-        if (ms < best) {
-          best = ms;
-          bestv = trioseq_plan_s::Tuned{v, ti};
-        }
+        if (result != TRIOSEQ_OK) break;
       }
-      if (result != TRIOSEQ_OK) break;
+      plan->tuning = false;
     }
-    plan->tuning = false;
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  if (result != TRIOSEQ_OK) return result;
-  plan->tuned[tune_key(mode, n, maxlen)] = bestv;
-  if (tile_j) *tile_j = bestv.var.nj;
-  if (tile_k) *tile_k = bestv.var.nk;
-  if (ti) *ti = bestv.TI;
-  return TRIOSEQ_OK;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (result != TRIOSEQ_OK) return result;
+    plan->tuned[tune_key(mode, n, maxlen)] = bestv;
+    if (tile_j) *tile_j = bestv.var.nj;
+    if (tile_k) *tile_k = bestv.var.nk;
+    if (ti) *ti = bestv.TI;
+    return TRIOSEQ_OK;
+  });
 }
 
 trioseq_status trioseq_plan_io_bytes(trioseq_plan_t plan, uint64_t* h2d, uint64_t* d2h) {
-  if (!plan || !plan->last) return TRIOSEQ_EINVAL;
-  if (h2d) *h2d = plan->last->h2d_bytes;
-  if (d2h) *d2h = plan->last->d2h_bytes;
-  return TRIOSEQ_OK;
+  return no_throw([&]() -> trioseq_status {
+    if (!plan || !plan->last) return TRIOSEQ_EINVAL;
+    if (h2d) *h2d = plan->last->h2d_bytes;
+    if (d2h) *d2h = plan->last->d2h_bytes;
+    return TRIOSEQ_OK;
+  });
 }
 
 trioseq_status trioseq_batch_destroy(trioseq_batch_t bt) {
-  if (!bt) return TRIOSEQ_OK;
-  DeviceGuard g(bt->plan->device);
-  cudaDeviceSynchronize();
-  delete bt;
-  return TRIOSEQ_OK;
+  return no_throw([&]() -> trioseq_status {
+    if (!bt) return TRIOSEQ_OK;
+    DeviceGuard g(bt->plan->device);
+    cudaDeviceSynchronize();
+    delete bt;
+    return TRIOSEQ_OK;
+  });
 }
 
 }  // extern "C"
@@ -1385,10 +1424,17 @@ void srv_harvest(trioseq_server_s* S, SrvSlot& sl) {
         const uint8_t* base =
             reinterpret_cast<const uint8_t*>(h + sl.off_rows + (size_t)bt->row_off[q]);
         r.has_rows = true;
-        for (int s = 0; s < 3; s++) {
-          r.rows[s].resize((size_t)L);
-          const uint8_t* row = base + (size_t)s * rc + (rc - L);
-          for (int32_t t = 0; t < L; t++) r.rows[s][t] = row[t] == 255 ? '-' : alpha[row[t]];
+        r.st = no_throw([&] {
+          for (int s = 0; s < 3; s++) {
+            r.rows[s].resize((size_t)L);
+            const uint8_t* row = base + (size_t)s * rc + (rc - L);
+            for (int32_t t = 0; t < L; t++) r.rows[s][t] = row[t] == 255 ? '-' : alpha[row[t]];
+          }
+          return TRIOSEQ_OK;
+        });
+        if (r.st != TRIOSEQ_OK) {
+          r.has_rows = false;
+          for (auto& x : r.rows) std::string().swap(x);
         }
       }
     }
@@ -1445,7 +1491,7 @@ void srv_loop(trioseq_server_s* S) {
         continue;
       }
       lk.unlock();
-      sl.launch_st = srv_launch(S, sl);
+      sl.launch_st = no_throw([&] { return srv_launch(S, sl); });  // the thread must not throw
       lk.lock();
       busy_any = true;
     }
@@ -1460,115 +1506,123 @@ extern "C" {
 
 trioseq_status trioseq_server_create(const trioseq_plan_t* plans, int32_t nplans,
                                      size_t hbm_budget, trioseq_server_t* out) {
-  if (!out) return TRIOSEQ_EINVAL;
-  *out = nullptr;
-  if (!plans || nplans < 1) return TRIOSEQ_EINVAL;
-  for (int32_t i = 0; i < nplans; i++)
-    if (!plans[i] || plans[i]->device != plans[0]->device) return TRIOSEQ_EINVAL;
-  std::unique_ptr<trioseq_server_s> S(new (std::nothrow) trioseq_server_s());
-  if (!S) return TRIOSEQ_ENOMEM;
-  S->plans.assign(plans, plans + nplans);
-  S->device = plans[0]->device;
-  DeviceGuard g(S->device);
-  if (hbm_budget == 0) {
-    size_t fr = 0, tot = 0;
-    if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return cuda_status(cudaGetLastError());
-    hbm_budget = fr / 10 * 8;
-  }
-  S->slot_budget = std::max<size_t>(hbm_budget / trioseq_server_s::kSlots, 1 << 20);
-  S->max_pending = (size_t)std::max(0, env_int("TRIOSEQ_SERVER_MAX_PENDING", 1 << 20));
-  for (auto& sl : S->slots) {
-    if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess)
-      return cuda_status(cudaGetLastError());
-    sl.ws.alloc_stream = sl.stream;
-  }
-  try {
-    S->th = std::thread(srv_loop, S.get());
-  } catch (...) {
-    return TRIOSEQ_ENOMEM;
-  }
-  *out = S.release();
-  return TRIOSEQ_OK;
+  return no_throw([&]() -> trioseq_status {
+    if (!out) return TRIOSEQ_EINVAL;
+    *out = nullptr;
+    if (!plans || nplans < 1) return TRIOSEQ_EINVAL;
+    for (int32_t i = 0; i < nplans; i++)
+      if (!plans[i] || plans[i]->device != plans[0]->device) return TRIOSEQ_EINVAL;
+    std::unique_ptr<trioseq_server_s> S(new (std::nothrow) trioseq_server_s());
+    if (!S) return TRIOSEQ_ENOMEM;
+    S->plans.assign(plans, plans + nplans);
+    S->device = plans[0]->device;
+    DeviceGuard g(S->device);
+    if (hbm_budget == 0) {
+      size_t fr = 0, tot = 0;
+      if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return cuda_status(cudaGetLastError());
+      hbm_budget = fr / 10 * 8;
+    }
+    S->slot_budget = std::max<size_t>(hbm_budget / trioseq_server_s::kSlots, 1 << 20);
+    S->max_pending = (size_t)std::max(0, env_int("TRIOSEQ_SERVER_MAX_PENDING", 1 << 20));
+    for (auto& sl : S->slots) {
+      if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) != cudaSuccess)
+        return cuda_status(cudaGetLastError());
+      sl.ws.alloc_stream = sl.stream;
+    }
+    try {
+      S->th = std::thread(srv_loop, S.get());
+    } catch (...) {
+      return TRIOSEQ_ENOMEM;
+    }
+    *out = S.release();
+    return TRIOSEQ_OK;
+  });
 }
 
 trioseq_status trioseq_submit(trioseq_server_t S, const trioseq_triplet* t, int32_t plan_id,
                               uint32_t mode, uint64_t* ticket) {
-  if (!S || !t || !ticket || plan_id < 0 || plan_id >= (int32_t)S->plans.size() ||
-      mode > TRIOSEQ_WITH_TRACEBACK)
-    return TRIOSEQ_EINVAL;
-  const trioseq_plan_s* plan = S->plans[plan_id];
-  SrvReq r;
-  r.plan_id = plan_id;
-  r.mode = mode;
-  int64_t sumlen = 0;
-  for (int q = 0; q < 3; q++) {
-    if (t->len[q] && !t->s[q]) return TRIOSEQ_EINVAL;
-    if (t->len[q] > (1u << 24)) return TRIOSEQ_EOVERFLOW;
-    const unsigned char* src = reinterpret_cast<const unsigned char*>(t->s[q]);
-    for (uint32_t e = 0; e < t->len[q]; e++)
-      if (plan->lut[src[e]] < 0) return TRIOSEQ_EINVAL;
-    r.s[q].assign(t->s[q] ? t->s[q] : "", t->len[q]);
-    sumlen += t->len[q];
-  }
-  if ((int64_t)std::max(plan->max_abs_sig2, plan->atype != kGlobal ? -2 * plan->gap : 0) *
-          sumlen >= (1LL << 26) - 1)
-    return TRIOSEQ_EOVERFLOW;
-  r.bytes = request_bytes(plan, mode, t->len);
-  {
-    std::lock_guard<std::mutex> lk(S->mu);
-    if (S->stop) return TRIOSEQ_EINVAL;
-    if (S->pending.size() >= S->max_pending) return TRIOSEQ_EAGAIN;
-    r.ticket = S->next_ticket++;
-    *ticket = r.ticket;
-    S->live[r.ticket] = 0;
-    S->pending.push_back(std::move(r));
-  }
-  S->cv.notify_one();
-  return TRIOSEQ_OK;
+  return no_throw([&]() -> trioseq_status {
+    if (!S || !t || !ticket || plan_id < 0 || plan_id >= (int32_t)S->plans.size() ||
+        mode > TRIOSEQ_WITH_TRACEBACK)
+      return TRIOSEQ_EINVAL;
+    const trioseq_plan_s* plan = S->plans[plan_id];
+    SrvReq r;
+    r.plan_id = plan_id;
+    r.mode = mode;
+    int64_t sumlen = 0;
+    for (int q = 0; q < 3; q++) {
+      if (t->len[q] && !t->s[q]) return TRIOSEQ_EINVAL;
+      if (t->len[q] > (1u << 24)) return TRIOSEQ_EOVERFLOW;
+      const unsigned char* src = reinterpret_cast<const unsigned char*>(t->s[q]);
+      for (uint32_t e = 0; e < t->len[q]; e++)
+        if (plan->lut[src[e]] < 0) return TRIOSEQ_EINVAL;
+      r.s[q].assign(t->s[q] ? t->s[q] : "", t->len[q]);
+      sumlen += t->len[q];
+    }
+    if ((int64_t)std::max(plan->max_abs_sig2, plan->atype != kGlobal ? -2 * plan->gap : 0) *
+            sumlen >= (1LL << 26) - 1)
+      return TRIOSEQ_EOVERFLOW;
+    r.bytes = request_bytes(plan, mode, t->len);
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      if (S->stop) return TRIOSEQ_EINVAL;
+      if (S->pending.size() >= S->max_pending) return TRIOSEQ_EAGAIN;
+      r.ticket = S->next_ticket++;
+      *ticket = r.ticket;
+      S->live[r.ticket] = 0;
+      S->pending.push_back(std::move(r));
+    }
+    S->cv.notify_one();
+    return TRIOSEQ_OK;
+  });
 }
 
 trioseq_status trioseq_poll(trioseq_server_t S, uint64_t ticket, int32_t* score, char* rows[3],
                             size_t cap, size_t* aln_len) {
-  if (!S) return TRIOSEQ_EINVAL;
-  std::lock_guard<std::mutex> lk(S->mu);
-  auto it = S->done.find(ticket);
-  if (it == S->done.end()) return S->live.count(ticket) ? TRIOSEQ_EAGAIN : TRIOSEQ_EINVAL;
-  SrvRes& r = it->second;
-  if (r.st == TRIOSEQ_OK && r.has_rows) {
-    if (aln_len) *aln_len = r.rows[0].size();
-    if (rows) {
-      if (cap < r.rows[0].size() || !rows[0] || !rows[1] || !rows[2]) return TRIOSEQ_EINVAL;
-      for (int s = 0; s < 3; s++) std::memcpy(rows[s], r.rows[s].data(), r.rows[s].size());
+  return no_throw([&]() -> trioseq_status {
+    if (!S) return TRIOSEQ_EINVAL;
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->done.find(ticket);
+    if (it == S->done.end()) return S->live.count(ticket) ? TRIOSEQ_EAGAIN : TRIOSEQ_EINVAL;
+    SrvRes& r = it->second;
+    if (r.st == TRIOSEQ_OK && r.has_rows) {
+      if (aln_len) *aln_len = r.rows[0].size();
+      if (rows) {
+        if (cap < r.rows[0].size() || !rows[0] || !rows[1] || !rows[2]) return TRIOSEQ_EINVAL;
+        for (int s = 0; s < 3; s++) std::memcpy(rows[s], r.rows[s].data(), r.rows[s].size());
+      }
+    } else if (aln_len) {
+      *aln_len = 0;
     }
-  } else if (aln_len) {
-    *aln_len = 0;
-  }
-  if (score) *score = r.score;
-  const trioseq_status st = r.st;
-  S->done.erase(it);
-  S->live.erase(ticket);
-  return st;
+    if (score) *score = r.score;
+    const trioseq_status st = r.st;
+    S->done.erase(it);
+    S->live.erase(ticket);
+    return st;
+  });
 }
 
 trioseq_status trioseq_server_destroy(trioseq_server_t S) {
-  if (!S) return TRIOSEQ_OK;
-  {
-    std::lock_guard<std::mutex> lk(S->mu);
-    S->stop = true;
-  }
-  S->cv.notify_all();
-  if (S->th.joinable()) S->th.join();
-  {
-    DeviceGuard g(S->device);
-    for (auto& sl : S->slots) {
-      if (sl.stream) cudaStreamSynchronize(sl.stream);
-      if (sl.done) cudaEventDestroy(sl.done);
-      if (sl.stream) cudaStreamDestroy(sl.stream);
+  return no_throw([&]() -> trioseq_status {
+    if (!S) return TRIOSEQ_OK;
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      S->stop = true;
     }
-  }
-  delete S;
-  return TRIOSEQ_OK;
+    S->cv.notify_all();
+    if (S->th.joinable()) S->th.join();
+    {
+      DeviceGuard g(S->device);
+      for (auto& sl : S->slots) {
+        if (sl.stream) cudaStreamSynchronize(sl.stream);
+        if (sl.done) cudaEventDestroy(sl.done);
+        if (sl.stream) cudaStreamDestroy(sl.stream);
+      }
+    }
+    delete S;
+    return TRIOSEQ_OK;
+  });
 }
 
 }  // extern "C"
