@@ -179,13 +179,17 @@ def kernel_source_hash(tile: str) -> str:
 
 
 def global_workload(key: str, world: int):
-    """The whole job's batch when a multi-triplet workload runs on `world` ranks: `world` times
-    the single-GPU batch (same recipe and seed), so each rank's share stays about the same size
-    (weak scaling). None for single-triplet workloads, which run as replicas."""
+    """The whole job's batch and its description when a multi-triplet workload runs on `world`
+    ranks: `world` times the single-GPU batch (same recipe and seed), so each rank's share stays
+    about the same size (weak scaling). (None, None) for single-triplet workloads, which run as
+    replicas."""
     from paper_2605_28400_gb300 import synth
     if key == "batch4096":
-        return synth.config2(n=4096 * world)
-    return None
+        n = 4096 * world
+        return synth.config2(n=n), (f"{n} related DNA triplets, ancestor lengths U[100,300], "
+                                    f"score only, sharded over {world} ranks, one persistent "
+                                    "launch per rank")
+    return None, None
 
 
 def shard_workload(w, world: int, rank: int, B):
@@ -723,8 +727,9 @@ def main():
     from paper_2605_28400_gb300 import binding as B
     B.load()
     make, desc = workloads()[args.workload]
-    wg = global_workload(args.workload, world) if world > 1 else None
+    wg, gdesc = global_workload(args.workload, world) if world > 1 else (None, None)
     if wg is not None:  # a batch: shard its triplets over the ranks (Sec. V-D)
+        desc = gdesc
         w, rank_cells = shard_workload(wg, world, rank, B)
         cells_total = wg.cells
         parallelism = (f"dp{world}: triplets sharded by the dynamic partition (Sec. V-D), "

@@ -178,3 +178,20 @@ def test_all_core_oracle_replay_of_the_serving_mix():
     got = bench.cpu_all_cores_mix(reqs, dna, prot, target_s=0.05)
     assert got["kind"] == "oracle" and got["value"] > 0 and got["cores"] >= 1
     assert "requests of the mix" in got["sample"]
+
+
+def test_global_batch_extends_the_single_gpu_batch():
+    """At N ranks the batch workload is N x 4096 triplets of the same recipe and seed; the
+    generator is counter-based per triplet, so the first 4096 are the single-GPU batch."""
+    import numpy as np
+
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2605_28400_gb300 import synth
+
+    wg, desc = bench.global_workload("batch4096", 2)
+    one = synth.config2()
+    assert len(wg.triplets) == 8192 and desc.startswith("8192 related DNA triplets")
+    for t in (0, 1, 2047, 4095):
+        assert all(np.array_equal(x, y) for x, y in zip(wg.triplets[t], one.triplets[t]))
+    assert bench.global_workload("protein4000", 2) == (None, None)
