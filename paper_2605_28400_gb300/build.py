@@ -72,19 +72,22 @@ def build(force: bool = False, verbose: bool = False) -> str:
                 sys.stderr.write(r.stderr)
             return obj
 
-        with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
-            objs = list(ex.map(comp, SOURCES))
+        every = [os.path.join(LIBDIR, src.replace(".cu", f".{tag}.o")) for src in SOURCES]
         tmp = LIB + f".{tag}.tmp"
-        cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs
-        r = subprocess.run(cmd, capture_output=True, text=True)
-        for o in objs:
-            try:
-                os.remove(o)
-            except OSError:
-                pass
-        if r.returncode != 0:
-            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
+        try:
+            with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+                objs = list(ex.map(comp, SOURCES))
+            cmd = [cc] + ARCH + ["-shared", "-o", tmp] + objs
+            r = subprocess.run(cmd, capture_output=True, text=True)
+            if r.returncode != 0:
+                raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+            os.replace(tmp, LIB)
+        finally:  # no objects or partial library left behind, whether or not the build worked
+            for f in every + [tmp]:
+                try:
+                    os.remove(f)
+                except OSError:
+                    pass
         return LIB
 
 
