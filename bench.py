@@ -242,8 +242,9 @@ def triplet_strings(w):
 
 # ------------------------------------------------------------------------------------------
 def host_cpu() -> dict:
-    """CPU model, logical core count and clock (lscpu's max MHz, and the current MHz of CPU 0 from
-    cpufreq where the kernel exposes it) of the host running the oracle."""
+    """CPU model, logical core count and clock of the host running the oracle: the max MHz from
+    lscpu, else cpufreq, else ACPI CPPC (nominal clock x highest / nominal performance); the
+    current MHz of CPU 0 from cpufreq and the CPPC nominal MHz where the kernel exposes them."""
     model, max_mhz, cur_mhz = "", None, None
     try:  # lscpu names Arm cores (Neoverse-V2 on Grace); /proc/cpuinfo there does not
         out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
@@ -270,6 +271,18 @@ def host_cpu() -> dict:
                 max_mhz = int(fh.read().strip()) / 1000.0
         except (OSError, ValueError):
             pass
+    nominal_mhz = None
+    cppc = "/sys/devices/system/cpu/cpu0/acpi_cppc/"
+    try:  # Arm servers without cpufreq: ACPI CPPC gives the nominal clock and the perf range
+        with open(cppc + "nominal_freq") as fh:
+            nominal_mhz = float(fh.read().strip())
+        if max_mhz is None:
+            with open(cppc + "highest_perf") as fh, open(cppc + "nominal_perf") as gh:
+                hi, nom = float(fh.read().strip()), float(gh.read().strip())
+            if nom > 0:
+                max_mhz = nominal_mhz * hi / nom
+    except (OSError, ValueError):
+        pass
     try:
         with open("/proc/cpuinfo") as fh:
             for line in fh:
@@ -281,7 +294,8 @@ def host_cpu() -> dict:
     if not model:
         import platform
         model = platform.processor() or platform.machine()
-    return {"cpu": model, "nproc": os.cpu_count(), "max_mhz": max_mhz, "cur_mhz": cur_mhz}
+    return {"cpu": model, "nproc": os.cpu_count(), "max_mhz": max_mhz, "cur_mhz": cur_mhz,
+            "nominal_mhz": nominal_mhz}
 
 
 def cpu_all_cores_sample(triplets, sc, target_s: float = 3.0):
