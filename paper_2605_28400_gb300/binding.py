@@ -7,6 +7,7 @@ no CPU fallback.
 from __future__ import annotations
 
 import ctypes
+import itertools
 import os
 
 import numpy as np
@@ -171,30 +172,31 @@ _TRIPLET_DTYPE = np.dtype({"names": ["s", "len"], "formats": [("<u8", 3), ("<u4"
 
 
 def _triplet_array(triplets):
-    """Triplet records (as a ctypes pointer) plus the buffers keeping the strings alive.
+    """Triplet records (as a ctypes pointer) plus the objects keeping the strings alive.
 
-    All sequences are joined into one buffer and the records are filled with numpy, so
-    marshalling thousands of triplets costs one copy of the residues rather than one Python
-    call per field."""
+    All sequences are joined into one bytes object and the records, filled with numpy, point
+    into it, so marshalling thousands of triplets costs one copy of the residues rather than one
+    Python call per field. The library only reads the strings (it copies them before returning)."""
     n = len(triplets)
     if any(len(t) != 3 for t in triplets):
         raise ValueError("a triplet has three sequences")
-    flat = [t[q] for t in triplets for q in range(3)]
-    if all(isinstance(x, str) for x in flat):
+    flat = list(itertools.chain.from_iterable(triplets))
+    try:  # all str (the common case): one join, one byte per character, as residues are
+        joined = "".join(flat).encode("latin-1")
         lens = np.fromiter(map(len, flat), dtype=np.uint32, count=3 * n)
-        joined = "".join(flat).encode("latin-1")  # one byte per character, as residues are
-    else:
+    except TypeError:  # bytes or code arrays among them
         parts = [_as_bytes(x) for x in flat]
         lens = np.fromiter(map(len, parts), dtype=np.uint32, count=3 * n)
         joined = b"".join(parts)
-    buf = ctypes.create_string_buffer(joined, max(1, len(joined)))
+    base = ctypes.c_char_p(joined)  # points into the bytes object, which `keep` holds alive
     offs = np.zeros(3 * n, dtype=np.uint64)
     if n:
         offs[1:] = np.cumsum(lens[:-1], dtype=np.uint64)
     rec = np.zeros(max(1, n), dtype=_TRIPLET_DTYPE)
-    rec["s"][:n] = (np.uint64(ctypes.addressof(buf)) + offs).reshape(n, 3)
+    addr = ctypes.cast(base, ctypes.c_void_p).value or 0
+    rec["s"][:n] = (np.uint64(addr) + offs).reshape(n, 3)
     rec["len"][:n] = lens.reshape(n, 3)
-    return rec.ctypes.data_as(ctypes.POINTER(Triplet)), (buf, rec)
+    return rec.ctypes.data_as(ctypes.POINTER(Triplet)), (joined, base, rec)
 
 
 def trioseq_plan(alphabet: str, sub, gap: int, flags: int = 0):

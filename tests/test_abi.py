@@ -60,3 +60,31 @@ def test_host_allocation_failure_returns_enomem_without_a_gpu():
                        text=True, timeout=120)
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == "out of memory"
+
+
+def test_triplet_marshalling_points_at_every_sequence():
+    """The binding's triplet records (one joined buffer, no per-field Python calls) hold, for
+    every sequence, a pointer and length that read back the exact input: str, bytes and code
+    arrays, empty sequences and an empty batch."""
+    import numpy as np
+
+    trips = [("ACGT", "", "GGA"), (b"AC", b"T", b""), ("A" * 1000, "C", "G" * 7),
+             (np.array([65, 67], dtype=np.uint8), "TT", b"G")]
+    class Raw(ctypes.Structure):  # the record layout with the pointers as plain addresses
+        _fields_ = [("s", ctypes.c_void_p * 3), ("len", ctypes.c_uint32 * 3)]
+
+    assert ctypes.sizeof(Raw) == ctypes.sizeof(binding.Triplet)
+    for batch in (trips[:1], trips, [trips[0]] * 3, []):
+        ptr, keep = binding._triplet_array(batch)
+        raw = ctypes.cast(ptr, ctypes.POINTER(Raw))
+        for t, want in enumerate(batch):
+            for q in range(3):
+                assert raw[t].s[q]  # never null, even for an empty sequence
+                got = ctypes.string_at(raw[t].s[q], raw[t].len[q])
+                assert got == binding._as_bytes(want[q])
+    try:
+        binding._triplet_array([("A", "C")])
+    except ValueError:
+        pass
+    else:
+        raise AssertionError("a two-sequence triplet was accepted")
