@@ -40,13 +40,19 @@ struct NoallocLayout {
 
 __host__ __device__ inline size_t up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-NoallocLayout layout_for(int a, int b, int c, int KP) {
+// Workspace layout of one call, sized in 64-bit arithmetic: the task count nJ * nK of a long,
+// thin triplet can exceed 2^31 even though each length is at most 2^24. Returns false when the
+// task count or any size does not fit (the caller then reports TRIOSEQ_ESCRATCH); the layout's
+// int fields are set only when it fits.
+bool layout_for(int64_t a, int64_t b, int64_t c, int KP, NoallocLayout* out) {
   NoallocLayout L{};
-  const int WJ = kPR * kNoallocNJ, WK = kPC * kNoallocNK;
-  L.nJ = (b + 1 + WJ - 1) / WJ;
-  L.nK = (c + 1 + WK - 1) / WK;
-  L.T = a + 1 + (kPR - 1) + (kPC - 1);
-  L.ntasks = L.nJ * L.nK;
+  const int64_t WJ = kPR * kNoallocNJ, WK = kPC * kNoallocNK;
+  const int64_t nJ = (b + 1 + WJ - 1) / WJ, nK = (c + 1 + WK - 1) / WK;
+  const int64_t ntasks = nJ * nK;  // < 2^38 for lengths <= 2^24: no 64-bit overflow
+  // Every task holds (a + 1) slices of records, at least one int32 each: a task count beyond
+  // the array's int32 capacity can never fit, and rejecting it first keeps the products below
+  // (ntasks * (a + 1) * record width) far from 64-bit overflow.
+  if (ntasks > (int64_t)(kScratchBytes / sizeof(int32_t))) return false;
   size_t off = 0;
   L.off_seq = off;
   off = up(off + up((size_t)a, 16) + up((size_t)b, 16) + up((size_t)c, 16) + 16, 256);
@@ -55,13 +61,19 @@ NoallocLayout layout_for(int a, int b, int c, int KP) {
   L.off_desc = off;
   off = up(off + sizeof(TripDesc), 256);
   L.off_tasks = off;
-  off = up(off + sizeof(Task) * (size_t)L.ntasks, 256);
+  off = up(off + sizeof(Task) * (size_t)ntasks, 256);
   L.off_prog = off;
-  off = up(off + sizeof(int32_t) * ((size_t)L.ntasks + 64), 256);
+  off = up(off + sizeof(int32_t) * ((size_t)ntasks + 64), 256);
   L.off_faces = off;
-  off += sizeof(int32_t) * (size_t)L.ntasks * (size_t)(a + 1) * (size_t)((WK + 4) + WJ);
+  off += sizeof(int32_t) * (size_t)ntasks * (size_t)(a + 1) * (size_t)((WK + 4) + WJ);
   L.total = up(off, 256);
-  return L;
+  if (L.total > kScratchBytes) return false;
+  L.nJ = (int)nJ;
+  L.nK = (int)nK;
+  L.T = (int)(a + 1 + (kPR - 1) + (kPC - 1));
+  L.ntasks = (int)ntasks;
+  *out = L;
+  return true;
 }
 
 // Set-up of one call (after the progress flags, queue head and error word were cleared on the
@@ -164,8 +176,8 @@ extern "C" trioseq_status trioseq_align_noalloc(const trioseq_scoring* sc,
   const int64_t sumlen = (int64_t)a + b + c;
   if (a > (1u << 24) || b > (1u << 24) || c > (1u << 24)) return TRIOSEQ_ESCRATCH;
   if ((int64_t)mx * sumlen >= (1LL << 26) - 1) return TRIOSEQ_EOVERFLOW;
-  const NoallocLayout L = layout_for((int)a, (int)b, (int)c, KP);
-  if (L.total > kScratchBytes) return TRIOSEQ_ESCRATCH;
+  NoallocLayout L{};
+  if (!layout_for(a, b, c, KP, &L)) return TRIOSEQ_ESCRATCH;
 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {

@@ -88,3 +88,20 @@ def test_triplet_marshalling_points_at_every_sequence():
         pass
     else:
         raise AssertionError("a two-sequence triplet was accepted")
+
+
+def test_noalloc_rejects_a_task_grid_beyond_int32_before_any_device_call():
+    """The allocation-free entry point sizes its workspace in 64-bit arithmetic. A long, thin
+    triplet whose task grid nJ * nK (65536 * 65537 with the 8x8 tile) exceeds 2^31 passes the
+    length and score-range checks, and must be rejected with TRIOSEQ_ESCRATCH before any device
+    access: the dummy non-null addresses below are never dereferenced, and no GPU is needed."""
+    import numpy as np
+
+    sub = np.array([[2 if i == j else -1 for j in range(4)] for i in range(4)], dtype=np.int8)
+    dummy = 0x1000
+    for a, b, c in ((0, 2097151, 4194367), (0, 4194367, 2097151), (1, 1 << 24, 1 << 24)):
+        st = binding.trioseq_align_noalloc("ACGT", sub, -2, dummy if a else 0, a,
+                                           dummy, b, dummy, c, dummy)
+        assert st in (binding.ESCRATCH, binding.EOVERFLOW), (a, b, c, st)
+    st = binding.trioseq_align_noalloc("ACGT", sub, -2, 0, 0, dummy, 2097151, dummy, 4194367, dummy)
+    assert st == binding.ESCRATCH
