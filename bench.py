@@ -240,6 +240,44 @@ def triplet_strings(w):
     return [[synth.to_str(s, w.scoring.alphabet) for s in t] for t in w.triplets]
 
 
+def oracle_golden(key: str, w):
+    """Stored oracle scores (and alignment digests) of a full-size workload, written by
+    tests/golden/make_goldens.py from the oracle alone, or None when none is stored for it or
+    the stored inputs' digest differs from this workload's inputs."""
+    from tests.golden import goldens
+    loaders = {"protein4000": goldens.load_config3, "batch4096": goldens.load_config2,
+               "dna1000": goldens.load_config1, "dna128": goldens.load_config0}
+    if key not in loaders:
+        return None
+    try:
+        meta, want = loaders[key]()
+    except (OSError, ValueError, AssertionError):
+        return None
+    if meta.get("input_sha256") != goldens.input_digest(w.triplets):
+        return None
+    return want
+
+
+def check_golden(key: str, w, scores, rows=None):
+    """True when the scores (and the rows of a one-triplet traceback workload) equal the stored
+    oracle values, None when none are stored. A mismatch stops the benchmark: a number measured
+    on wrong results is not reported."""
+    from tests.golden import goldens
+    want = oracle_golden(key, w)
+    if want is None:
+        return None
+    if isinstance(want, dict):  # one triplet with its alignment
+        ok = [int(x) for x in scores] == [want["score"]]
+        if rows is not None:
+            ok &= goldens.rows_digest(rows) == want["rows_sha256"]
+    elif hasattr(want, "__len__"):
+        ok = [int(x) for x in scores] == [int(x) for x in want]
+    else:
+        ok = [int(x) for x in scores] == [int(want)]
+    assert ok, f"{key}: results differ from the stored oracle values"
+    return True
+
+
 # ------------------------------------------------------------------------------------------
 def host_cpu() -> dict:
     """CPU model, logical core count and clock of the host running the oracle: the max MHz from
@@ -295,7 +333,53 @@ def host_cpu() -> dict:
         import platform
         model = platform.processor() or platform.machine()
     return {"cpu": model, "nproc": os.cpu_count(), "max_mhz": max_mhz, "cur_mhz": cur_mhz,
-            "nominal_mhz": nominal_mhz}
+            "nominal_mhz": nominal_mhz, "measured_mhz": measured_host_mhz(),
+            "measured_mhz_method": "one host thread: a dependent chain of n (add, xor) pairs, "
+                                   "2 cycles per pair (1-cycle integer add and xor latency on "
+                                   "x86-64 and Neoverse cores), 2n / wall time, best of 5"}
+
+
+_CLOCK_C = r"""
+#include <stdint.h>
+uint64_t trioseq_clock_chain(uint64_t n, uint64_t x, uint64_t y) {
+  for (uint64_t i = 0; i < n; i++) { x += y; y ^= x; }
+  return x ^ y;
+}
+"""
+_host_mhz = None
+
+
+def measured_host_mhz():
+    """Clock of the host core running the oracle, measured: gcc builds a loop whose iterations
+    are one dependent integer add and xor (2 cycles at 1-cycle latency each; the loop counter
+    runs beside them), and the clock is 2n cycles over the wall time. Used where the kernel
+    exposes no frequency (no cpufreq, no CPPC nominal clock). None if gcc is missing."""
+    global _host_mhz
+    if _host_mhz is not None:
+        return _host_mhz
+    import ctypes
+    import shutil
+    import tempfile
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if not cc:
+        return None
+    with tempfile.TemporaryDirectory() as d:
+        src, lib = os.path.join(d, "clk.c"), os.path.join(d, "clk.so")
+        with open(src, "w") as fh:
+            fh.write(_CLOCK_C)
+        if subprocess.run([cc, "-O2", "-shared", "-fPIC", src, "-o", lib],
+                          capture_output=True).returncode != 0:
+            return None
+        fn = ctypes.CDLL(lib).trioseq_clock_chain
+        fn.restype = ctypes.c_uint64
+        fn.argtypes = [ctypes.c_uint64] * 3
+        n, best = 100_000_000, 0.0
+        for _ in range(5):
+            t = time.perf_counter()
+            fn(n, 1, 2)
+            best = max(best, 2 * n / (time.perf_counter() - t) / 1e6)
+    _host_mhz = round(best, 1)
+    return _host_mhz
 
 
 def cpu_all_cores_sample(triplets, sc, target_s: float = 3.0):
@@ -458,6 +542,27 @@ def _serve(B, srv, reqs, strs, rate, cap):
     return t_sub, t_done, results, tickets
 
 
+def serving_golden(reqs, results):
+    """Served results of the stream's first requests against the stored oracle values (scores,
+    and the alignment digests of traceback requests): the number of requests checked, or None
+    when no values are stored for these inputs. A mismatch stops the benchmark."""
+    from tests.golden import goldens
+    try:
+        meta, want = goldens.load_config4()
+    except (OSError, ValueError, AssertionError):
+        return None
+    n = len(want)
+    if len(reqs) < n or meta.get("input_sha256") != goldens.input_digest(
+            [r["triplet"] for r in reqs[:n]]):
+        return None
+    for wnt, (score, rows) in zip(want, results[:n]):
+        assert score == wnt["score"], f"served request {wnt['id']}: score differs from the oracle"
+        if wnt["traceback"]:
+            assert goldens.rows_digest(rows) == wnt["rows_sha256"], \
+                f"served request {wnt['id']}: alignment differs from the oracle"
+    return {"requests_checked": n, "equal": True}
+
+
 def cpu_all_cores_mix(reqs, dna, prot, target_s: float = 3.0):
     """The oracle on every host core over the serving mix, replayed in arrival order: a prefix of
     the requests sized for about target_s seconds, each scoring scheme's requests as one
@@ -487,7 +592,7 @@ def cpu_all_cores_mix(reqs, dna, prot, target_s: float = 3.0):
             "host": host_cpu()}
 
 
-def serving_measurement(B, n_req: int = 2000, load: float = 0.7, n_cal: int = 600,
+def serving_measurement(B, n_req: int = 10000, load: float = 0.7, n_cal: int = 600,
                         cpu_legs: bool = True):
     """Serving stream: mixed DNA/protein requests (20% traceback). The server's capacity on this
     mix is measured first with a closed-loop burst (n_cal requests submitted at once); the stream
@@ -525,7 +630,9 @@ def serving_measurement(B, n_req: int = 2000, load: float = 0.7, n_cal: int = 60
             same &= rows == B.trioseq_traceback(pl, 0)
     for p in plans:
         B.trioseq_plan_destroy(p)
+    golden = serving_golden(reqs, [results[tickets[i]] for i in range(len(reqs))])
     return {"requests": len(reqs), "arrival_rate_per_s": rate,
+            "equals_oracle_on_stored_prefix": golden,
             "server_capacity_gcups": capacity, "capacity_burst_requests": n_cal,
             "load_vs_server_capacity": load,
             "mean_cells_per_request": mean_cells, "p50_ms": lat[len(lat) // 2],
@@ -545,7 +652,7 @@ def aux_measurements(B, torch, stream, flush, sms, clock_mhz, skip: str, cpu_leg
     stream (p50/p99 latency)."""
     from paper_2605_28400_gb300 import synth
     out = {}
-    for key in ("dna1000", "protein4000"):
+    for key in ("dna1000", "protein4000", "dna128"):
         if key == skip:
             continue
         make, desc = workloads()[key]
@@ -573,15 +680,44 @@ def aux_measurements(B, torch, stream, flush, sms, clock_mhz, skip: str, cpu_leg
         if w.traceback:
             entry["walk_ms"] = statistics.mean(wk)
             entry["roofline"]["code_stream_gbs"] = CODE_BYTES_PER_CELL * w.cells / kmean / 1e6
+        entry["equals_oracle"] = check_golden(
+            key, w, sc, B.trioseq_batch_alignment(bt, 0) if w.traceback else None)
         out[key] = entry
         B.trioseq_batch_destroy(bt)
         B.trioseq_plan_destroy(plan)
 
-    # Semi-global and local types (Sec. II) on the n=4000 protein triplet, score only. Local adds
-    # the v = 0 candidate and the running best per cell: 15 algorithmic int32 ops instead of 13.
+    # The n=4000 protein triplet on the int32 8x8 kernel (one cell per register lane), the
+    # kernel the two-cells-per-register one is measured against; interval 16, its best there.
     w = synth.config3()
-    for flags, name, ops in ((B.SEMIGLOBAL, "semiglobal", OPS_PER_CELL),
-                             (B.LOCAL, "local", OPS_PER_CELL + 2)):
+    os.environ["TRIOSEQ_SCORE_TILE"], os.environ["TRIOSEQ_TI"] = "8x8", "16"
+    try:
+        plan = B.trioseq_plan(w.scoring.alphabet, w.scoring.sub, w.scoring.gap)
+    finally:
+        os.environ.pop("TRIOSEQ_SCORE_TILE", None)
+        os.environ.pop("TRIOSEQ_TI", None)
+    bt = B.trioseq_batch_create(plan, triplet_strings(w), B.SCORE_ONLY)
+    binfo = B.trioseq_batch_info(bt)
+    assert binfo["packing"] == 1 and binfo["tile"] == (8, 8)
+    sm, km, _, sc = time_batch(B, torch, bt, 5, 3, stream, flush, 1)
+    kmean = statistics.mean(km)
+    ach = OPS_PER_CELL * w.cells / (kmean / 1e3) / 1e12
+    peak = sms * lanes * clock_mhz * 1e6 / 1e12
+    out["protein4000_int32_8x8"] = {
+        "workload": f"{w.name}: the main line's triplet on the int32 kernel (tile 8x8, interval 16)",
+        "gcups": w.cells / (statistics.mean(sm) / 1e3) / 1e9, "kernel_ms": kmean,
+        "score": int(sc[0]), "dtype": "int32", "equals_oracle": check_golden("protein4000", w, sc),
+        "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TOPS (int32)",
+                     "frac": ach / peak, "kernel": "wavefront_kernel<8,8>",
+                     "traffic": measured_traffic("protein4000", "8x8")}}
+    B.trioseq_batch_destroy(bt)
+    B.trioseq_plan_destroy(plan)
+
+    # Semi-global and local types (Sec. II) on the n=4000 protein triplet, score only. Both are
+    # counted at the metric's 13 algorithmic int32 ops per cell. Local also does the v = 0
+    # candidate and the running best per cell (15 ops): its fraction at 15 is reported beside.
+    w = synth.config3()
+    for flags, name, extra in ((B.SEMIGLOBAL, "semiglobal", 0), (B.LOCAL, "local", 2)):
+        ops = OPS_PER_CELL
         plan = B.trioseq_plan(w.scoring.alphabet, w.scoring.sub, w.scoring.gap, flags)
         tuned = B.trioseq_plan_autotune(plan, triplet_strings(w), B.SCORE_ONLY)
         bt = B.trioseq_batch_create(plan, triplet_strings(w), B.SCORE_ONLY)
@@ -595,6 +731,9 @@ def aux_measurements(B, torch, stream, flush, sms, clock_mhz, skip: str, cpu_leg
             "score": int(sc[0]), "tuned": tuned, "ops_per_cell": ops,
             "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TOPS (int32)",
                          "frac": ach / peak}}
+        if extra:
+            out[f"protein4000_{name}"]["roofline"]["frac_counting_type_ops"] = {
+                "ops_per_cell": ops + extra, "frac": (ops + extra) / ops * ach / peak}
         B.trioseq_batch_destroy(bt)
         B.trioseq_plan_destroy(plan)
 
@@ -633,6 +772,7 @@ def aux_measurements(B, torch, stream, flush, sms, clock_mhz, skip: str, cpu_leg
     B.trioseq_plan_destroy(plan)
     per_triplet = w.cells / (statistics.mean(reps) / 1e3) / 1e9
     out["batch4096_score_only"] = {
+        "equals_oracle": check_golden("batch4096", w, sc_batched),
         "batched_gcups": batched, "per_triplet_launch_gcups": per_triplet,
         "batched_over_per_triplet": batched / per_triplet, "identical_scores": bool(same),
         "tuned_batched": tuned_batch, "packing": packing, "kernel_ms": kb,
@@ -830,7 +970,12 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": ("int32" if packing == 1 else
+                      "int16x2 (two cells per 32-bit register, each a 16-bit value relative to "
+                      "a per-task base; exact by the range bound, boundary records int32)"
+                      if len(strs) == 1 else
+                      "int16x2 (two triplets per 32-bit register; exact by the range bound)"),
             "data": "synthetic",
             "config": {"workload": f"{(wg or w).name}: {desc}", "cells_per_step": cells_total,
                        "cells_per_rank": rank_cells,
@@ -846,7 +991,10 @@ def main():
                     "d2h_bytes_per_step": int(d2h), "ms_per_step": statistics.mean(e2e_ms)},
             "gpu_launches": world * args.steps * (2 if tb else 1),
             "clocks": clocks,
-            "score": int(scores[0])}
+            "score": int(scores[0]),
+            "equals_oracle": check_golden(args.workload, w, scores,
+                                          B.trioseq_batch_alignment(bt, 0) if tb and
+                                          len(strs) == 1 else None) if wg is None else None}
     B.trioseq_batch_destroy(bt)
     B.trioseq_plan_destroy(plan)
 

@@ -104,7 +104,10 @@ typedef struct trioseq_plan_s* trioseq_plan_t;
 trioseq_status trioseq_plan(const trioseq_scoring* scoring, uint32_t max_len_hint, uint32_t flags,
                             trioseq_plan_t* out);
 
-/* Release a plan and its device memory. Null is accepted. */
+/* Release a plan and its device memory. Null is accepted. Destroy the plan's device-resident
+ * batches and any server that names it first. The call waits for the plan's own last
+ * trioseq_align_batch work only; it synchronises no other stream (a running server's included),
+ * and the memory is freed in the order of the plan's private stream. */
 trioseq_status trioseq_plan_destroy(trioseq_plan_t plan);
 
 /* trioseq_align_batch — align n triplets (host strings) in one persistent launch.
@@ -202,6 +205,9 @@ trioseq_status trioseq_batch_packing(trioseq_batch_t batch, int32_t* per_word);
  * Scores and alignments are identical to the one-launch path. Errors: EINVAL (null). */
 trioseq_status trioseq_batch_slabs(trioseq_batch_t batch, int32_t* slices, int32_t* slabs);
 
+/* Release a device-resident batch. Null is accepted. The call waits for the batch's own last
+ * trioseq_batch_run (an event recorded on the stream that run was given) and synchronises no
+ * other stream; the batch's memory is freed in the order of its private stream. */
 trioseq_status trioseq_batch_destroy(trioseq_batch_t batch);
 
 /* trioseq_batch_profile — when enable != 0, each trioseq_batch_run records CUDA events on its
@@ -238,10 +244,17 @@ trioseq_status trioseq_plan_io_bytes(trioseq_plan_t plan, uint64_t* h2d, uint64_
 typedef struct trioseq_server_s* trioseq_server_t;
 
 /* trioseq_server_create — start a server thread that owns a pending queue and admits requests
- * by free device memory (`hbm_budget` bytes of workspace, 0 = 80% of free memory at creation)
- * and free slots, re-batching them each tick into launches on several CUDA streams so that work
- * of different requests overlaps on the device. plans[0..nplans) are the scoring schemes a
- * request may name by index (e.g. 0 = DNA, 1 = protein); they must outlive the server.
+ * by device memory and free slots, re-batching them each tick into launches on several CUDA
+ * streams so that work of different requests overlaps on the device.
+ * Admission: the workspace estimates of all launches on the device together stay within
+ * `hbm_budget` bytes (0 = 80% of the memory free at creation, and then each admission is also
+ * bounded by the memory free on the device at that moment). One launch groups same-scheme,
+ * same-mode requests up to a quarter of the budget; a single larger request (up to the whole
+ * budget; a global-type triplet counted at its slab workspace, see trioseq_batch_slabs) waits in
+ * arrival order until the running launches leave it room. A request larger than the budget
+ * completes with ENOMEM (reported by trioseq_poll).
+ * plans[0..nplans) are the scoring schemes a request may name by index (e.g. 0 = DNA,
+ * 1 = protein); they must outlive the server.
  * Errors: EINVAL, ENOMEM, ECUDA. */
 trioseq_status trioseq_server_create(const trioseq_plan_t* plans, int32_t nplans,
                                      size_t hbm_budget, trioseq_server_t* out);

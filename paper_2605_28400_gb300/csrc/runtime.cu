@@ -61,34 +61,38 @@ bool injected_alloc_failure() {
 struct DevBuf {
   void* p = nullptr;
   size_t cap = 0;
-  ~DevBuf() {
-    if (p) cudaFree(p);
+  cudaStream_t st_ = nullptr;  // stream of a stream-ordered allocation (freed in its order)
+  ~DevBuf() { reset(); }
+  // Release the buffer: stream-ordered allocations are freed in their stream's order, which
+  // blocks neither the host nor other streams.
+  void reset() {
+    if (p) {
+      if (st_)
+        cudaFreeAsync(p, st_);
+      else
+        cudaFree(p);
+    }
+    p = nullptr;
+    cap = 0;
+    st_ = nullptr;
   }
   // Grow to at least `bytes` (contents are not preserved). With a stream, the old buffer is
   // released and the new one taken in that stream's order (no device-wide synchronisation), so
-  // a growing workspace does not stall work running on other streams.
+  // a growing workspace does not stall work running on other streams. The caller orders that
+  // stream after the old buffer's last use.
   bool ensure(size_t bytes, cudaStream_t st = nullptr) {
     if (bytes <= cap && p) return true;
     const size_t want = std::max<size_t>(bytes, 256);
     if (injected_alloc_failure()) return false;
-    cudaError_t e;
-    if (st) {
-      if (p) cudaFreeAsync(p, st);
-      p = nullptr;
-      cap = 0;
-      e = cudaMallocAsync(&p, want, st);
-    } else {
-      if (p) cudaFree(p);
-      p = nullptr;
-      cap = 0;
-      e = cudaMalloc(&p, want);
-    }
+    reset();
+    const cudaError_t e = st ? cudaMallocAsync(&p, want, st) : cudaMalloc(&p, want);
     if (e != cudaSuccess) {
       p = nullptr;
       cudaGetLastError();
       return false;
     }
     cap = want;
+    st_ = st;
     return true;
   }
   template <typename T>
@@ -132,7 +136,56 @@ struct Workspace {
   DevBuf best64;    // semi-global / local traceback: (score, first cell) key per triplet
   DevBuf spans;     // traceback: begin and end cell of each alignment (6 int32)
   HostPinned staging;
-  cudaStream_t alloc_stream = nullptr;  // grow buffers in this stream's order (serving slots)
+  // Buffers are allocated and freed in this stream's order. Plans and device-resident batches
+  // own a private stream here (own_stream); a serving slot uses its launch stream.
+  cudaStream_t alloc_stream = nullptr;
+  bool own_stream = false;
+  // Recorded on the launching stream after each enqueued use: growth and destruction wait for
+  // this workspace's own work only, never for the whole device.
+  cudaEvent_t last_use = nullptr;
+  bool used = false;
+
+  // A private allocation stream (non-blocking, so it never waits on the legacy default stream).
+  cudaError_t make_own_stream() {
+    const cudaError_t e = cudaStreamCreateWithFlags(&alloc_stream, cudaStreamNonBlocking);
+    own_stream = e == cudaSuccess;
+    if (e != cudaSuccess) alloc_stream = nullptr;
+    return e;
+  }
+  // Mark the end of a use enqueued on `st`.
+  cudaError_t mark_use(cudaStream_t st) {
+    if (!last_use) {
+      const cudaError_t e = cudaEventCreateWithFlags(&last_use, cudaEventDisableTiming);
+      if (e != cudaSuccess) {
+        last_use = nullptr;
+        return e;
+      }
+    }
+    const cudaError_t e = cudaEventRecord(last_use, st);
+    used = used || e == cudaSuccess;
+    return e;
+  }
+  // Host wait for this workspace's last recorded use (not for other streams' work).
+  void wait_last_use() {
+    if (used && last_use) cudaEventSynchronize(last_use);
+  }
+  // Order the allocation stream after the last recorded use, before buffers are freed there.
+  void order_after_last_use() {
+    if (used && last_use && alloc_stream) cudaStreamWaitEvent(alloc_stream, last_use, 0);
+  }
+  // Free every device buffer in the allocation stream's order, after the last recorded use.
+  // Must run while that stream exists (a serving slot calls it before destroying its stream).
+  void release() {
+    order_after_last_use();
+    for (DevBuf* b : {&inputs, &faces, &progress, &codes, &scores, &rows, &lens, &planes,
+                      &walkstate, &best64, &spans})
+      b->reset();
+  }
+  ~Workspace() {
+    release();
+    if (last_use) cudaEventDestroy(last_use);
+    if (own_stream && alloc_stream) cudaStreamDestroy(alloc_stream);  // released when idle
+  }
 };
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
@@ -231,7 +284,7 @@ struct trioseq_batch_s {
   // holds the buffer addresses and the profiling switch the graph was captured with.
   cudaGraphExec_t gexec = nullptr;
   cudaStream_t capture_stream = nullptr;
-  std::array<const void*, 8> gkey{};
+  std::array<const void*, 12> gkey{};
   ~trioseq_batch_s() {
     for (auto& e : ev)
       if (e) cudaEventDestroy(e);
@@ -612,6 +665,7 @@ trioseq_status upload(trioseq_batch_s* bt, cudaStream_t st, bool pinned) {
   const bool tb = bt->mode == TRIOSEQ_WITH_TRACEBACK;
   const size_t nprog = bt->tasks.size() + 64;
   cudaStream_t as = ws.alloc_stream;
+  ws.order_after_last_use();  // a buffer that grows is freed only after its last use
   if (!ws.inputs.ensure(bt->inputs_bytes, as) ||
       !ws.faces.ensure(bt->face_ints * sizeof(int32_t), as) ||
       !ws.progress.ensure(nprog * sizeof(int32_t), as) ||
@@ -627,6 +681,9 @@ trioseq_status upload(trioseq_batch_s* bt, cudaStream_t st, bool pinned) {
        !ws.best64.ensure(std::max<size_t>(bt->n, 1) * sizeof(unsigned long long), as)) ||
       (pinned && !ws.staging.ensure(bt->inputs_bytes)))
     return TRIOSEQ_ENOMEM;
+  // On a private allocation stream, the buffers are ready before any launch stream uses them.
+  if (ws.own_stream && cudaStreamSynchronize(as) != cudaSuccess)
+    return cuda_status(cudaGetLastError());
   std::vector<char> pageable;
   if (!pinned) pageable.assign(bt->inputs_bytes, 0);
   char* h = pinned ? reinterpret_cast<char*>(ws.staging.p) : pageable.data();
@@ -796,9 +853,12 @@ trioseq_status run(trioseq_batch_s* bt, cudaStream_t st) {
 // buffers or the profiling switch changed since it was captured.
 trioseq_status run_graph(trioseq_batch_s* bt, cudaStream_t st) {
   const Workspace& ws = *bt->ws;
-  const std::array<const void*, 8> key{ws.inputs.p, ws.faces.p, ws.progress.p, ws.codes.p,
-                                       ws.scores.p, ws.rows.p, ws.lens.p,
-                                       bt->profile ? (const void*)bt->ev[0] : nullptr};
+  // every device address a captured launch bakes in (the slab and walk launches included)
+  const std::array<const void*, 12> key{ws.inputs.p,    ws.faces.p,     ws.progress.p,
+                                        ws.codes.p,     ws.scores.p,    ws.rows.p,
+                                        ws.lens.p,      ws.planes.p,    ws.walkstate.p,
+                                        ws.best64.p,    ws.spans.p,
+                                        bt->profile ? (const void*)bt->ev[0] : nullptr};
   if (!bt->gexec || key != bt->gkey) {
     if (bt->gexec) {
       cudaGraphExecDestroy(bt->gexec);
@@ -968,11 +1028,16 @@ trioseq_status trioseq_plan(const trioseq_scoring* sc, uint32_t max_len_hint, ui
       }
     plan->max_abs_sig2 = std::max(mx, 1);
     plan->sig2_nonneg = mn >= 0;
-    if (!plan->sig_score.ensure(s2.size() * 4) || !plan->sig_tb.ensure(s8.size() * 4))
+    // The plan's device memory is allocated and freed in the order of its own stream.
+    if (plan->ws.make_own_stream() != cudaSuccess) return cuda_status(cudaGetLastError());
+    cudaStream_t as = plan->ws.alloc_stream;
+    if (!plan->sig_score.ensure(s2.size() * 4, as) || !plan->sig_tb.ensure(s8.size() * 4, as))
       return TRIOSEQ_ENOMEM;
-    if (cudaMemcpy(plan->sig_score.p, s2.data(), s2.size() * 4, cudaMemcpyHostToDevice) !=
+    if (cudaMemcpyAsync(plan->sig_score.p, s2.data(), s2.size() * 4, cudaMemcpyHostToDevice,
+                        as) != cudaSuccess ||
+        cudaMemcpyAsync(plan->sig_tb.p, s8.data(), s8.size() * 4, cudaMemcpyHostToDevice, as) !=
             cudaSuccess ||
-        cudaMemcpy(plan->sig_tb.p, s8.data(), s8.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+        cudaStreamSynchronize(as) != cudaSuccess)
       return cuda_status(cudaGetLastError());
     plan->TI = std::max(1, env_int("TRIOSEQ_TI", 8));
     plan->graphs = env_int("TRIOSEQ_GRAPHS", 1) != 0;
@@ -1015,7 +1080,15 @@ trioseq_status trioseq_plan_destroy(trioseq_plan_t plan) {
   return no_throw([&]() -> trioseq_status {
     if (!plan) return TRIOSEQ_OK;
     DeviceGuard g(plan->device);
-    cudaDeviceSynchronize();
+    // Wait for the plan's own last use only (its trioseq_align_batch work); batches made from
+    // the plan are destroyed before it and have waited for theirs. Other streams, a running
+    // server's included, are not synchronised. The substitution tables are freed in the order
+    // of the plan's stream, before the workspace releases that stream.
+    plan->ws.wait_last_use();
+    plan->last.reset();
+    plan->ws.order_after_last_use();
+    plan->sig_score.reset();
+    plan->sig_tb.reset();
     delete plan;
     return TRIOSEQ_OK;
   });
@@ -1035,7 +1108,9 @@ trioseq_status trioseq_align_batch(trioseq_plan_t plan, const trioseq_triplet* t
     if (s != TRIOSEQ_OK) return s;
     bt->ws = &plan->ws;
     if ((s = upload(bt.get(), st, true)) != TRIOSEQ_OK) return s;
-    if ((s = run(bt.get(), st)) != TRIOSEQ_OK) return s;
+    s = run(bt.get(), st);
+    plan->ws.mark_use(st);  // also after a partial enqueue: destroy waits for what did run
+    if (s != TRIOSEQ_OK) return s;
     if ((s = fetch(bt.get(), st, scores_out)) != TRIOSEQ_OK) return s;
     bt->seq.clear();
     bt->seq.shrink_to_fit();
@@ -1074,6 +1149,7 @@ trioseq_status trioseq_batch_create(trioseq_plan_t plan, const trioseq_triplet* 
     if (s != TRIOSEQ_OK) return s;
     bt->own_ws.reset(new (std::nothrow) Workspace());
     if (!bt->own_ws) return TRIOSEQ_ENOMEM;
+    if (bt->own_ws->make_own_stream() != cudaSuccess) return cuda_status(cudaGetLastError());
     bt->ws = bt->own_ws.get();
     if ((s = upload(bt.get(), nullptr, false)) != TRIOSEQ_OK) return s;
     *out = bt.release();
@@ -1086,7 +1162,10 @@ trioseq_status trioseq_batch_run(trioseq_batch_t bt, void* stream) {
     NvtxRange range("trioseq_batch_run");
     if (!bt) return TRIOSEQ_EINVAL;
     DeviceGuard g(bt->plan->device);
-    return bt->plan->graphs ? run_graph(bt, (cudaStream_t)stream) : run(bt, (cudaStream_t)stream);
+    const cudaStream_t st = (cudaStream_t)stream;
+    const trioseq_status s = bt->plan->graphs ? run_graph(bt, st) : run(bt, st);
+    const cudaError_t e = bt->ws->mark_use(st);
+    return s != TRIOSEQ_OK ? s : cuda_status(e);
   });
 }
 
@@ -1267,7 +1346,9 @@ trioseq_status trioseq_batch_destroy(trioseq_batch_t bt) {
   return no_throw([&]() -> trioseq_status {
     if (!bt) return TRIOSEQ_OK;
     DeviceGuard g(bt->plan->device);
-    cudaDeviceSynchronize();
+    // Wait for this batch's own last run only; its buffers are then freed in the order of its
+    // private stream. Other streams (a running server's included) are not synchronised.
+    bt->ws->wait_last_use();
     delete bt;
     return TRIOSEQ_OK;
   });
@@ -1295,7 +1376,8 @@ struct SrvReq {
   int32_t plan_id = 0;
   uint32_t mode = 0;
   std::string s[3];
-  size_t bytes = 0;
+  size_t bytes = 0;        // workspace estimate inside a launch of several requests
+  size_t bytes_alone = 0;  // estimate of a launch of this request alone (slab form if it applies)
 };
 
 struct SrvRes {
@@ -1314,6 +1396,7 @@ struct SrvSlot {
   size_t off_err = 0, off_lens = 0, off_rows = 0;
   std::unique_ptr<trioseq_batch_s> batch;
   std::vector<SrvReq> reqs;
+  size_t bytes = 0;  // workspace estimate admitted for the launch on this slot
   trioseq_status launch_st = TRIOSEQ_OK;
 };
 
@@ -1330,13 +1413,35 @@ size_t request_bytes(const trioseq_plan_s* plan, uint32_t mode, const uint32_t l
   return bytes;
 }
 
+// The same request launched alone: a global-type triplet whose one-launch workspace exceeds the
+// plan's slab budget runs in slabs within that budget (build_batch), so it needs no more.
+size_t request_bytes_alone(const trioseq_plan_s* plan, uint32_t mode, const uint32_t len[3]) {
+  const size_t full = request_bytes(plan, mode, len);
+  return plan->atype == kGlobal ? std::min(full, std::max<size_t>(plan->slab_budget, 1 << 20))
+                                : full;
+}
+
+size_t workspace_device_bytes(const Workspace& ws) {
+  return ws.inputs.cap + ws.faces.cap + ws.progress.cap + ws.codes.cap + ws.scores.cap +
+         ws.rows.cap + ws.lens.cap + ws.planes.cap + ws.walkstate.cap + ws.best64.cap +
+         ws.spans.cap;
+}
+
 }  // namespace
 
 struct trioseq_server_s {
   static constexpr int kSlots = 4;
   std::vector<trioseq_plan_s*> plans;
   int device = 0;
-  size_t slot_budget = 0;
+  // Admission by device memory: launches on the device together hold at most `budget` bytes of
+  // workspace estimates (in_flight). With no budget given, each admission is also bounded by
+  // the memory free on the device at that moment. launch_share (budget / kSlots) caps how many
+  // small requests one launch groups, so that several launches overlap; a single larger
+  // request may use whatever room is left, and waits for room while other launches run.
+  size_t budget = 0;
+  size_t launch_share = 0;
+  size_t in_flight = 0;
+  bool budget_from_free = false;
   size_t max_pending = (size_t)1 << 20;  // TRIOSEQ_SERVER_MAX_PENDING at creation
   size_t max_batch = 1024;
   std::thread th;
@@ -1443,6 +1548,8 @@ void srv_harvest(trioseq_server_s* S, SrvSlot& sl) {
   sl.reqs.clear();
   sl.batch.reset();
   sl.busy = false;
+  S->in_flight -= std::min(S->in_flight, sl.bytes);
+  sl.bytes = 0;
 }
 
 void srv_loop(trioseq_server_s* S) {
@@ -1461,35 +1568,60 @@ void srv_loop(trioseq_server_s* S) {
     }
     for (auto& sl : S->slots) {
       if (sl.busy || S->pending.empty()) continue;
+      // Room for a launch on this slot: the budget minus the launches in flight, and with no
+      // budget given, no more than the device has free now (plus what this slot already holds,
+      // which the launch reuses).
+      size_t room = S->budget > S->in_flight ? S->budget - S->in_flight : 0;
+      if (S->budget_from_free) {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess)
+          room = std::min(room, fr / 10 * 9 + workspace_device_bytes(sl.ws));
+        else
+          cudaGetLastError();
+      }
+      bool others_busy = false;
+      for (auto& o : S->slots) others_busy = others_busy || o.busy;
+      const SrvReq& head = S->pending.front();
+      if (head.bytes_alone > room) {
+        if (others_busy) break;  // wait: harvested launches give their room back
+        if (head.bytes_alone > S->budget) {  // can never fit: fail it alone
+          SrvRes r;
+          r.st = TRIOSEQ_ENOMEM;
+          S->done[head.ticket] = std::move(r);
+          S->pending.pop_front();
+          acted = true;
+          continue;
+        }
+        // nothing else runs: launch it; its allocations report a real shortage (ENOMEM)
+      }
       // Form a launch: the oldest request fixes the group; same-group requests follow in arrival
-      // order while the workspace estimate fits the slot's share of the budget.
-      const int32_t pid = S->pending.front().plan_id;
-      const uint32_t mode = S->pending.front().mode;
-      size_t bytes = 0;
+      // order while the launch's estimate stays within its share of the room.
+      const int32_t pid = head.plan_id;
+      const uint32_t mode = head.mode;
+      const size_t limit = std::max(head.bytes_alone, std::min(room, S->launch_share));
+      size_t full = 0;
       std::deque<SrvReq> rest;
       while (!S->pending.empty()) {
         SrvReq& r = S->pending.front();
         const bool same = r.plan_id == pid && r.mode == mode;
-        if (same && sl.reqs.size() < S->max_batch &&
-            (sl.reqs.empty() || bytes + r.bytes <= S->slot_budget)) {
-          bytes += r.bytes;
+        if (sl.reqs.empty() ||
+            (same && sl.reqs.size() < S->max_batch && full + r.bytes <= limit)) {
+          full += r.bytes;
           sl.reqs.push_back(std::move(r));
         } else {
           rest.push_back(std::move(r));
         }
         S->pending.pop_front();
-        if (sl.reqs.size() >= S->max_batch || bytes >= S->slot_budget) break;
+        if (sl.reqs.size() >= S->max_batch || full >= limit) break;
       }
       while (!rest.empty()) {  // keep arrival order of what was skipped
         S->pending.push_front(std::move(rest.back()));
         rest.pop_back();
       }
+      sl.bytes = sl.reqs.size() == 1 ? sl.reqs.front().bytes_alone : full;
+      S->in_flight += sl.bytes;
       sl.busy = true;
       acted = true;
-      if (bytes > S->slot_budget) {  // a single request larger than the budget
-        sl.launch_st = TRIOSEQ_ENOMEM;
-        continue;
-      }
       lk.unlock();
       sl.launch_st = no_throw([&] { return srv_launch(S, sl); });  // the thread must not throw
       lk.lock();
@@ -1521,8 +1653,10 @@ trioseq_status trioseq_server_create(const trioseq_plan_t* plans, int32_t nplans
       size_t fr = 0, tot = 0;
       if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return cuda_status(cudaGetLastError());
       hbm_budget = fr / 10 * 8;
+      S->budget_from_free = true;
     }
-    S->slot_budget = std::max<size_t>(hbm_budget / trioseq_server_s::kSlots, 1 << 20);
+    S->budget = std::max<size_t>(hbm_budget, 1 << 20);
+    S->launch_share = std::max<size_t>(S->budget / trioseq_server_s::kSlots, 1 << 20);
     S->max_pending = (size_t)std::max(0, env_int("TRIOSEQ_SERVER_MAX_PENDING", 1 << 20));
     for (auto& sl : S->slots) {
       if (cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess ||
@@ -1564,6 +1698,7 @@ trioseq_status trioseq_submit(trioseq_server_t S, const trioseq_triplet* t, int3
             sumlen >= (1LL << 26) - 1)
       return TRIOSEQ_EOVERFLOW;
     r.bytes = request_bytes(plan, mode, t->len);
+    r.bytes_alone = request_bytes_alone(plan, mode, t->len);
     {
       std::lock_guard<std::mutex> lk(S->mu);
       if (S->stop) return TRIOSEQ_EINVAL;
@@ -1615,6 +1750,9 @@ trioseq_status trioseq_server_destroy(trioseq_server_t S) {
     {
       DeviceGuard g(S->device);
       for (auto& sl : S->slots) {
+        if (sl.stream) cudaStreamSynchronize(sl.stream);
+        sl.batch.reset();
+        sl.ws.release();  // freed in the slot stream's order, while the stream exists
         if (sl.stream) cudaStreamSynchronize(sl.stream);
         if (sl.done) cudaEventDestroy(sl.done);
         if (sl.stream) cudaStreamDestroy(sl.stream);

@@ -134,3 +134,53 @@ def test_variant_plans_served_with_traceback():
         if tb:  # an empty alignment comes back as no rows
             assert (got_rows or ("", "", "")) == tuple(
                 "".join("-" if v == 255 else sc.alphabet[v] for v in r) for r in rows)
+
+
+def test_request_beyond_a_launch_share_waits_for_room_and_is_exact():
+    """Admission shares one device-memory budget among the launches in flight. With a 64 MiB
+    budget, a quarter (one launch's share of small requests) is 16 MiB. A 600-residue triplet
+    needs about 46 MiB of workspace: it must wait for room among small requests and complete
+    exactly (oracle). An 800-residue triplet needs about 108 MiB, more than the whole budget:
+    it completes with ENOMEM while everything around it still completes exactly."""
+    dna = synth.dna_scoring()
+    plan = B.trioseq_plan(dna.alphabet, dna.sub, dna.gap)
+    small = [synth.related_triplet(77, i, 90 + 7 * i, dna, 0.05, 0.02, 2.0) for i in range(12)]
+    mid = synth.related_triplet(78, 0, 600, dna, 0.05, 0.02, 2.0)
+    huge = synth.related_triplet(79, 0, 800, dna, 0.05, 0.02, 2.0)
+    order = small[:6] + [mid] + small[6:9] + [huge] + small[9:]
+    srv = B.trioseq_server_create([plan], hbm_budget=64 << 20)
+    try:
+        tickets = []
+        for i, trip in enumerate(order):
+            mode = B.WITH_TRACEBACK if i % 4 == 1 else B.SCORE_ONLY
+            st, tk = B.trioseq_submit(srv, [synth.to_str(s, dna.alphabet) for s in trip], 0, mode)
+            assert st == B.OK
+            tickets.append((tk, mode))
+        huge_tk = tickets[order.index(huge)][0]
+        rest = [tk for tk, _ in tickets if tk != huge_tk]
+        got = _poll_all(srv, rest, 3 * 700)
+        t0 = time.time()
+        while True:
+            try:
+                st, _, _ = B.trioseq_poll(srv, huge_tk, 0)
+            except B.TrioseqError as e:
+                assert e.status == B.ENOMEM
+                break
+            assert st == B.EAGAIN and time.time() - t0 < 60
+            time.sleep(0.001)
+    finally:
+        B.trioseq_server_destroy(srv)
+    try:
+        for (tk, mode), trip in zip(tickets, order):
+            if tk == huge_tk:
+                continue
+            score, rows = got[tk]
+            if mode == B.WITH_TRACEBACK:
+                want, wrows = oracle.align(*trip, dna.sub, dna.gap, traceback=True)
+                assert rows == tuple("".join("-" if v == 255 else dna.alphabet[v] for v in r)
+                                     for r in wrows)
+            else:
+                want = oracle.align(*trip, dna.sub, dna.gap)
+            assert score == want
+    finally:
+        B.trioseq_plan_destroy(plan)
