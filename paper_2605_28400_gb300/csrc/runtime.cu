@@ -216,6 +216,7 @@ struct trioseq_plan_s {
   int TI = 8;
   int64_t wait_ns = 2000000000LL;  // 2 s without progress = give up
   bool test_wait_unset = false;    // test switch: first-wave warps wait on a flag nothing sets
+  bool test_poison = false;        // test switch: boundary records start as a large garbage value
   bool graphs = true;              // trioseq_batch_run replays a captured CUDA graph
   bool packed16 = true;            // pair score-only global triplets in int16 halves if they fit
   bool sig2_nonneg = false;        // every sigma'' >= 0: the biased packed mode applies
@@ -701,6 +702,15 @@ trioseq_status upload(trioseq_batch_s* bt, cudaStream_t st, bool pinned) {
       pinned ? cudaMemcpyAsync(ws.inputs.p, h, bt->inputs_bytes, cudaMemcpyHostToDevice, st)
              : cudaMemcpy(ws.inputs.p, h, bt->inputs_bytes, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return cuda_status(e);
+  // Test switch: fill the boundary records and slab planes with 0x3F3F3F3F, a value far above
+  // any score, so that a kernel reading a record slot before (or without) its producer writing
+  // it gives a wrong result instead of one that fresh, zeroed memory would hide.
+  if (bt->plan->test_poison) {
+    if (ws.faces.p && (e = cudaMemsetAsync(ws.faces.p, 0x3F, ws.faces.cap, st)) != cudaSuccess)
+      return cuda_status(e);
+    if (ws.planes.p && (e = cudaMemsetAsync(ws.planes.p, 0x3F, ws.planes.cap, st)) != cudaSuccess)
+      return cuda_status(e);
+  }
   bt->uploaded = true;
   bt->h2d_bytes = bt->inputs_bytes;
   return TRIOSEQ_OK;
@@ -1045,6 +1055,7 @@ trioseq_status trioseq_plan(const trioseq_scoring* sc, uint32_t max_len_hint, ui
     plan->pace = env_int("TRIOSEQ_PACE", 1) != 0;
     plan->wait_ns = (int64_t)std::max(1, env_int("TRIOSEQ_WAIT_MS", 2000)) * 1000000LL;
     plan->test_wait_unset = env_int("TRIOSEQ_TEST_WAIT_UNSET", 0) != 0;
+    plan->test_poison = env_int("TRIOSEQ_TEST_POISON", 0) != 0;
     g_alloc_calls.store(0);
     g_alloc_fail_at.store(std::max(0, env_int("TRIOSEQ_TEST_FAIL_ALLOC", 0)));
     {
@@ -1267,7 +1278,7 @@ trioseq_status trioseq_plan_autotune(trioseq_plan_t plan, const trioseq_triplet*
     // 8x16 and 8x8 with vl: two cells of one triplet per register
     static const Variant kScoreTiles[] = {{8, 8}, {4, 8}, {4, 4}, {8, 16, 1}, {8, 8, 1}};
     static const Variant kTbTiles[] = {{8, 8}, {4, 8}, {4, 4}, {8, 4}};
-    static const int kTI[] = {4, 8, 16, 32};
+    static const int kTI[] = {2, 4, 8, 16, 32};
     const bool tb_mode = mode == TRIOSEQ_WITH_TRACEBACK;
     const Variant* tiles = tb_mode ? kTbTiles : kScoreTiles;
     const size_t ntiles = tb_mode ? sizeof(kTbTiles) / sizeof(kTbTiles[0])

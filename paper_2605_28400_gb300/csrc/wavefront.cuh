@@ -40,6 +40,17 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
   return v;
 }
 
+// Relaxed gpu-scope load of a progress flag, issued a step before its value is needed; when
+// the value is used, fence_acquire() completes the acquire pattern (relaxed load, then acquire
+// fence), so the record loads that follow see the producer's stores before its release.
+__device__ __forceinline__ int ld_relaxed(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+
+__device__ __forceinline__ void fence_acquire() { asm volatile("fence.acquire.gpu;" ::: "memory"); }
+
 __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -52,8 +63,9 @@ __device__ __forceinline__ uint64_t global_ns() {
 
 // Lane-0 wait until *flag >= need. `cached` keeps the last value seen. Polls with acquire loads
 // (the satisfying one orders the record loads that follow; unlike a fence it does not wait for
-// this warp's own record stores in flight) and exponential back-off, light on L2 while many
-// warps wait. Gives up (returns false) when the flag has not moved for wait_ns.
+// this warp's own record stores in flight) and exponential back-off up to 256 ns, light on L2
+// while many warps wait and at most a fraction of a step late. Gives up (returns false) when
+// the flag has not moved for wait_ns.
 __device__ __noinline__ bool wait_flag(const int* flag, int need, int* cached, int64_t wait_ns) {
   int v = ld_acquire(flag);
   if (v >= need) {
@@ -65,7 +77,7 @@ __device__ __noinline__ bool wait_flag(const int* flag, int need, int* cached, i
   uint64_t t0 = global_ns();
   for (;;) {
     __nanosleep(ns);
-    if (ns < 1024) ns <<= 1;
+    if (ns < 256) ns <<= 1;
     v = ld_acquire(flag);
     if (v >= need) {
       *cached = v;
@@ -393,6 +405,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
     const int* progK = p.progress + d.prog_base + (me - 1);
     int* progMe = p.progress + d.prog_base + me;
     int cachedJ = J > 0 ? 0 : 1 << 30, cachedK = K > 0 ? 0 : 1 << 30;  // warp-uniform
+    int pfJ = 0, pfK = 0;  // lane 0: producers' progress read one step ahead (relaxed loads)
     uint32_t* code_base = (TB && (!SLAB || p.codes))
                               ? p.codes + d.code_off + (int64_t)me * T * 32 * W + lane * W
                               : nullptr;
@@ -419,13 +432,22 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
         bool okl = true;
         int cj = cachedJ, ck = cachedK;
         if (lane == 0) {
+          // First the values read one step ago: a check they satisfy costs no L2 round trip.
+          const bool pre = pfJ > cj || pfK > ck;
+          cj = max(cj, pfJ);
+          ck = max(ck, pfK);
           if (cj < needJ) okl = wait_flag(progJ, needJ, &cj, p.wait_ns);
           if (okl && ck < needK) okl = wait_flag(progK, needK, &ck, p.wait_ns);
+          if (pre) fence_acquire();  // the prefetched values' acquire pattern
         }
         ok = __shfl_sync(kFull, okl, 0);
         cachedJ = __shfl_sync(kFull, cj, 0);
         cachedK = __shfl_sync(kFull, ck, 0);
         __syncwarp();
+      }
+      if (lane == 0) {  // progress for the next step's check
+        if (cachedJ < T) pfJ = ld_relaxed(progJ);
+        if (cachedK < T) pfK = ld_relaxed(progK);
       }
       const int sl = u - cp_delta;
       pf_u = u;

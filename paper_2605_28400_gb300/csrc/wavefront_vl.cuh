@@ -194,6 +194,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, (NH >= 8 ? 2 : 3))
     const int* progK = p.progress + d.prog_base + (me - 1);
     int* progMe = p.progress + d.prog_base + me;
     int cachedJ = J > 0 ? 0 : 1 << 30, cachedK = K > 0 ? 0 : 1 << 30;  // warp-uniform
+    int pfJ = 0, pfK = 0;  // lane 0: producers' progress read one step ahead (relaxed loads)
     bool ok = true;
 
     // Face pieces (absolute int32 records, kNeg where absent): loaded two steps ahead, parked one
@@ -208,14 +209,22 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, (NH >= 8 ? 2 : 3))
       if (cachedJ < needJ || cachedK < needK) {  // warp-uniform
         bool okl = true;
         int cj = cachedJ, ck = cachedK;
-        if (lane == 0) {
+        if (lane == 0) {  // prefetched values first, as in wavefront_kernel
+          const bool pre = pfJ > cj || pfK > ck;
+          cj = max(cj, pfJ);
+          ck = max(ck, pfK);
           if (cj < needJ) okl = wait_flag(progJ, needJ, &cj, p.wait_ns);
           if (okl && ck < needK) okl = wait_flag(progK, needK, &ck, p.wait_ns);
+          if (pre) fence_acquire();
         }
         ok = __shfl_sync(kFull, okl, 0);
         cachedJ = __shfl_sync(kFull, cj, 0);
         cachedK = __shfl_sync(kFull, ck, 0);
         __syncwarp();
+      }
+      if (lane == 0) {
+        if (cachedJ < T) pfJ = ld_relaxed(progJ);
+        if (cachedK < T) pfK = ld_relaxed(progK);
       }
       pf_u = u;
 #pragma unroll
@@ -237,13 +246,17 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, (NH >= 8 ? 2 : 3))
 
     fetch(0);
     // The task's base: the largest record value its first slice borders (0 without producers);
-    // every cell of the working set lies within the range argument of it.
+    // every cell of the working set lies within the range argument of it. The first j-record
+    // piece (record slots 0..3) carries only the corner in slot 3: slots 0..2 are never
+    // written, so they stay out of the maximum.
     int Bt = 0;
     {
       int mx = kNeg;
 #pragma unroll
-      for (int m = 0; m < G::NPL; ++m)
-        mx = max(mx, max(max(pf[m].x, pf[m].y), max(pf[m].z, pf[m].w)));
+      for (int m = 0; m < G::NPL; ++m) {
+        const bool corner_only = cp_kind[m] == 1 && cp_col[m] == 0;
+        mx = max(mx, corner_only ? pf[m].w : max(max(pf[m].x, pf[m].y), max(pf[m].z, pf[m].w)));
+      }
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(kFull, mx, off));
       Bt = mx > kNeg / 2 ? mx : 0;

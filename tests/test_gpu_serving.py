@@ -156,7 +156,7 @@ def test_request_beyond_a_launch_share_waits_for_room_and_is_exact():
             st, tk = B.trioseq_submit(srv, [synth.to_str(s, dna.alphabet) for s in trip], 0, mode)
             assert st == B.OK
             tickets.append((tk, mode))
-        huge_tk = tickets[order.index(huge)][0]
+        huge_tk = tickets[next(i for i, t in enumerate(order) if t is huge)][0]
         rest = [tk for tk, _ in tickets if tk != huge_tk]
         got = _poll_all(srv, rest, 3 * 700)
         t0 = time.time()
