@@ -169,7 +169,7 @@ def kernel_source_hash(tile: str) -> str:
     """Hash of the sources a tile's wavefront kernel is compiled from: the two-cells-per-register
     kernel (tile label ending in 'v') or the int32 / two-triplets kernel family."""
     common = ("wavefront.cuh", "engine.h")
-    own = (("wavefront_vl.cuh", "kernels_vl.cu") if tile.endswith("v")
+    own = (("wavefront_vl.cuh", "kernels_vl.cu") if tile.endswith(("v", "s")) or tile == "8x16"
            else ("kernels.cu", "kernels_packed.cu", "kernels_slab.cu", "kernels_variants.cu"))
     h = hashlib.sha256()
     for f in common + own:
@@ -207,16 +207,10 @@ def shard_workload(w, world: int, rank: int, B):
 
 
 def kernel_of(info: dict, n_triplets: int):
-    """(tile label, kernel name) of a batch. A packed one-triplet batch runs two column halves
-    of the triplet per register (wavefront_vl_kernel<8, half width>, tile label with a 'v');
-    a packed batch of several triplets runs two triplets per register."""
-    tj, tk = info["tile"]
-    packing = info.get("packing", 1)
-    if packing == 2 and n_triplets == 1:
-        return f"{tj}x{tk}v", f"wavefront_vl_kernel<{tj},{tk // 2}>"
-    if packing == 2:
-        return f"{tj}x{tk}", f"wavefront_kernel<{tj},{tk}> (two triplets per register)"
-    return f"{tj}x{tk}", f"wavefront_kernel<{tj},{tk}>"
+    """(tile label, kernel name) of a batch, as the library reports them (trioseq_batch_kernel):
+    e.g. ("8x8v", "wavefront_vl_kernel<8,4,false>") for two column halves of one triplet per
+    register, ("8x16s", ...) for its variant with the sigma''(y,z) tile in shared memory."""
+    return info["tile_label"], info["kernel"]
 
 
 def measured_traffic(key: str, tile: str):

@@ -193,6 +193,14 @@ trioseq_status trioseq_batch_info(trioseq_batch_t batch, size_t* n, uint64_t* ce
  * Results are identical either way. Errors: EINVAL (null). */
 trioseq_status trioseq_batch_packing(trioseq_batch_t batch, int32_t* per_word);
 
+/* trioseq_batch_kernel — the wavefront kernel a batch launches, as a NUL-terminated name with
+ * its template arguments and tile label (for example "wavefront_vl_kernel<8,4,false> tile 8x8v",
+ * "wavefront_vl_kernel<8,8,true> tile 8x16s" or "wavefront_kernel<8,4,traceback,global> tile
+ * 8x4"), written into name[0..cap). The "8x16s" tile keeps the lane's sigma''(y,z) tile and
+ * 16-bit profiles in shared memory and runs 2-warp CTAs. Errors: EINVAL (null, cap too small:
+ * the name is then cut). */
+trioseq_status trioseq_batch_kernel(trioseq_batch_t batch, char* name, size_t cap);
+
 /* trioseq_batch_slabs — slab layout of a one-triplet batch: *slices = slices per slab, *slabs =
  * number of slabs, both 0 when the cube runs in one launch.
  * A one-triplet, global-type batch runs in slabs when its boundary records, plus with traceback

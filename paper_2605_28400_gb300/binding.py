@@ -86,6 +86,7 @@ def load(build_if_missing: bool = True):
                                   i32),
         "trioseq_plan_autotune": ([vp, ctypes.POINTER(Triplet), sz, u32, i32p, i32p, i32p], i32),
         "trioseq_batch_packing": ([vp, i32p], i32),
+        "trioseq_batch_kernel": ([vp, ctypes.c_char_p, sz], i32),
         "trioseq_batch_slabs": ([vp, i32p, i32p], i32),
         "trioseq_traceback_span": ([vp, sz, i32p, i32p], i32),
         "trioseq_batch_span": ([vp, sz, i32p, i32p], i32),
@@ -109,7 +110,8 @@ def exported_symbols() -> list[str]:
             "trioseq_batch_destroy", "trioseq_batch_profile", "trioseq_batch_timing",
             "trioseq_plan_io_bytes", "trioseq_server_create", "trioseq_submit", "trioseq_poll",
             "trioseq_server_destroy", "trioseq_strerror", "trioseq_align_noalloc",
-            "trioseq_plan_autotune", "trioseq_batch_packing", "trioseq_batch_slabs",
+            "trioseq_plan_autotune", "trioseq_batch_packing", "trioseq_batch_kernel",
+            "trioseq_batch_slabs",
             "trioseq_traceback_span", "trioseq_batch_span", "trioseq_alu_rate",
             "trioseq_partition"]
 
@@ -306,8 +308,12 @@ def trioseq_batch_info(batch) -> dict:
     sl, ns = ctypes.c_int32(), ctypes.c_int32()
     _check(load().trioseq_batch_slabs(batch, ctypes.byref(sl), ctypes.byref(ns)),
            "trioseq_batch_slabs")
+    name = ctypes.create_string_buffer(160)
+    _check(load().trioseq_batch_kernel(batch, name, 160), "trioseq_batch_kernel")
+    kernel, _, label = name.value.decode().partition(" tile ")
     return {"n": n.value, "cells": cells.value, "tasks": tasks.value, "tile": (tj.value, tk.value),
-            "packing": per.value, "slab_slices": sl.value, "slabs": ns.value}
+            "packing": per.value, "slab_slices": sl.value, "slabs": ns.value, "kernel": kernel,
+            "tile_label": label}
 
 
 def trioseq_batch_destroy(batch):

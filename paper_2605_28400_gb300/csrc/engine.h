@@ -141,7 +141,9 @@ struct WalkParams {
 // semi-global and local exist for score mode (tb = false) only, and their scores are
 // accumulated with atomicMax, so the score array must hold INT_MIN-like values before launch.
 // `slab` selects the slab-launch instantiations (global type, int32, either mode).
-// `pk` is the packed mode: 0 int32, 1 signed int16x2, 2 biased unsigned int16x2.
+// `pk` is the packed mode: 0 int32, 1 signed int16x2, 2 biased unsigned int16x2, 3 two cells of
+// one triplet per register, 4 and 5 the same with the sigma''(y,z) tile in shared memory (2-warp
+// and 1-warp CTAs).
 int launch_wavefront(int nj, int nk, bool tb, int at, int pk, bool slab, const WaveParams& p,
                      int grid, size_t smem, void* stream);
 int wavefront_occupancy(int nj, int nk, bool tb, int at, int pk, bool slab, size_t smem,
@@ -150,12 +152,18 @@ int wavefront_occupancy(int nj, int nk, bool tb, int at, int pk, bool slab, size
 const void* wavefront_variant(int nj, int nk, int at, bool tb);
 // Kernel entry of a packed int16x2 (global, score) instantiation (kernels_packed.cu), or null.
 const void* wavefront_packed(int nj, int nk, int mode);
-// two cells of one triplet per register (wavefront_vl.cuh): nj x nk = 8 x 16 cells per lane
-const void* wavefront_vl(int nj, int nk);
-size_t wavefront_vl_smem_bytes(int nj, int nk, int KP);
+// two cells of one triplet per register (wavefront_vl.cuh): nj x nk = 8 x 16 or 8 x 8 cells per
+// lane; cs = 1 or 2: the lane's sigma''(y,z) tile in shared memory (8 x 16 only; 2-warp or
+// 1-warp CTAs), 0: in registers
+const void* wavefront_vl(int nj, int nk, int cs);
+size_t wavefront_vl_smem_bytes(int nj, int nk, int KP, int cs);
+int wavefront_vl_warps(int cs);
 // Kernel entry of a slab-launch instantiation (kernels_slab.cu), or null.
 const void* wavefront_slab(int nj, int nk, bool tb);
 int launch_walk(const WalkParams& p, void* stream);
 size_t wavefront_smem_bytes(int nj, int nk, int KP, bool pk);
+// threads per CTA of a launch in packed mode pk (2 warps for pk = 4, 1 for pk = 5, else
+// kWarpsPerCta)
+int wavefront_block_threads(int pk);
 
 }  // namespace trioseq

@@ -248,7 +248,7 @@ const void* kptr() {
 
 const void* pick(int nj, int nk, bool tb, int at, int pk, bool slab) {
   if (slab) return (pk || at != kGlobal) ? nullptr : wavefront_slab(nj, nk, tb);
-  if (pk == 3) return (tb || at != kGlobal) ? nullptr : wavefront_vl(nj, nk);
+  if (pk >= 3) return (tb || at != kGlobal) ? nullptr : wavefront_vl(nj, nk, pk - 3);
   if (pk) return (tb || at != kGlobal) ? nullptr : wavefront_packed(nj, nk, pk);
   if (at != kGlobal) return wavefront_variant(nj, nk, at, tb);
   if (nj == 8 && nk == 8) return tb ? kptr<8, 8, true>() : kptr<8, 8, false>();
@@ -261,6 +261,8 @@ const void* pick(int nj, int nk, bool tb, int at, int pk, bool slab) {
 }
 
 }  // namespace
+
+int wavefront_block_threads(int pk) { return 32 * (pk >= 3 ? wavefront_vl_warps(pk - 3) : kWarpsPerCta); }
 
 size_t wavefront_smem_bytes(int nj, int nk, int KP, bool pk) {
   const int WJ = kPR * nj, WK = kPC * nk;
@@ -278,8 +280,8 @@ int wavefront_occupancy(int nj, int nk, bool tb, int at, int pk, bool slab, size
   if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
       cudaSuccess)
     return -2;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, kWarpsPerCta * 32, smem) !=
-      cudaSuccess)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k, wavefront_block_threads(pk),
+                                                    smem) != cudaSuccess)
     return -2;
   return 0;
 }
@@ -289,8 +291,8 @@ int launch_wavefront(int nj, int nk, bool tb, int at, int pk, bool slab, const W
   const void* k = pick(nj, nk, tb, at, pk, slab);
   if (!k) return -1;
   void* args[] = {const_cast<WaveParams*>(&p)};
-  const cudaError_t e = cudaLaunchKernel(k, dim3(grid), dim3(kWarpsPerCta * 32), args, smem,
-                                         (cudaStream_t)stream);
+  const cudaError_t e = cudaLaunchKernel(k, dim3(grid), dim3(wavefront_block_threads(pk)), args,
+                                         smem, (cudaStream_t)stream);
   return e == cudaSuccess ? 0 : -2;
 }
 

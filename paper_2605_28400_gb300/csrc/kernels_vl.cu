@@ -1,28 +1,44 @@
 // kernels_vl.cu — instantiations of the two-cells-per-register score kernel (wavefront_vl.cuh):
-// 8 rows x 2 x 8 columns per lane (column tasks of 32 x 128 cells, 2 CTAs per SM) and 8 rows x
-// 2 x 4 columns per lane (tasks of 32 x 64 cells, 3 CTAs per SM).
+// 8 rows x 2 x 8 columns per lane (column tasks of 32 x 128 cells, 2 CTAs per SM), 8 rows x
+// 2 x 4 columns per lane (tasks of 32 x 64 cells, 3 CTAs per SM), and the 32 x 128 tasks with
+// the lane's sigma''(y,z) tile and 16-bit profiles in shared memory (2-warp CTAs, 5 per SM, or
+// 1-warp CTAs, 9 per SM).
 #include "wavefront_vl.cuh"
 
 namespace trioseq {
 
-const void* wavefront_vl(int nj, int nk) {
-  if (nj == 8 && nk == 16) return reinterpret_cast<const void*>(&wavefront_vl_kernel<8, 8>);
-  if (nj == 8 && nk == 8) return reinterpret_cast<const void*>(&wavefront_vl_kernel<8, 4>);
+// cs: sigma''(y,z) tile in shared memory, 2-warp CTAs (1, tile label "8x16s") or 1-warp CTAs
+// (2, "8x16t"); 0: in registers
+const void* wavefront_vl(int nj, int nk, int cs) {
+  if (nj == 8 && nk == 16) {
+    if (cs == 1) return reinterpret_cast<const void*>(&wavefront_vl_kernel<8, 8, 1>);
+    if (cs == 2) return reinterpret_cast<const void*>(&wavefront_vl_kernel<8, 8, 2>);
+    return reinterpret_cast<const void*>(&wavefront_vl_kernel<8, 8, 0>);
+  }
+  if (nj == 8 && nk == 8 && cs == 0)
+    return reinterpret_cast<const void*>(&wavefront_vl_kernel<8, 4, 0>);
   return nullptr;
 }
 
+int wavefront_vl_warps(int cs) {
+  return cs == 1 ? VlLaunch<8, 1>::warps : (cs == 2 ? VlLaunch<8, 2>::warps : kWarpsPerCta);
+}
+
 namespace {
-template <int NJ, int NH>
+template <int NJ, int NH, int CS>
 size_t vl_smem(int KP) {
   using G = VlGeom<NJ, NH>;
   const size_t sigN = (size_t)((KP * KP + 3) & ~3);
-  return (sigN + (size_t)kWarpsPerCta * (KP * (G::PJ + G::PK) + kRing * G::SLOT)) * sizeof(int);
+  const size_t prof = CS ? (size_t)KP * (G::PJ16 + G::PK16) / 2 : (size_t)KP * (G::PJ + G::PK);
+  const size_t cv = CS ? (size_t)32 * 4 * G::CVG : 0;
+  return (sigN + (size_t)VlLaunch<NH, CS>::warps * (prof + kRing * G::SLOT + cv)) * sizeof(int);
 }
 }  // namespace
 
-size_t wavefront_vl_smem_bytes(int nj, int nk, int KP) {
-  if (nj == 8 && nk == 16) return vl_smem<8, 8>(KP);
-  if (nj == 8 && nk == 8) return vl_smem<8, 4>(KP);
+size_t wavefront_vl_smem_bytes(int nj, int nk, int KP, int cs) {
+  if (nj == 8 && nk == 16)
+    return cs == 1 ? vl_smem<8, 8, 1>(KP) : (cs == 2 ? vl_smem<8, 8, 2>(KP) : vl_smem<8, 8, 0>(KP));
+  if (nj == 8 && nk == 8 && cs == 0) return vl_smem<8, 4, 0>(KP);
   return 0;
 }
 

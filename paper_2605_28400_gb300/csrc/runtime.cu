@@ -17,6 +17,7 @@
 #include <chrono>
 #include <condition_variable>
 #include <cstdlib>
+#include <cstdio>
 #include <cstring>
 #include <deque>
 #include <map>
@@ -350,7 +351,7 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
   // own candidate runs, work it cannot take runs on the int32 8x8 kernel instead.
   if (bt->var.vl) {
     bool ok_vl = !tb && plan->atype == kGlobal && plan->sig2_nonneg && plan->max_abs_sig2 <= 33 &&
-                 wavefront_vl(bt->var.nj, bt->var.nk) != nullptr;
+                 wavefront_vl(bt->var.nj, bt->var.nk, bt->var.vl - 1) != nullptr;
     if (ok_vl) {
       const int wj = kPR * bt->var.nj, wk = kPC * bt->var.nk;
       double rec = 0;  // int32 boundary records of all triplets: (a+1) x tasks x (WK+4 + WJ)
@@ -462,7 +463,7 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
   std::vector<std::pair<int32_t, int32_t>> units;  // (low-half triplet, high-half triplet or -1)
   bt->packed = 0;
   const bool vl = bt->var.vl != 0;  // admitted above
-  if (vl) bt->packed = 3;
+  if (vl) bt->packed = 2 + bt->var.vl;  // 3: registers; 4, 5: sigma'' tile in shared memory
   const int pmode = plan->sig2_nonneg ? 2 : 1;
   if (!vl && !tb && plan->atype == kGlobal && plan->packed16 && n >= 2 &&
       wavefront_packed(NJ, NK, pmode) != nullptr) {
@@ -644,7 +645,7 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
   off = align_up(off + sizeof(int32_t) * std::max<size_t>(bt->row_cap.size(), 1), 256);
   bt->inputs_bytes = off;
   // launch shape
-  bt->smem = bt->packed == 3 ? wavefront_vl_smem_bytes(NJ, NK, plan->KP)
+  bt->smem = bt->packed >= 3 ? wavefront_vl_smem_bytes(NJ, NK, plan->KP, bt->packed - 3)
                              : wavefront_smem_bytes(NJ, NK, plan->KP, bt->packed != 0);
   int bpm = 0;
   if (wavefront_occupancy(NJ, NK, tb, plan->atype, bt->packed, bt->slab > 0, bt->smem, &bpm) !=
@@ -1076,8 +1077,10 @@ trioseq_status trioseq_plan(const trioseq_scoring* sc, uint32_t max_len_hint, ui
       if (!end || *end != 'x') return;
       char* end2 = nullptr;
       const long ck = std::strtol(end + 1, &end2, 10);
-      // "8x16" and a trailing 'v' ("8x8v") select the two-cells-per-register kernel
-      const int two = (ck == 16 || (end2 && *end2 == 'v')) ? 1 : 0;
+      // "8x16" and a trailing 'v' ("8x8v") select the two-cells-per-register kernel; a trailing
+      // 's' or 't' ("8x16s", "8x16t") its variants with the sigma''(y,z) tile in shared memory
+      const char sfx = end2 ? *end2 : 0;
+      const int two = sfx == 's' ? 2 : (sfx == 't' ? 3 : ((ck == 16 || sfx == 'v') ? 1 : 0));
       if (rj > 0 && rj <= 16 && ck > 0 && ck <= 32) *out = Variant{(int)rj, (int)ck, two};
     };
     parse_tile(std::getenv("TRIOSEQ_SCORE_TILE"), &plan->score_variant);
@@ -1240,6 +1243,30 @@ trioseq_status trioseq_batch_packing(trioseq_batch_t bt, int32_t* per_word) {
   });
 }
 
+trioseq_status trioseq_batch_kernel(trioseq_batch_t bt, char* name, size_t cap) {
+  return no_throw([&]() -> trioseq_status {
+    if (!bt || !name || cap == 0) return TRIOSEQ_EINVAL;
+    const bool tb = bt->mode == TRIOSEQ_WITH_TRACEBACK;
+    const int at = bt->plan->atype;
+    const char* type = at == kLocal ? "local" : (at == kSemiGlobal ? "semiglobal" : "global");
+    const int nj = bt->var.nj, nk = bt->var.nk;
+    char buf[160];
+    if (bt->packed >= 3)
+      std::snprintf(buf, sizeof buf, "wavefront_vl_kernel<%d,%d,%d> tile %dx%d%s", nj, nk / 2,
+                    bt->packed - 3, nj, nk,
+                    bt->packed == 4 ? "s" : (bt->packed == 5 ? "t" : (nk == 16 ? "" : "v")));
+    else if (bt->packed)
+      std::snprintf(buf, sizeof buf, "wavefront_kernel<%d,%d,score,global,%s> tile %dx%d", nj, nk,
+                    bt->packed == 2 ? "two triplets per register, biased" :
+                                      "two triplets per register, signed", nj, nk);
+    else
+      std::snprintf(buf, sizeof buf, "wavefront_kernel<%d,%d,%s,%s%s> tile %dx%d", nj, nk,
+                    tb ? "traceback" : "score", type, bt->slab ? ",slab" : "", nj, nk);
+    std::snprintf(name, cap, "%s", buf);
+    return std::strlen(buf) < cap ? TRIOSEQ_OK : TRIOSEQ_EINVAL;
+  });
+}
+
 trioseq_status trioseq_batch_profile(trioseq_batch_t bt, int32_t enable) {
   return no_throw([&]() -> trioseq_status {
     if (!bt) return TRIOSEQ_EINVAL;
@@ -1276,7 +1303,8 @@ trioseq_status trioseq_plan_autotune(trioseq_plan_t plan, const trioseq_triplet*
     DeviceGuard g(plan->device);
     // candidate tiles per mode; 8x4 exists for traceback keys only
     // 8x16 and 8x8 with vl: two cells of one triplet per register
-    static const Variant kScoreTiles[] = {{8, 8}, {4, 8}, {4, 4}, {8, 16, 1}, {8, 8, 1}};
+    static const Variant kScoreTiles[] = {{8, 8},    {4, 8},    {4, 4},   {8, 16, 1},
+                                          {8, 8, 1}, {8, 16, 2}, {8, 16, 3}};
     static const Variant kTbTiles[] = {{8, 8}, {4, 8}, {4, 4}, {8, 4}};
     static const int kTI[] = {2, 4, 8, 16, 32};
     const bool tb_mode = mode == TRIOSEQ_WITH_TRACEBACK;

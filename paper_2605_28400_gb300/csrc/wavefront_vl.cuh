@@ -47,11 +47,41 @@ struct VlGeom {
   static constexpr int PKR = NJ / 4;                  // 16-byte pieces per lane row (k-records)
   static constexpr int NPIECE = kPC * (PL + PH) + kPR * PKR;
   static constexpr int NPL = (NPIECE + 31) / 32;      // pieces per lane
+  // Shared-memory variant (CS): 16-bit profile rows padded to a multiple of 8 halves (16-byte
+  // aligned rows) and the lane's sigma''(y,z) tile in shared memory.
+  static constexpr int PJ16 = WJ + 8, PK16 = WK + 8;  // halves per profile row
+  static constexpr int CVG = NJ * NH / 4;             // 16-byte groups of a lane's sigma'' tile
 };
 
+// Launch shape of a variant: CS = 0 keeps the lane's sigma''(y,z) tile in registers (4 warps per
+// CTA; 2 or 3 CTAs per SM, register-bound); CS = 1 and 2 keep it and 16-bit profiles in shared
+// memory, which frees 64 registers, with small CTAs so that occupancy rises in finer steps:
+// CS = 1 runs 2-warp CTAs, 5 per SM (10 warps, <= 200 registers), CS = 2 1-warp CTAs, 9 per SM
+// (9 warps, <= 224 registers).
+template <int NH, int CS>
+struct VlLaunch {
+  static constexpr int warps = CS == 1 ? 2 : (CS == 2 ? 1 : kWarpsPerCta);
+  static constexpr int min_blocks = CS == 1 ? 5 : (CS == 2 ? 9 : (NH >= 8 ? 2 : 3));
+  static constexpr int regs = 65536 / (warps * 32 * min_blocks) / 8 * 8;
+  static constexpr int max_regs = regs > 255 ? 255 : regs;
+};
+
+// Position of tile cell (pp, qq) in anti-diagonal order (diagonal pp + qq ascending, pp
+// ascending within it): the order pass 2 visits the cells in, and pass 1 in reverse.
 template <int NJ, int NH>
-__global__ void __launch_bounds__(kWarpsPerCta * 32, (NH >= 8 ? 2 : 3))
-    wavefront_vl_kernel(const WaveParams p) {
+__host__ __device__ constexpr int vl_diag_index(int pp, int qq) {
+  int e = 0;
+  for (int dg = 0; dg < pp + qq; ++dg) {
+    const int lo = dg - (NH - 1) > 0 ? dg - (NH - 1) : 0, hi = dg < NJ - 1 ? dg : NJ - 1;
+    e += hi - lo + 1;
+  }
+  const int lo = pp + qq - (NH - 1) > 0 ? pp + qq - (NH - 1) : 0;
+  return e + (pp - lo);
+}
+
+template <int NJ, int NH, int CS>
+__global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
+    __maxnreg__((VlLaunch<NH, CS>::max_regs)) wavefront_vl_kernel(const WaveParams p) {
   using G = VlGeom<NJ, NH>;
   static_assert(NJ % 4 == 0 && NH % 4 == 0, "tile sides must be multiples of 4");
   constexpr int NK = G::NK, WJ = G::WJ, WK = G::WK;
@@ -63,9 +93,16 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, (NH >= 8 ? 2 : 3))
   const int sigN = (KP * KP + 3) & ~3;
   int* sig = smem;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int* profJ = smem + sigN + warp * (KP * (G::PJ + G::PK) + kRing * G::SLOT);
-  int* profK = profJ + KP * G::PJ;
-  int* ring = profK + KP * G::PK;
+  // per warp: profiles (32-bit, or 16-bit with CS), the staging ring, and with CS the sigma''
+  // tiles of the warp's lanes ([group][lane][4] ints, conflict-free 16-byte loads)
+  const int prof_ints = CS ? KP * (G::PJ16 + G::PK16) / 2 : KP * (G::PJ + G::PK);
+  const int warp_ints = prof_ints + kRing * G::SLOT + (CS ? 32 * 4 * G::CVG : 0);
+  int* profJ = smem + sigN + warp * warp_ints;
+  int* profK = profJ + (CS ? KP * G::PJ16 / 2 : KP * G::PJ);
+  int* ring = profJ + prof_ints;
+  int4* cvs = reinterpret_cast<int4*>(ring + kRing * G::SLOT);  // CS only
+  unsigned short* profJ16 = reinterpret_cast<unsigned short*>(profJ);
+  unsigned short* profK16 = reinterpret_cast<unsigned short*>(profK);
   for (int e = threadIdx.x; e < KP * KP; e += blockDim.x) sig[e] = p.sig[e];
   __syncthreads();
   const int r = lane >> 3, lc = lane & 7;
@@ -134,15 +171,22 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, (NH >= 8 ? 2 : 3))
     for (int e = lane; e < KP * WJ; e += 32) {
       const int x = e / WJ, jl = e - x * WJ, j = J * WJ + jl;
       const int y = (j >= 1 && j <= b) ? (int)S1[j - 1] : VIRT;
-      profJ[x * G::PJ + jl] = sig[x * KP + y];
+      if (CS)
+        profJ16[x * G::PJ16 + jl] = (unsigned short)sig[x * KP + y];
+      else
+        profJ[x * G::PJ + jl] = sig[x * KP + y];
     }
     for (int e = lane; e < KP * WK; e += 32) {
       const int x = e / WK, kl = e - x * WK, k = K * WK + kl;
       const int z = (k >= 1 && k <= c) ? (int)S2[k - 1] : VIRT;
-      profK[x * G::PK + kl] = sig[x * KP + z];
+      if (CS)
+        profK16[x * G::PK16 + kl] = (unsigned short)sig[x * KP + z];
+      else
+        profK[x * G::PK + kl] = sig[x * KP + z];
     }
-    // sigma''(y_j, z_k) for both halves (left and right NH columns), packed, for the whole task
-    int Cv[NJ][NH];
+    // sigma''(y_j, z_k) for both halves (left and right NH columns), packed, for the whole task:
+    // in registers, or (CS) in shared memory in anti-diagonal order, read as the passes go
+    int Cv[CS ? 1 : NJ][CS ? 1 : NH];
     {
       int yo[NJ];
 #pragma unroll
@@ -156,8 +200,15 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, (NH >= 8 ? 2 : 3))
         const int zl = (kl >= 1 && kl <= c) ? (int)S2[kl - 1] : VIRT;
         const int zh = (kh >= 1 && kh <= c) ? (int)S2[kh - 1] : VIRT;
 #pragma unroll
-        for (int pp = 0; pp < NJ; ++pp)
-          Cv[pp][qq] = (int)__byte_perm(sig[yo[pp] + zl], sig[yo[pp] + zh], 0x5410);
+        for (int pp = 0; pp < NJ; ++pp) {
+          const int v = (int)__byte_perm(sig[yo[pp] + zl], sig[yo[pp] + zh], 0x5410);
+          if constexpr (CS) {
+            const int e = vl_diag_index<NJ, NH>(pp, qq);
+            reinterpret_cast<int*>(cvs + (e >> 2) * 32 + lane)[e & 3] = v;
+          } else {
+            Cv[pp][qq] = v;
+          }
+        }
       }
     }
     __syncwarp();
@@ -326,7 +377,34 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, (NH >= 8 ? 2 : 3))
       const bool active = s >= 0 && s <= a + 1;
       if (active) {
         int A[NJ], Bq[NH];
-        {
+        if constexpr (CS) {
+          // 16-bit profiles: one 16-byte load holds 8 values of a half; a PRMT pairs the low
+          // half's value with the high half's
+          const int4* pl = reinterpret_cast<const int4*>(profJ16 + xl * G::PJ16 + r * NJ);
+          const int4* ph = reinterpret_cast<const int4*>(profJ16 + xh * G::PJ16 + r * NJ);
+#pragma unroll
+          for (int p8 = 0; p8 < NJ / 8; ++p8) {
+            const int4 u = pl[p8], v = ph[p8];
+            const int uu[4] = {u.x, u.y, u.z, u.w}, vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+              A[8 * p8 + 2 * w] = (int)__byte_perm(uu[w], vv[w], 0x5410);
+              A[8 * p8 + 2 * w + 1] = (int)__byte_perm(uu[w], vv[w], 0x7632);
+            }
+          }
+          const int4* ql = reinterpret_cast<const int4*>(profK16 + xl * G::PK16 + lc * NK);
+          const int4* qh = reinterpret_cast<const int4*>(profK16 + xh * G::PK16 + lc * NK + NH);
+#pragma unroll
+          for (int q8 = 0; q8 < NH / 8; ++q8) {
+            const int4 u = ql[q8], v = qh[q8];
+            const int uu[4] = {u.x, u.y, u.z, u.w}, vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+              Bq[8 * q8 + 2 * w] = (int)__byte_perm(uu[w], vv[w], 0x5410);
+              Bq[8 * q8 + 2 * w + 1] = (int)__byte_perm(uu[w], vv[w], 0x7632);
+            }
+          }
+        } else {
           const int4* pl = reinterpret_cast<const int4*>(profJ + xl * G::PJ + r * NJ);
           const int4* ph = reinterpret_cast<const int4*>(profJ + xh * G::PJ + r * NJ);
 #pragma unroll
@@ -348,6 +426,15 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, (NH >= 8 ? 2 : 3))
             Bq[4 * q4 + 3] = (int)__byte_perm(u.w, v.w, 0x5410);
           }
         }
+        // sigma''(y, z) of tile cell (pp, qq): a register, or (CS) a shared-memory read
+        const auto cv = [&](const int pp, const int qq) -> unsigned {
+          if constexpr (CS) {
+            const int e = vl_diag_index<NJ, NH>(pp, qq);
+            return (unsigned)reinterpret_cast<const int*>(cvs + (e >> 2) * 32 + lane)[e & 3];
+          } else {
+            return (unsigned)Cv[pp][qq];
+          }
+        };
         // Two passes in place, as in the biased packed mode of wavefront_kernel.
         auto pass1 = [&](const int pp, const int qq) {
           const int Pd = (pp == 0) ? rowPrev[qq] : (qq == 0 ? colPrev[pp - 1] : P[pp - 1][qq - 1]);
@@ -357,14 +444,13 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, (NH >= 8 ? 2 : 3))
           const unsigned x2 = (unsigned)mad_lo(Bq[qq], p.one, mad_lo(A[pp], p.one, Pd));
           unsigned e = __viaddmax_u16x2((unsigned)Pxy, (unsigned)A[pp], (unsigned)Sx);
           e = __viaddmax_u16x2((unsigned)Pxz, (unsigned)Bq[qq], e);
-          P[pp][qq] = (int)__viaddmax_u16x2(x2, (unsigned)Cv[pp][qq], e);
+          P[pp][qq] = (int)__viaddmax_u16x2(x2, cv(pp, qq), e);
         };
         auto pass2 = [&](const int pp, const int qq) {
           const int Myz = (pp == 0) ? rowCur[qq] : (qq == 0 ? colCur[pp - 1] : P[pp - 1][qq - 1]);
           const int Sy = (pp == 0) ? rowCur[qq + 1] : P[pp - 1][qq];
           const int Sz = (qq == 0) ? colCur[pp] : P[pp][qq - 1];
-          const unsigned q =
-              __viaddmax_u16x2((unsigned)Myz, (unsigned)Cv[pp][qq], (unsigned)P[pp][qq]);
+          const unsigned q = __viaddmax_u16x2((unsigned)Myz, cv(pp, qq), (unsigned)P[pp][qq]);
           P[pp][qq] = (int)__vimax3_u16x2(q, (unsigned)Sy, (unsigned)Sz);
         };
 #pragma unroll

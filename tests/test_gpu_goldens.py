@@ -2,8 +2,9 @@
 tests/golden/make_goldens.py from the oracle alone).
 
 - Config 3, the protein triplet with ancestor length 4000 (about 6.4e10 cells): its score on
-  every score kernel that can take it: the two two-cells-per-register tiles (8x16 and 8x8v)
-  and the int32 8x8 kernel, through a device-resident batch and through trioseq_align_batch.
+  every score kernel that can take it: the two-cells-per-register tiles (8x16, 8x8v, and 8x16s
+  and 8x16t with the sigma'' tile in shared memory) and the int32 8x8 kernel, through a
+  device-resident batch and through trioseq_align_batch.
 - Config 2, all 4,096 related DNA triplets: every score on the packed int16x2 path (the
   default), on the int32 kernel, and on the two-cells-per-register kernel.
 - Config 4, the first 200 requests of the serving stream (lognormal lengths up to 2000, 30%
@@ -51,6 +52,8 @@ def config3():
 
 
 @pytest.mark.parametrize("tile,want_tile,want_packing", [("8x8v", (8, 8), 2), ("8x16", (8, 16), 2),
+                                                         ("8x16s", (8, 16), 2),
+                                                         ("8x16t", (8, 16), 2),
                                                          ("8x8", (8, 8), 1)])
 def test_config3_full_size_equals_oracle(config3, tile, want_tile, want_packing):
     w, want = config3

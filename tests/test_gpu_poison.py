@@ -57,9 +57,11 @@ def _strs(trips, sc):
                                  {"TRIOSEQ_SCORE_TILE": "4x4", "TRIOSEQ_PACKED": 0},
                                  {"TRIOSEQ_SCORE_TILE": "8x8"},
                                  {"TRIOSEQ_SCORE_TILE": "8x16"},
-                                 {"TRIOSEQ_SCORE_TILE": "8x8v"}],
+                                 {"TRIOSEQ_SCORE_TILE": "8x8v"},
+                                 {"TRIOSEQ_SCORE_TILE": "8x16s"},
+                                 {"TRIOSEQ_SCORE_TILE": "8x16t"}],
                          ids=["int32-8x8", "int32-4x8", "int32-4x4", "packed-8x8", "vl-8x16",
-                              "vl-8x8v"])
+                              "vl-8x8v", "vl-8x16s", "vl-8x16t"])
 def test_score_kernels_poisoned(sc, env):
     trips = _trips(61, sc)
     want = oracle.align_many(trips, sc.sub, sc.gap).tolist()

@@ -22,8 +22,10 @@ pytestmark = pytest.mark.gpu
 
 DNA = synth.dna_scoring()
 PROT = synth.protein_scoring(1003)
-# the two instantiations: 8 x (8+8) cells per lane (32 x 128 tasks) and 8 x (4+4) (32 x 64 tasks)
-VL_TILES = ["8x16", "8x8v"]
+# the instantiations: 8 x (8+8) cells per lane (32 x 128 tasks) and 8 x (4+4) (32 x 64 tasks)
+# with the sigma''(y,z) tile in registers, and 8 x (8+8) with it in shared memory (2-warp CTAs,
+# "8x16s", or 1-warp CTAs, "8x16t")
+VL_TILES = ["8x16", "8x8v", "8x16s", "8x16t"]
 
 
 def _plan(sc, tile="8x16"):
@@ -59,7 +61,8 @@ def test_vl_is_selected_for_nonnegative_schemes(tile):
         bt = B.trioseq_batch_create(plan, [["ACGT" * 20, "ACG" * 20, "AGT" * 20]])
         try:
             info = B.trioseq_batch_info(bt)
-            assert info["tile"] == ((8, 16) if tile == "8x16" else (8, 8))
+            assert info["tile"] == ((8, 8) if tile == "8x8v" else (8, 16))
+            assert info["tile_label"] == tile and info["kernel"].startswith("wavefront_vl_kernel")
             assert info["packing"] == 2
         finally:
             B.trioseq_batch_destroy(bt)
