@@ -3,7 +3,8 @@
 Python access to ``oracle.cpp``: a plain, slow CPU implementation of exact 3-way alignment
 (Eq. 1 with the sum-of-pairs column score and the global initialisation of Sec. II, int64
 arithmetic, first-maximal-move tie-break in Eq. 1's listing order), plus the scores of the
-semi-global and local alignment types of Sec. II.
+semi-global and local alignment types of Sec. II, and the sum-of-pairs score with affine gaps
+(natural gap costs; the paper's future work, Sec. VI) with its textbook pairwise counterpart.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may import
 this package. The product library never loads it, and it shares no code with the CUDA path.
@@ -72,6 +73,13 @@ def _load():
                                              ctypes.c_int, i64p, u8p, ctypes.c_int64, i64p, i32p,
                                              i32p]
         lib.oracle_align_type_tb.restype = ctypes.c_int
+        lib.oracle_align_affine.argtypes = [u8p, ctypes.c_int, u8p, ctypes.c_int, u8p,
+                                            ctypes.c_int, ctypes.c_int, i32p, ctypes.c_int32,
+                                            ctypes.c_int32, i64p, u8p, ctypes.c_int64, i64p]
+        lib.oracle_align_affine.restype = ctypes.c_int
+        lib.oracle_gotoh2.argtypes = [u8p, ctypes.c_int, u8p, ctypes.c_int, ctypes.c_int, i32p,
+                                      ctypes.c_int32, ctypes.c_int32, i64p]
+        lib.oracle_gotoh2.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -218,3 +226,46 @@ def align_type_tb(s0, s1, s2, sub, gap: int, kind: int):
         raise RuntimeError(f"oracle_align_type_tb failed ({rc})")
     r = rows.reshape(3, cap)[:, : L.value].copy()
     return int(score.value), r, tuple(beg), tuple(end)
+
+
+def align_affine(s0, s1, s2, sub, gap: int, gap_open: int, traceback: bool = False):
+    """Global 3-way score under affine gaps with natural gap costs: the sum over the three pairs
+    of the induced pairwise alignment's score (columns with a gap in both sequences of the pair
+    deleted), sigma per residue pair, `gap` per residue against a gap and `gap_open` per maximal
+    gap run. With gap_open = 0 it equals align(). With ``traceback`` also the (3, L) rows.
+    (The paper names affine gaps as future work, Sec. VI; this definition is the build's reading.)"""
+    lib = _load()
+    n = [len(s0), len(s1), len(s2)]
+    a0, a1, a2 = _u8(s0), _u8(s1), _u8(s2)
+    sm, K = _sub(sub)
+    score = ctypes.c_int64(0)
+    if traceback:
+        cap = max(1, sum(n))
+        rows = np.zeros(3 * cap, dtype=np.uint8)
+        L = ctypes.c_int64(0)
+        rc = lib.oracle_align_affine(_ptr(a0, ctypes.c_uint8), n[0], _ptr(a1, ctypes.c_uint8),
+                                     n[1], _ptr(a2, ctypes.c_uint8), n[2], K,
+                                     _ptr(sm, ctypes.c_int32), int(gap), int(gap_open),
+                                     ctypes.byref(score), _ptr(rows, ctypes.c_uint8), cap,
+                                     ctypes.byref(L))
+        if rc:
+            raise RuntimeError(f"oracle_align_affine failed ({rc})")
+        return int(score.value), rows.reshape(3, cap)[:, : L.value].copy()
+    rc = lib.oracle_align_affine(_ptr(a0, ctypes.c_uint8), n[0], _ptr(a1, ctypes.c_uint8), n[1],
+                                 _ptr(a2, ctypes.c_uint8), n[2], K, _ptr(sm, ctypes.c_int32),
+                                 int(gap), int(gap_open), ctypes.byref(score), None, 0, None)
+    if rc:
+        raise RuntimeError(f"oracle_align_affine failed ({rc})")
+    return int(score.value)
+
+
+def gotoh2(x, y, sub, gap: int, gap_open: int) -> int:
+    """Textbook pairwise alignment score with affine gaps (a gap run of length l scores
+    gap_open + l * gap)."""
+    lib = _load()
+    ax, ay = _u8(x), _u8(y)
+    sm, K = _sub(sub)
+    out = ctypes.c_int64(0)
+    lib.oracle_gotoh2(_ptr(ax, ctypes.c_uint8), len(x), _ptr(ay, ctypes.c_uint8), len(y), K,
+                      _ptr(sm, ctypes.c_int32), int(gap), int(gap_open), ctypes.byref(out))
+    return int(out.value)

@@ -305,6 +305,166 @@ int oracle_align_type_tb(const uint8_t* s0, int a, const uint8_t* s1, int b, con
   return 0;
 }
 
+// ---------------------------------------------------------------------------------------------
+// Affine gaps (the paper's future work, Sec. VI; no definition is given there). Reading: the
+// sum-of-pairs score with natural gap costs (Altschul 1989) in Gotoh's affine form (Gotoh 1982,
+// 1986): the score of a 3-way alignment is the sum, over the three pairs (p, q), of the score of
+// the pairwise alignment it induces on (p, q) once the columns with a gap in both p and q are
+// deleted. That pairwise score is sigma(x, y) per residue pair, alpha per residue aligned to a gap
+// (the linear term of Sec. II), and gamma (gap_open, <= 0) once per maximal run of consecutive
+// induced columns with a gap in the same sequence. With gamma = 0 it is Eq. 1's score.
+//
+// Dynamic program. The state of an alignment prefix records, for each pair, the kind of its last
+// induced column: 0 = both residues (or no column yet), 1 = gap in the pair's first sequence,
+// 2 = gap in its second. A new column of move m leaves a pair's state unchanged where m has a gap
+// in both sequences of the pair, and otherwise sets it; it opens a run (gamma) where it has a gap
+// in one sequence of the pair and the pair's state is not already a gap in that sequence.
+// F[i][j][k][s] = best score of the prefixes ending in state s; F[0][0][0][all zero] = 0.
+namespace {
+
+constexpr int kPairs[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+constexpr int64_t kNoState = INT64_MIN / 4;  // F of a state no prefix ends in
+
+inline int state_index(const int st[3]) { return st[0] * 9 + st[1] * 3 + st[2]; }
+
+// Column m (residues x, y, z or -1 for a gap) appended to state `from`: its score and new state.
+int64_t affine_step(const Scoring& sc, int64_t gamma, int from, const int v[3], int* to) {
+  int st[3] = {from / 9, (from / 3) % 3, from % 3};
+  int64_t cost = 0;
+  for (int q = 0; q < 3; q++) {
+    const int p0 = kPairs[q][0], p1 = kPairs[q][1];
+    const bool r0 = v[p0] >= 0, r1 = v[p1] >= 0;
+    if (!r0 && !r1) continue;  // deleted from this pair's induced alignment
+    if (r0 && r1) {
+      cost += sc.sub[v[p0] * sc.K + v[p1]];
+      st[q] = 0;
+    } else {
+      const int kind = r0 ? 2 : 1;  // 1: gap in p0, 2: gap in p1
+      cost += sc.gap + (st[q] == kind ? 0 : gamma);
+      st[q] = kind;
+    }
+  }
+  *to = state_index(st);
+  return cost;
+}
+
+}  // namespace
+
+// Exact 3-way global alignment score under affine gaps with natural gap costs (above).
+//   gap: alpha (per residue aligned to a gap), gap_open: gamma (per maximal gap run of a pair).
+//   If rows != nullptr the alignment is emitted as in oracle_align (cap >= a+b+c); the end state
+//   is the first maximal state in index order, and the walk back takes, at each (cell, state), the
+//   first maximal (move in Eq. 1's listing order, previous state in index order).
+// Returns 0, -1 (bad arguments) or -2 (allocation failure).
+int oracle_align_affine(const uint8_t* s0, int a, const uint8_t* s1, int b, const uint8_t* s2,
+                        int c, int K, const int32_t* sub, int32_t gap, int32_t gap_open,
+                        int64_t* score_out, uint8_t* rows, int64_t cap, int64_t* len_out) {
+  if (a < 0 || b < 0 || c < 0 || K <= 0 || !sub || !score_out) return -1;
+  if (rows && (cap < (int64_t)a + b + c || !len_out)) return -1;
+  Scoring sc{K, sub, gap};
+  const int64_t C = c + 1, plane = (int64_t)(b + 1) * C;
+  const bool want_tb = rows != nullptr;
+  // traceback: per (cell, state) the winning (move * 27 + previous state), 255 = none
+  std::vector<uint16_t> from;
+  try {
+    if (want_tb) from.assign((size_t)(a + 1) * (size_t)plane * 27, 0xFFFF);
+  } catch (...) {
+    return -2;
+  }
+  std::vector<int64_t> prev(plane * 27, kNoState), cur(plane * 27, kNoState);
+  for (int i = 0; i <= a; i++) {
+    for (int j = 0; j <= b; j++) {
+      for (int k = 0; k <= c; k++) {
+        int64_t* F = &cur[((int64_t)j * C + k) * 27];
+        for (int s = 0; s < 27; s++) F[s] = kNoState;
+        if (i == 0 && j == 0 && k == 0) {
+          F[0] = 0;
+          continue;
+        }
+        for (int m = 0; m < 7; m++) {
+          const int di = kMoves[m][0], dj = kMoves[m][1], dk = kMoves[m][2];
+          if (i - di < 0 || j - dj < 0 || k - dk < 0) continue;
+          const int64_t* G = &(di ? prev : cur)[((int64_t)(j - dj) * C + (k - dk)) * 27];
+          const int v[3] = {di ? (int)s0[i - 1] : -1, dj ? (int)s1[j - 1] : -1,
+                            dk ? (int)s2[k - 1] : -1};
+          for (int s = 0; s < 27; s++) {
+            if (G[s] == kNoState) continue;
+            int to = 0;
+            const int64_t cand = G[s] + affine_step(sc, gap_open, s, v, &to);
+            if (cand > F[to]) {  // strict: the first maximal (move, state) is kept
+              F[to] = cand;
+              if (want_tb)
+                from[((size_t)i * plane + (size_t)j * C + k) * 27 + to] = (uint16_t)(m * 27 + s);
+            }
+          }
+        }
+      }
+    }
+    std::swap(prev, cur);
+  }
+  const int64_t* E = &prev[((int64_t)b * C + c) * 27];
+  int best_s = 0;
+  for (int s = 1; s < 27; s++)
+    if (E[s] > E[best_s]) best_s = s;
+  *score_out = E[best_s];
+  if (!want_tb) return 0;
+  std::vector<uint8_t> r0, r1, r2;
+  int i = a, j = b, k = c, s = best_s;
+  while (i > 0 || j > 0 || k > 0) {
+    const uint16_t f = from[((size_t)i * plane + (size_t)j * C + k) * 27 + s];
+    if (f == 0xFFFF) return -1;  // cannot happen for a reachable state
+    const int m = f / 27, ps = f % 27;
+    const int di = kMoves[m][0], dj = kMoves[m][1], dk = kMoves[m][2];
+    r0.push_back(di ? s0[i - 1] : ORACLE_GAP);
+    r1.push_back(dj ? s1[j - 1] : ORACLE_GAP);
+    r2.push_back(dk ? s2[k - 1] : ORACLE_GAP);
+    i -= di;
+    j -= dj;
+    k -= dk;
+    s = ps;
+  }
+  const int64_t L = (int64_t)r0.size();
+  for (int64_t t = 0; t < L; t++) {
+    rows[t] = r0[L - 1 - t];
+    rows[cap + t] = r1[L - 1 - t];
+    rows[2 * cap + t] = r2[L - 1 - t];
+  }
+  *len_out = L;
+  return 0;
+}
+
+// Textbook pairwise alignment with affine gaps (Gotoh 1982): three matrices (ending in a residue
+// pair, in a gap in x, in a gap in y); a gap run of length l scores gap_open + l * gap. Used by the
+// affine oracle's pins (one-empty reduction, pairwise upper bound).
+int oracle_gotoh2(const uint8_t* x, int a, const uint8_t* y, int b, int K, const int32_t* sub,
+                  int32_t gap, int32_t gap_open, int64_t* score_out) {
+  if (a < 0 || b < 0 || !score_out) return -1;
+  const int64_t NEG = INT64_MIN / 4;
+  std::vector<int64_t> Mp(b + 1, NEG), Xp(b + 1, NEG), Yp(b + 1, NEG);
+  std::vector<int64_t> Mc(b + 1), Xc(b + 1), Yc(b + 1);
+  // row 0: M = 0 at (0,0); a gap in x (y consumed) along j
+  Mp[0] = 0;
+  for (int j = 1; j <= b; j++) Xp[j] = (int64_t)gap_open + (int64_t)j * gap;
+  for (int i = 1; i <= a; i++) {
+    Mc[0] = NEG;
+    Xc[0] = NEG;
+    Yc[0] = (int64_t)gap_open + (int64_t)i * gap;  // gap in y (x consumed)
+    for (int j = 1; j <= b; j++) {
+      const int64_t best_prev = std::max(Mp[j - 1], std::max(Xp[j - 1], Yp[j - 1]));
+      Mc[j] = best_prev + sub[x[i - 1] * K + y[j - 1]];
+      // gap in x: y[j-1] against a gap; extends a gap in x or opens one
+      Xc[j] = std::max(Xc[j - 1] + gap, std::max(Mc[j - 1], Yc[j - 1]) + gap_open + gap);
+      // gap in y: x[i-1] against a gap
+      Yc[j] = std::max(Yp[j] + gap, std::max(Mp[j], Xp[j]) + gap_open + gap);
+    }
+    std::swap(Mp, Mc);
+    std::swap(Xp, Xc);
+    std::swap(Yp, Yc);
+  }
+  *score_out = std::max(Mp[b], std::max(Xp[b], Yp[b]));
+  return 0;
+}
+
 // Sum-of-pairs score of a given 3-row alignment (Sec. II SOP summed over columns).
 // rows: 3 rows of length L at stride cap, gap = 255. Returns 0, or -1 on a residue >= K.
 int oracle_sp_score(const uint8_t* rows, int64_t L, int64_t cap, int K, const int32_t* sub,
