@@ -232,7 +232,7 @@ trioseq_status trioseq_batch_timing(trioseq_batch_t batch, float ms[2]);
  * of 32x64, 16x64 and 16x32 cells per warp, and in traceback mode also 8x4, 32x32 cells; in
  * score-only global mode with every sigma'' in [0, 33] also the two-cells-per-register tiles
  * 8x16 and 8x8v, 32x128 and 32x64 cells per warp) times
- * progress intervals of 2, 4, 8, 16 and 32 steps —
+ * progress intervals of 4, 8, 16 and 32 steps —
  * times two passes of each with CUDA events on the legacy default stream, and remembers the
  * fastest in the plan for batches of the same mode, the same single-or-batch kind, and the same
  * bit length of the longest sequence. Later batches of that class use it; other classes keep

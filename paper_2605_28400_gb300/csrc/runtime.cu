@@ -1306,7 +1306,7 @@ trioseq_status trioseq_plan_autotune(trioseq_plan_t plan, const trioseq_triplet*
     static const Variant kScoreTiles[] = {{8, 8},    {4, 8},    {4, 4},   {8, 16, 1},
                                           {8, 8, 1}, {8, 16, 2}, {8, 16, 3}};
     static const Variant kTbTiles[] = {{8, 8}, {4, 8}, {4, 4}, {8, 4}};
-    static const int kTI[] = {2, 4, 8, 16, 32};
+    static const int kTI[] = {4, 8, 16, 32};
     const bool tb_mode = mode == TRIOSEQ_WITH_TRACEBACK;
     const Variant* tiles = tb_mode ? kTbTiles : kScoreTiles;
     const size_t ntiles = tb_mode ? sizeof(kTbTiles) / sizeof(kTbTiles[0])

@@ -40,17 +40,6 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
   return v;
 }
 
-// Relaxed gpu-scope load of a progress flag, issued a step before its value is needed; when
-// the value is used, fence_acquire() completes the acquire pattern (relaxed load, then acquire
-// fence), so the record loads that follow see the producer's stores before its release.
-__device__ __forceinline__ int ld_relaxed(const int* p) {
-  int v;
-  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p));
-  return v;
-}
-
-__device__ __forceinline__ void fence_acquire() { asm volatile("fence.acquire.gpu;" ::: "memory"); }
-
 __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -405,7 +394,6 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
     const int* progK = p.progress + d.prog_base + (me - 1);
     int* progMe = p.progress + d.prog_base + me;
     int cachedJ = J > 0 ? 0 : 1 << 30, cachedK = K > 0 ? 0 : 1 << 30;  // warp-uniform
-    int pfJ = 0, pfK = 0;  // lane 0: producers' progress read one step ahead (relaxed loads)
     uint32_t* code_base = (TB && (!SLAB || p.codes))
                               ? p.codes + d.code_off + (int64_t)me * T * 32 * W + lane * W
                               : nullptr;
@@ -432,22 +420,13 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
         bool okl = true;
         int cj = cachedJ, ck = cachedK;
         if (lane == 0) {
-          // First the values read one step ago: a check they satisfy costs no L2 round trip.
-          const bool pre = pfJ > cj || pfK > ck;
-          cj = max(cj, pfJ);
-          ck = max(ck, pfK);
           if (cj < needJ) okl = wait_flag(progJ, needJ, &cj, p.wait_ns);
           if (okl && ck < needK) okl = wait_flag(progK, needK, &ck, p.wait_ns);
-          if (pre) fence_acquire();  // the prefetched values' acquire pattern
         }
         ok = __shfl_sync(kFull, okl, 0);
         cachedJ = __shfl_sync(kFull, cj, 0);
         cachedK = __shfl_sync(kFull, ck, 0);
         __syncwarp();
-      }
-      if (lane == 0) {  // progress for the next step's check
-        if (cachedJ < T) pfJ = ld_relaxed(progJ);
-        if (cachedK < T) pfK = ld_relaxed(progK);
       }
       const int sl = u - cp_delta;
       pf_u = u;

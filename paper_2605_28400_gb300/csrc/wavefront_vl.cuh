@@ -245,7 +245,6 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
     const int* progK = p.progress + d.prog_base + (me - 1);
     int* progMe = p.progress + d.prog_base + me;
     int cachedJ = J > 0 ? 0 : 1 << 30, cachedK = K > 0 ? 0 : 1 << 30;  // warp-uniform
-    int pfJ = 0, pfK = 0;  // lane 0: producers' progress read one step ahead (relaxed loads)
     bool ok = true;
 
     // Face pieces (absolute int32 records, kNeg where absent): loaded two steps ahead, parked one
@@ -260,22 +259,14 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
       if (cachedJ < needJ || cachedK < needK) {  // warp-uniform
         bool okl = true;
         int cj = cachedJ, ck = cachedK;
-        if (lane == 0) {  // prefetched values first, as in wavefront_kernel
-          const bool pre = pfJ > cj || pfK > ck;
-          cj = max(cj, pfJ);
-          ck = max(ck, pfK);
+        if (lane == 0) {
           if (cj < needJ) okl = wait_flag(progJ, needJ, &cj, p.wait_ns);
           if (okl && ck < needK) okl = wait_flag(progK, needK, &ck, p.wait_ns);
-          if (pre) fence_acquire();
         }
         ok = __shfl_sync(kFull, okl, 0);
         cachedJ = __shfl_sync(kFull, cj, 0);
         cachedK = __shfl_sync(kFull, ck, 0);
         __syncwarp();
-      }
-      if (lane == 0) {
-        if (cachedJ < T) pfJ = ld_relaxed(progJ);
-        if (cachedK < T) pfK = ld_relaxed(progK);
       }
       pf_u = u;
 #pragma unroll
