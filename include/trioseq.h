@@ -104,6 +104,21 @@ typedef struct trioseq_plan_s* trioseq_plan_t;
 trioseq_status trioseq_plan(const trioseq_scoring* scoring, uint32_t max_len_hint, uint32_t flags,
                             trioseq_plan_t* out);
 
+/* trioseq_plan_affine — a plan for the sum-of-pairs score with affine gaps. The paper names
+ * affine gaps as future work (Sec. VI) and gives no definition; this library reads them as
+ * natural gap costs (Altschul 1989) in Gotoh's affine form: each pair's induced pairwise
+ * alignment (the columns with a gap in both of its sequences deleted) scores sub[x][y] per
+ * residue pair, scoring->gap (alpha) per residue against a gap, and gap_open (gamma) once per
+ * maximal run of gaps in one of its sequences. gap_open = 0 gives the linear model of Sec. II.
+ * Arguments: scoring as for trioseq_plan; gap_open <= 0 (>= -2^20); flags must be
+ * TRIOSEQ_GLOBAL. The plan serves trioseq_align_batch and the device-resident batch calls in
+ * score-only mode (traceback: ENOTIMPL); trioseq_plan_autotune has nothing to choose. The
+ * kernel keeps 13 int32 states per cell and sweeps anti-diagonal planes (one CTA per triplet).
+ * Errors: EINVAL (as trioseq_plan, gap_open out of range, other flags), ENOMEM, ECUDA;
+ * EOVERFLOW at batch time when (3 max|sub| + 3|gap| + 3|gap_open|) * (a+b+c) >= 2^29. */
+trioseq_status trioseq_plan_affine(const trioseq_scoring* scoring, int32_t gap_open,
+                                   uint32_t flags, trioseq_plan_t* out);
+
 /* Release a plan and its device memory. Null is accepted. Destroy the plan's device-resident
  * batches and any server that names it first. The call waits for the plan's own last
  * trioseq_align_batch work only; it synchronises no other stream (a running server's included),

@@ -87,6 +87,7 @@ def load(build_if_missing: bool = True):
         "trioseq_plan_autotune": ([vp, ctypes.POINTER(Triplet), sz, u32, i32p, i32p, i32p], i32),
         "trioseq_batch_packing": ([vp, i32p], i32),
         "trioseq_batch_kernel": ([vp, ctypes.c_char_p, sz], i32),
+        "trioseq_plan_affine": ([ctypes.POINTER(Scoring), i32, u32, ctypes.POINTER(vp)], i32),
         "trioseq_batch_slabs": ([vp, i32p, i32p], i32),
         "trioseq_traceback_span": ([vp, sz, i32p, i32p], i32),
         "trioseq_batch_span": ([vp, sz, i32p, i32p], i32),
@@ -111,6 +112,7 @@ def exported_symbols() -> list[str]:
             "trioseq_plan_io_bytes", "trioseq_server_create", "trioseq_submit", "trioseq_poll",
             "trioseq_server_destroy", "trioseq_strerror", "trioseq_align_noalloc",
             "trioseq_plan_autotune", "trioseq_batch_packing", "trioseq_batch_kernel",
+            "trioseq_plan_affine",
             "trioseq_batch_slabs",
             "trioseq_traceback_span", "trioseq_batch_span", "trioseq_alu_rate",
             "trioseq_partition"]
@@ -211,6 +213,21 @@ def trioseq_plan(alphabet: str, sub, gap: int, flags: int = 0):
     sc = Scoring(alphabet.encode(), K, sub.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)), int(gap))
     h = ctypes.c_void_p()
     _check(lib.trioseq_plan(ctypes.byref(sc), 0, int(flags), ctypes.byref(h)), "trioseq_plan")
+    return h
+
+
+def trioseq_plan_affine(alphabet: str, sub, gap: int, gap_open: int, flags: int = 0):
+    """Plan for the sum-of-pairs score with affine gaps (natural gap costs): ``gap`` per residue
+    against a gap, ``gap_open`` per maximal gap run of a pair. Score only, global type."""
+    lib = load()
+    sub = np.ascontiguousarray(np.asarray(sub, dtype=np.int8))
+    K = len(alphabet)
+    if sub.shape != (K, K):
+        raise ValueError("substitution matrix must be K x K")
+    sc = Scoring(alphabet.encode(), K, sub.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)), int(gap))
+    h = ctypes.c_void_p()
+    _check(lib.trioseq_plan_affine(ctypes.byref(sc), int(gap_open), int(flags), ctypes.byref(h)),
+           "trioseq_plan_affine")
     return h
 
 

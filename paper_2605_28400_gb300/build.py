@@ -20,7 +20,8 @@ CSRC = os.path.join(HERE, "csrc")
 LIBDIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIBDIR, "libtrioseq.so")
 SOURCES = ["runtime.cu", "kernels.cu", "kernels_variants.cu", "kernels_packed.cu",
-           "kernels_slab.cu", "noalloc.cu", "alu_rate.cu", "kernels_vl.cu", "partition.cu"]
+           "kernels_slab.cu", "noalloc.cu", "alu_rate.cu", "kernels_vl.cu", "partition.cu",
+           "affine.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 _lock = threading.Lock()
 
