@@ -71,6 +71,13 @@ struct TripDesc {
   int32_t score_base;  // 2*alpha*(a+b+c)
   int32_t out_idx;     // index into the score output
   int32_t tb_idx;      // index among the batch's traceback triplets (-1: none)
+  // Two-cells-per-register kernel only: the i axis of every column block cut into nH sub-tasks
+  // of isub slices (the last one shorter), task (J, K, h) = Task{trip, J, K, h}, each with its
+  // own progress counter (prog_base + (h*nJ + J)*nK + K). Sub-task h starts from the plane of
+  // slice h*isub - 1 that sub-task h-1 of the same column left at plane_off + column*WJ*WK
+  // (int32, row-major in the block's (j, k)). nH = 1: the whole axis in one task.
+  int64_t plane_off;
+  int32_t nH, isub;
 };
 
 struct Task {
@@ -136,6 +143,24 @@ struct WalkParams {
   int32_t* scores;           // written from best64 for those types
   int32_t* span;             // per request: begin (i, j, k) and end (i, j, k) of the alignment
 };
+
+// Affine gaps (affine.cu): natural gap costs, 13 reachable states per cell, score only.
+constexpr int kAffineStates = 13;
+struct AffineParams {
+  const TripDesc* desc;
+  const Task* tasks;      // queue: one entry per triplet (Task.trip), largest cube first
+  int32_t n;
+  int32_t KP;
+  const int8_t* seq;
+  const int32_t* sub;     // KP x KP table of sigma (the virtual row and column unused)
+  int32_t gap, gap_open;  // alpha (per residue against a gap), gamma (per maximal gap run)
+  int32_t* planes;        // per CTA: 4 plane buffers of plane_cells * kAffineStates int32
+  int64_t plane_cells;    // (max b + 1) * (max c + 1) over the batch
+  int32_t* queue;         // zeroed before launch
+  int32_t* scores;
+};
+int affine_occupancy(int* blocks_per_sm);
+int launch_affine(const AffineParams& p, int grid, void* stream);
 
 // Host-side launchers implemented in kernels.cu. `at` is the alignment type (kGlobal, ...);
 // semi-global and local exist for score mode (tb = false) only, and their scores are

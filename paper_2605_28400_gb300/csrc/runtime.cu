@@ -15,6 +15,7 @@
 #include <array>
 #include <atomic>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstdlib>
 #include <cstdio>
@@ -212,12 +213,17 @@ struct trioseq_plan_s {
   int atype = kGlobal;             // alignment type of Sec. II (plan flags)
   int32_t max_abs_sig2 = 0;        // max |sigma''| over the extended table
   DevBuf sig_score, sig_tb;        // KP*KP int32 device tables
+  bool affine = false;             // trioseq_plan_affine: natural affine gap costs (affine.cu)
+  int32_t gap_open = 0;            // gamma, per maximal gap run of a pair
+  DevBuf sig_affine;               // KP*KP int32 table of sigma itself (affine model)
+  int32_t max_abs_sub = 0;         // max |sigma|
   Workspace ws;                    // workspace of trioseq_align_batch
   std::unique_ptr<trioseq_batch_s> last;  // last align_batch (traceback rows kept here)
   int TI = 8;
   int64_t wait_ns = 2000000000LL;  // 2 s without progress = give up
   bool test_wait_unset = false;    // test switch: first-wave warps wait on a flag nothing sets
   bool test_poison = false;        // test switch: boundary records start as a large garbage value
+  int isplit = 0;                  // TRIOSEQ_ISPLIT: forced sub-tasks along i (0 = chosen)
   bool graphs = true;              // trioseq_batch_run replays a captured CUDA graph
   bool packed16 = true;            // pair score-only global triplets in int16 halves if they fit
   bool sig2_nonneg = false;        // every sigma'' >= 0: the biased packed mode applies
@@ -266,6 +272,7 @@ struct trioseq_batch_s {
   size_t smem = 0;
   int TI = 8;  // progress-publication interval of this batch's launches
   int packed = 0;  // packed int16x2 mode (0: none, 1: signed, 2: biased): two triplets per task
+  int64_t affine_cells = 0;  // affine model: cells of the largest (j, k) plane
   // Slab mode (one triplet whose records, or codes, would not fit at once): the cube runs as
   // nslab launches of `slab` slices, chained through planes of plane_ints int32 each.
   int slab = 0, nslab = 0;
@@ -317,6 +324,54 @@ trioseq_status cuda_status(cudaError_t e) {
 int env_int(const char* name, int def) {
   const char* v = std::getenv(name);
   return v ? std::atoi(v) : def;
+}
+
+// Device layout of a batch's input block: residues | descriptors | slab descriptors | queue |
+// traceback tables.
+void layout_inputs(trioseq_batch_s* bt) {
+  size_t off = align_up(bt->seq_bytes, 256);
+  bt->off_desc = off;
+  off = align_up(off + sizeof(TripDesc) * std::max<size_t>(bt->n, 1), 256);
+  bt->off_slab = off;
+  off = align_up(off + sizeof(TripDesc) * bt->slab_desc.size(), 256);
+  bt->off_tasks = off;
+  off = align_up(off + sizeof(Task) * std::max<size_t>(bt->tasks.size(), 1), 256);
+  bt->off_tb = off;
+  off = align_up(off + sizeof(int32_t) * std::max<size_t>(bt->tb_trips.size(), 1), 256);
+  bt->off_rowoff = off;
+  off = align_up(off + sizeof(int64_t) * std::max<size_t>(bt->row_off.size(), 1), 256);
+  bt->off_rowcap = off;
+  off = align_up(off + sizeof(int32_t) * std::max<size_t>(bt->row_cap.size(), 1), 256);
+  bt->inputs_bytes = off;
+}
+
+// Affine-gap batch (affine.cu): one queue entry per triplet, largest cube first; each CTA of
+// the persistent launch sweeps its triplets' anti-diagonal planes in four rotating plane
+// buffers of 13 int32 states per cell. Score only.
+trioseq_status build_affine(trioseq_plan_s* plan, trioseq_batch_s* bt) {
+  const size_t n = bt->n;
+  std::vector<int32_t> order(n);
+  int64_t maxcells = 1;
+  for (size_t t = 0; t < n; t++) {
+    order[t] = (int32_t)t;
+    const TripDesc& d = bt->desc[t];
+    maxcells = std::max<int64_t>(maxcells, (int64_t)(d.len[1] + 1) * (d.len[2] + 1));
+  }
+  const auto vol = [&](int32_t t) {
+    const TripDesc& d = bt->desc[t];
+    return (double)(d.len[0] + 1) * (d.len[1] + 1) * (d.len[2] + 1);
+  };
+  std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return vol(x) > vol(y); });
+  bt->tasks.clear();
+  for (const int32_t t : order) bt->tasks.push_back(Task{t, 0, 0, 0});
+  int bpm = 0;
+  if (affine_occupancy(&bpm) != 0 || bpm <= 0) return TRIOSEQ_ECUDA;
+  bt->grid = (int)std::max<size_t>(1, std::min<size_t>((size_t)plan->sms * bpm, n));
+  bt->affine_cells = maxcells;
+  bt->face_ints = (size_t)bt->grid * 4 * (size_t)maxcells * kAffineStates;
+  bt->seq_bytes = bt->seq.size();
+  layout_inputs(bt);
+  return TRIOSEQ_OK;
 }
 
 // Build the host side of a batch: encode, pack, describe, order the queue.
@@ -449,12 +504,24 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
     if (tb && plan->atype != kGlobal &&
         (double)(d.len[0] + 1) * (d.len[1] + 1) * (d.len[2] + 1) >= (double)(1ULL << 37))
       return TRIOSEQ_EOVERFLOW;
+    // affine: |score| <= (3 max|sigma| + 3|alpha| + 3|gamma|) * (a+b+c), kept below 2^29
+    if (plan->affine &&
+        (int64_t)(3 * plan->max_abs_sub + 3 * std::abs(plan->gap) + 3 * std::abs(plan->gap_open)) *
+                std::max<int64_t>(sumlen, 1) >= (1LL << 29))
+      return TRIOSEQ_EOVERFLOW;
     d.pair = -1;
+    d.nH = 1;
+    d.isub = 0;
+    d.plane_off = 0;
     d.score_base = 2 * plan->gap * (int32_t)sumlen;
     d.out_idx = (int32_t)t;
     d.tb_idx = -1;
     d.code_off = -1;
     bt->cells += (uint64_t)d.len[0] * (uint64_t)d.len[1] * (uint64_t)d.len[2];
+  }
+  if (plan->affine) {
+    if (tb) return TRIOSEQ_ENOTIMPL;  // the affine model is score-only on the device
+    return build_affine(plan, bt);
   }
   // 2. Units of work: one triplet, or in packed int16x2 mode two triplets of the same column-task
   //    grid class paired in one unit (the high halves run on the grid of their maximal lengths).
@@ -512,7 +579,34 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
     face += ntask * (size_t)(a + 1) * (size_t)WJ;
     face = align_up(face, 4);
     d.prog_base = prog;
-    prog += (int64_t)d.nJ * d.nK;
+    if (vl && n == 1) {
+      // Two cells per register, one triplet: cut each column's i axis into nH sub-tasks so that
+      // the launch runs about eight waves of tasks instead of a few long ones (the first and
+      // last task durations of a launch run with part of the warps idle). Each sub-task keeps
+      // at least 256 slices. TRIOSEQ_ISPLIT at plan creation forces nH.
+      int bpm = 0;
+      const size_t sm = wavefront_vl_smem_bytes(NJ, NK, plan->KP, bt->var.vl - 1);
+      if (wavefront_occupancy(NJ, NK, false, kGlobal, 2 + bt->var.vl, false, sm, &bpm) != 0)
+        bpm = 1;
+      const double resident = (double)plan->sms * std::max(bpm, 1) *
+                              (wavefront_block_threads(2 + bt->var.vl) / 32);
+      int nH = (int)std::ceil(8.0 * resident / (double)ntask);
+      nH = std::max(1, std::min(nH, (a + 1) / 256));
+      if (plan->isplit > 0) nH = plan->isplit;
+      nH = std::max(1, std::min(nH, std::max(1, (a + 1) / 64)));
+      d.nH = nH;
+      d.isub = (a + 1 + nH - 1) / nH;
+      d.nH = (a + 1 + d.isub - 1) / d.isub;  // no empty sub-task
+      if (d.nH > 1) {
+        d.plane_off = (int64_t)face;
+        face += ntask * (size_t)WJ * (size_t)WK;
+        face = align_up(face, 4);
+        d.T = d.isub + (kPR - 1) + (2 * kPC - 1);  // steps of a full sub-task (first-wave pacing)
+      } else {
+        d.isub = 0;
+      }
+    }
+    prog += (int64_t)d.nJ * d.nK * std::max(d.nH, 1);
     if (un.second >= 0 && un.second != un.first) {  // the high half shares the grid
       TripDesc& h = bt->desc[un.second];
       for (int q = 0; q < 3; q++) h.glen[q] = d.glen[q];
@@ -623,27 +717,33 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
   }
   for (size_t D = 1; D < start.size(); D++) start[D] += start[D - 1];
   bt->tasks.assign((size_t)prog, Task{0, 0, 0, 0});
-  for (const int32_t u : order) {
-    const int32_t t = units[u].first;
-    const TripDesc& d = bt->desc[t];
-    for (int J = 0; J < d.nJ; J++)
-      for (int K = 0; K < d.nK; K++) bt->tasks[start[(size_t)(J + K)]++] = Task{t, J, K, 0};
+  if (n == 1 && bt->desc[0].nH > 1) {
+    // Sub-tasks (J, K, h) ordered by an estimate of their earliest start: sub-task h - 1 of the
+    // same column must finish (isub + 18 steps), and each producer level lags by its skew and
+    // its publication interval (about 6 steps along j, 20 along k). Every producer's estimate is
+    // strictly smaller than its consumer's, so the order keeps producers first (no deadlock).
+    const TripDesc& d = bt->desc[0];
+    const double lagJ = kPR + 2, lagK = 2 * kPC + 4, lagH = d.isub + (kPR - 1) + (2 * kPC - 1);
+    std::vector<std::pair<double, Task>> est;
+    est.reserve(bt->tasks.size());
+    for (int hh = 0; hh < d.nH; hh++)
+      for (int J = 0; J < d.nJ; J++)
+        for (int K = 0; K < d.nK; K++)
+          est.emplace_back(hh * lagH + J * lagJ + K * lagK, Task{0, J, K, hh});
+    std::stable_sort(est.begin(), est.end(),
+                     [](const std::pair<double, Task>& x, const std::pair<double, Task>& y) {
+                       return x.first < y.first;
+                     });
+    for (size_t q = 0; q < est.size(); q++) bt->tasks[q] = est[q].second;
+  } else {
+    for (const int32_t u : order) {
+      const int32_t t = units[u].first;
+      const TripDesc& d = bt->desc[t];
+      for (int J = 0; J < d.nJ; J++)
+        for (int K = 0; K < d.nK; K++) bt->tasks[start[(size_t)(J + K)]++] = Task{t, J, K, 0};
+    }
   }
-  // device layout of the input block
-  size_t off = align_up(bt->seq_bytes, 256);
-  bt->off_desc = off;
-  off = align_up(off + sizeof(TripDesc) * std::max<size_t>(n, 1), 256);
-  bt->off_slab = off;
-  off = align_up(off + sizeof(TripDesc) * bt->slab_desc.size(), 256);
-  bt->off_tasks = off;
-  off = align_up(off + sizeof(Task) * std::max<size_t>(bt->tasks.size(), 1), 256);
-  bt->off_tb = off;
-  off = align_up(off + sizeof(int32_t) * std::max<size_t>(bt->tb_trips.size(), 1), 256);
-  bt->off_rowoff = off;
-  off = align_up(off + sizeof(int64_t) * std::max<size_t>(bt->row_off.size(), 1), 256);
-  bt->off_rowcap = off;
-  off = align_up(off + sizeof(int32_t) * std::max<size_t>(bt->row_cap.size(), 1), 256);
-  bt->inputs_bytes = off;
+  layout_inputs(bt);
   // launch shape
   bt->smem = bt->packed >= 3 ? wavefront_vl_smem_bytes(NJ, NK, plan->KP, bt->packed - 3)
                              : wavefront_smem_bytes(NJ, NK, plan->KP, bt->packed != 0);
@@ -739,6 +839,29 @@ trioseq_status run(trioseq_batch_s* bt, cudaStream_t st) {
   if (e != cudaSuccess) return cuda_status(e);
   if (bt->n == 0) return TRIOSEQ_OK;
   char* in = ws.inputs.as<char>();
+  if (plan->affine) {  // affine gaps (affine.cu): score only, one CTA per triplet at a time
+    AffineParams ap{};
+    ap.desc = reinterpret_cast<const TripDesc*>(in + bt->off_desc);
+    ap.tasks = reinterpret_cast<const Task*>(in + bt->off_tasks);
+    ap.n = (int32_t)bt->tasks.size();
+    ap.KP = plan->KP;
+    ap.seq = reinterpret_cast<const int8_t*>(in);
+    ap.sub = plan->sig_affine.as<int32_t>();
+    ap.gap = plan->gap;
+    ap.gap_open = plan->gap_open;
+    ap.planes = ws.faces.as<int32_t>();
+    ap.plane_cells = bt->affine_cells;
+    ap.queue = queue;
+    ap.scores = ws.scores.as<int32_t>();
+    if (bt->profile && record(bt->ev[0], st) != cudaSuccess) return cuda_status(cudaGetLastError());
+    if (launch_affine(ap, bt->grid, st) != 0) return cuda_status(cudaGetLastError());
+    if (bt->profile) {
+      if (record(bt->ev[1], st) != cudaSuccess || record(bt->ev[2], st) != cudaSuccess)
+        return cuda_status(cudaGetLastError());
+      bt->timed = true;
+    }
+    return TRIOSEQ_OK;
+  }
   WaveParams p{};
   p.desc = reinterpret_cast<const TripDesc*>(in + bt->off_desc);
   p.tasks = reinterpret_cast<const Task*>(in + bt->off_tasks);
@@ -756,17 +879,18 @@ trioseq_status run(trioseq_batch_s* bt, cudaStream_t st) {
   p.wait_ns = plan->wait_ns;
   p.g2 = -2 * plan->gap;
   p.one = 1;
+  const int warps_per_cta = wavefront_block_threads(bt->packed) / 32;  // resident warps per CTA
   if (plan->test_wait_unset && !bt->slab) {
     // Test of the bounded waits: every first-wave task but queue task 0 waits on a word of the
     // progress buffer that nothing writes (zeroed above), gives up after wait_ns, sets the error
     // word and returns; the call then reports TRIOSEQ_ETIMEOUT.
-    p.pace_n = bt->grid * kWarpsPerCta;
+    p.pace_n = bt->grid * warps_per_cta;
     p.pace_T = 1 << 20;
     p.pace_flag = prog + bt->tasks.size() + 48;
-  } else if (!bt->slab && plan->pace && bt->tasks.size() >= 2 * (size_t)bt->grid * kWarpsPerCta) {
+  } else if (!bt->slab && plan->pace && bt->tasks.size() >= 2 * (size_t)bt->grid * warps_per_cta) {
     // pace the first wave against the progress of queue task 0, the (0,0) block of its triplet
     const TripDesc& d0 = bt->desc[bt->tasks[0].trip];
-    p.pace_n = bt->grid * kWarpsPerCta;
+    p.pace_n = bt->grid * warps_per_cta;
     p.pace_T = d0.T;
     p.pace_flag = prog + d0.prog_base;
   }
@@ -1057,6 +1181,7 @@ trioseq_status trioseq_plan(const trioseq_scoring* sc, uint32_t max_len_hint, ui
     plan->wait_ns = (int64_t)std::max(1, env_int("TRIOSEQ_WAIT_MS", 2000)) * 1000000LL;
     plan->test_wait_unset = env_int("TRIOSEQ_TEST_WAIT_UNSET", 0) != 0;
     plan->test_poison = env_int("TRIOSEQ_TEST_POISON", 0) != 0;
+    plan->isplit = std::max(0, env_int("TRIOSEQ_ISPLIT", 0));
     g_alloc_calls.store(0);
     g_alloc_fail_at.store(std::max(0, env_int("TRIOSEQ_TEST_FAIL_ALLOC", 0)));
     {
@@ -1090,6 +1215,41 @@ trioseq_status trioseq_plan(const trioseq_scoring* sc, uint32_t max_len_hint, ui
   });
 }
 
+trioseq_status trioseq_plan_affine(const trioseq_scoring* sc, int32_t gap_open, uint32_t flags,
+                                   trioseq_plan_t* out) {
+  return no_throw([&]() -> trioseq_status {
+    NvtxRange range("trioseq_plan_affine");
+    if (!out) return TRIOSEQ_EINVAL;
+    *out = nullptr;
+    if (flags != TRIOSEQ_GLOBAL || gap_open > 0 || gap_open < -(1 << 20)) return TRIOSEQ_EINVAL;
+    trioseq_plan_t plan = nullptr;
+    trioseq_status s = trioseq_plan(sc, 0, flags, &plan);
+    if (s != TRIOSEQ_OK) return s;
+    std::unique_ptr<trioseq_plan_s, trioseq_status (*)(trioseq_plan_t)> keep(
+        plan, &trioseq_plan_destroy);
+    DeviceGuard g(plan->device);
+    plan->affine = true;
+    plan->gap_open = gap_open;
+    const int K = plan->K, KP = plan->KP;
+    std::vector<int32_t> tab((size_t)KP * KP, 0);
+    int32_t mx = 0;
+    for (int i = 0; i < K; i++)
+      for (int j = 0; j < K; j++) {
+        tab[(size_t)i * KP + j] = sc->sub[i * K + j];
+        mx = std::max(mx, std::abs((int32_t)sc->sub[i * K + j]));
+      }
+    plan->max_abs_sub = mx;
+    cudaStream_t as = plan->ws.alloc_stream;
+    if (!plan->sig_affine.ensure(tab.size() * 4, as)) return TRIOSEQ_ENOMEM;
+    if (cudaMemcpyAsync(plan->sig_affine.p, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice,
+                        as) != cudaSuccess ||
+        cudaStreamSynchronize(as) != cudaSuccess)
+      return cuda_status(cudaGetLastError());
+    *out = keep.release();
+    return TRIOSEQ_OK;
+  });
+}
+
 trioseq_status trioseq_plan_destroy(trioseq_plan_t plan) {
   return no_throw([&]() -> trioseq_status {
     if (!plan) return TRIOSEQ_OK;
@@ -1103,6 +1263,7 @@ trioseq_status trioseq_plan_destroy(trioseq_plan_t plan) {
     plan->ws.order_after_last_use();
     plan->sig_score.reset();
     plan->sig_tb.reset();
+    plan->sig_affine.reset();
     delete plan;
     return TRIOSEQ_OK;
   });
@@ -1251,7 +1412,9 @@ trioseq_status trioseq_batch_kernel(trioseq_batch_t bt, char* name, size_t cap) 
     const char* type = at == kLocal ? "local" : (at == kSemiGlobal ? "semiglobal" : "global");
     const int nj = bt->var.nj, nk = bt->var.nk;
     char buf[160];
-    if (bt->packed >= 3)
+    if (bt->plan->affine)
+      std::snprintf(buf, sizeof buf, "affine_kernel tile plane");
+    else if (bt->packed >= 3)
       std::snprintf(buf, sizeof buf, "wavefront_vl_kernel<%d,%d,%d> tile %dx%d%s", nj, nk / 2,
                     bt->packed - 3, nj, nk,
                     bt->packed == 4 ? "s" : (bt->packed == 5 ? "t" : (nk == 16 ? "" : "v")));
@@ -1301,6 +1464,12 @@ trioseq_status trioseq_plan_autotune(trioseq_plan_t plan, const trioseq_triplet*
     NvtxRange range("trioseq_plan_autotune");
     if (!plan || !sample || n == 0 || mode > TRIOSEQ_WITH_TRACEBACK) return TRIOSEQ_EINVAL;
     DeviceGuard g(plan->device);
+    if (plan->affine) {  // one kernel shape: nothing to choose
+      if (tile_j) *tile_j = 0;
+      if (tile_k) *tile_k = 0;
+      if (ti) *ti = 0;
+      return mode == TRIOSEQ_WITH_TRACEBACK ? TRIOSEQ_ENOTIMPL : TRIOSEQ_OK;
+    }
     // candidate tiles per mode; 8x4 exists for traceback keys only
     // 8x16 and 8x8 with vl: two cells of one triplet per register
     static const Variant kScoreTiles[] = {{8, 8},    {4, 8},    {4, 4},   {8, 16, 1},
