@@ -795,9 +795,52 @@ def aux_measurements(B, torch, stream, flush, sms, clock_mhz, skip: str, cpu_leg
                      "frac": ach_t / peak_t,
                      "code_stream_gbs": CODE_BYTES_PER_CELL * w.cells / kt / 1e6},
         "cells": w.cells}
+    out["batch4096_affine"] = affine_measurement(B, torch, stream, flush, sms, clock_mhz, lanes)
     out["serving_stream"] = serving_measurement(B, cpu_legs=cpu_legs)
     out["dna8000_linear_space_traceback"] = linear_space_measurement(B, torch, stream)
     return out
+
+
+# Affine gaps (natural gap costs): algorithmic int32 work per cell. Each of the 13 reachable
+# states takes the best of its (move, previous state) candidates: 4 moves with two or three
+# residues x 13 states plus 3 single-residue moves x 13 = 91 candidates, an add and a max each.
+AFFINE_OPS_PER_CELL = 2 * 91
+
+
+def affine_measurement(B, torch, stream, flush, sms, clock_mhz, lanes):
+    """The 4096-triplet DNA batch under affine gaps (trioseq_plan_affine: alpha = -2 per residue
+    against a gap, gamma = -4 per maximal gap run of a pair), score only, one persistent launch.
+    The first 64 scores are checked against the stored oracle values."""
+    from paper_2605_28400_gb300 import synth
+    from tests.golden import goldens
+    w = synth.config2()
+    strs = triplet_strings(w)
+    plan = B.trioseq_plan_affine(w.scoring.alphabet, w.scoring.sub, w.scoring.gap,
+                                 goldens.AFFINE_GAP_OPEN)
+    try:
+        bt = B.trioseq_batch_create(plan, strs, B.SCORE_ONLY)
+        sm, km, _, sc = time_batch(B, torch, bt, 3, 1, stream, flush, len(strs))
+        B.trioseq_batch_destroy(bt)
+    finally:
+        B.trioseq_plan_destroy(plan)
+    checked = None
+    try:
+        meta, want = goldens.load_config2_affine()
+        if meta.get("input_sha256") == goldens.input_digest(w.triplets[:len(want)]):
+            assert [int(x) for x in sc[:len(want)]] == [int(x) for x in want], \
+                "affine batch: scores differ from the stored oracle values"
+            checked = len(want)
+    except OSError:
+        pass
+    kmean = statistics.mean(km)
+    ach = AFFINE_OPS_PER_CELL * w.cells / (kmean / 1e3) / 1e12
+    peak = sms * lanes * clock_mhz * 1e6 / 1e12
+    return {"workload": f"{w.name}: affine gaps (natural gap costs, alpha -2, gamma "
+                        f"{goldens.AFFINE_GAP_OPEN}), score only",
+            "gcups": w.cells / (statistics.mean(sm) / 1e3) / 1e9, "kernel_ms": kmean,
+            "cells": w.cells, "equals_oracle_first": checked, "kernel": "affine_kernel",
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TOPS (int32)",
+                         "frac": ach / peak, "ops_per_cell": AFFINE_OPS_PER_CELL}}
 
 
 def linear_space_measurement(B, torch, stream):

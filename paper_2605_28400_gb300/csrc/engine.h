@@ -71,13 +71,6 @@ struct TripDesc {
   int32_t score_base;  // 2*alpha*(a+b+c)
   int32_t out_idx;     // index into the score output
   int32_t tb_idx;      // index among the batch's traceback triplets (-1: none)
-  // Two-cells-per-register kernel only: the i axis of every column block cut into nH sub-tasks
-  // of isub slices (the last one shorter), task (J, K, h) = Task{trip, J, K, h}, each with its
-  // own progress counter (prog_base + (h*nJ + J)*nK + K). Sub-task h starts from the plane of
-  // slice h*isub - 1 that sub-task h-1 of the same column left at plane_off + column*WJ*WK
-  // (int32, row-major in the block's (j, k)). nH = 1: the whole axis in one task.
-  int64_t plane_off;
-  int32_t nH, isub;
 };
 
 struct Task {

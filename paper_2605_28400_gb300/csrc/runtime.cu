@@ -15,7 +15,6 @@
 #include <array>
 #include <atomic>
 #include <chrono>
-#include <cmath>
 #include <condition_variable>
 #include <cstdlib>
 #include <cstdio>
@@ -223,7 +222,6 @@ struct trioseq_plan_s {
   int64_t wait_ns = 2000000000LL;  // 2 s without progress = give up
   bool test_wait_unset = false;    // test switch: first-wave warps wait on a flag nothing sets
   bool test_poison = false;        // test switch: boundary records start as a large garbage value
-  int isplit = 0;                  // TRIOSEQ_ISPLIT: forced sub-tasks along i (0 = chosen)
   bool graphs = true;              // trioseq_batch_run replays a captured CUDA graph
   bool packed16 = true;            // pair score-only global triplets in int16 halves if they fit
   bool sig2_nonneg = false;        // every sigma'' >= 0: the biased packed mode applies
@@ -510,9 +508,6 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
                 std::max<int64_t>(sumlen, 1) >= (1LL << 29))
       return TRIOSEQ_EOVERFLOW;
     d.pair = -1;
-    d.nH = 1;
-    d.isub = 0;
-    d.plane_off = 0;
     d.score_base = 2 * plan->gap * (int32_t)sumlen;
     d.out_idx = (int32_t)t;
     d.tb_idx = -1;
@@ -579,34 +574,7 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
     face += ntask * (size_t)(a + 1) * (size_t)WJ;
     face = align_up(face, 4);
     d.prog_base = prog;
-    if (vl && n == 1) {
-      // Two cells per register, one triplet: cut each column's i axis into nH sub-tasks so that
-      // the launch runs about eight waves of tasks instead of a few long ones (the first and
-      // last task durations of a launch run with part of the warps idle). Each sub-task keeps
-      // at least 256 slices. TRIOSEQ_ISPLIT at plan creation forces nH.
-      int bpm = 0;
-      const size_t sm = wavefront_vl_smem_bytes(NJ, NK, plan->KP, bt->var.vl - 1);
-      if (wavefront_occupancy(NJ, NK, false, kGlobal, 2 + bt->var.vl, false, sm, &bpm) != 0)
-        bpm = 1;
-      const double resident = (double)plan->sms * std::max(bpm, 1) *
-                              (wavefront_block_threads(2 + bt->var.vl) / 32);
-      int nH = (int)std::ceil(8.0 * resident / (double)ntask);
-      nH = std::max(1, std::min(nH, (a + 1) / 256));
-      if (plan->isplit > 0) nH = plan->isplit;
-      nH = std::max(1, std::min(nH, std::max(1, (a + 1) / 64)));
-      d.nH = nH;
-      d.isub = (a + 1 + nH - 1) / nH;
-      d.nH = (a + 1 + d.isub - 1) / d.isub;  // no empty sub-task
-      if (d.nH > 1) {
-        d.plane_off = (int64_t)face;
-        face += ntask * (size_t)WJ * (size_t)WK;
-        face = align_up(face, 4);
-        d.T = d.isub + (kPR - 1) + (2 * kPC - 1);  // steps of a full sub-task (first-wave pacing)
-      } else {
-        d.isub = 0;
-      }
-    }
-    prog += (int64_t)d.nJ * d.nK * std::max(d.nH, 1);
+    prog += (int64_t)d.nJ * d.nK;
     if (un.second >= 0 && un.second != un.first) {  // the high half shares the grid
       TripDesc& h = bt->desc[un.second];
       for (int q = 0; q < 3; q++) h.glen[q] = d.glen[q];
@@ -717,25 +685,7 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
   }
   for (size_t D = 1; D < start.size(); D++) start[D] += start[D - 1];
   bt->tasks.assign((size_t)prog, Task{0, 0, 0, 0});
-  if (n == 1 && bt->desc[0].nH > 1) {
-    // Sub-tasks (J, K, h) ordered by an estimate of their earliest start: sub-task h - 1 of the
-    // same column must finish (isub + 18 steps), and each producer level lags by its skew and
-    // its publication interval (about 6 steps along j, 20 along k). Every producer's estimate is
-    // strictly smaller than its consumer's, so the order keeps producers first (no deadlock).
-    const TripDesc& d = bt->desc[0];
-    const double lagJ = kPR + 2, lagK = 2 * kPC + 4, lagH = d.isub + (kPR - 1) + (2 * kPC - 1);
-    std::vector<std::pair<double, Task>> est;
-    est.reserve(bt->tasks.size());
-    for (int hh = 0; hh < d.nH; hh++)
-      for (int J = 0; J < d.nJ; J++)
-        for (int K = 0; K < d.nK; K++)
-          est.emplace_back(hh * lagH + J * lagJ + K * lagK, Task{0, J, K, hh});
-    std::stable_sort(est.begin(), est.end(),
-                     [](const std::pair<double, Task>& x, const std::pair<double, Task>& y) {
-                       return x.first < y.first;
-                     });
-    for (size_t q = 0; q < est.size(); q++) bt->tasks[q] = est[q].second;
-  } else {
+  {
     for (const int32_t u : order) {
       const int32_t t = units[u].first;
       const TripDesc& d = bt->desc[t];
@@ -1181,7 +1131,6 @@ trioseq_status trioseq_plan(const trioseq_scoring* sc, uint32_t max_len_hint, ui
     plan->wait_ns = (int64_t)std::max(1, env_int("TRIOSEQ_WAIT_MS", 2000)) * 1000000LL;
     plan->test_wait_unset = env_int("TRIOSEQ_TEST_WAIT_UNSET", 0) != 0;
     plan->test_poison = env_int("TRIOSEQ_TEST_POISON", 0) != 0;
-    plan->isplit = std::max(0, env_int("TRIOSEQ_ISPLIT", 0));
     g_alloc_calls.store(0);
     g_alloc_fail_at.store(std::max(0, env_int("TRIOSEQ_TEST_FAIL_ALLOC", 0)));
     {

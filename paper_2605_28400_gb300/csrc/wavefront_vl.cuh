@@ -156,16 +156,9 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
     }
     const Task tk = p.tasks[task];
     const TripDesc& d = p.desc[tk.trip];
-    const int aT = d.len[0], b = d.len[1], c = d.len[2];  // aT: the cube's last slice
-    const int nJ = d.nJ, nK = d.nK;
+    const int a = d.len[0], b = d.len[1], c = d.len[2];
+    const int nJ = d.nJ, nK = d.nK, T = d.T;
     const int J = tk.J, K = tk.K;
-    // Sub-task h of the column covers slices i0 .. i0 + a (local slices 0 .. a); h > 0 starts
-    // from the plane of slice i0 - 1 left by sub-task h - 1.
-    const int h = d.nH > 1 ? tk.pad : 0;
-    const int i0 = h * d.isub;
-    const int a = d.nH > 1 ? min(d.isub, aT + 1 - i0) - 1 : aT;
-    const int T = a + 1 + (kPR - 1) + (2 * kPC - 1);
-    const bool last_sub = d.nH <= 1 || h == d.nH - 1;
     const int8_t* S0 = p.seq + d.s_off[0];
     const int8_t* S1 = p.seq + d.s_off[1];
     const int8_t* S2 = p.seq + d.s_off[2];
@@ -222,7 +215,7 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
 
     // Owner of the final cell (a, b, c): its lane, half and tile cell.
     const int endK = c % WK;
-    const bool owns_end = last_sub && (J == b / WJ) && (K == c / WK) && (r == (b % WJ) / NJ) &&
+    const bool owns_end = (J == b / WJ) && (K == c / WK) && (r == (b % WJ) / NJ) &&
                           (lc == endK / NK);
     const int end_p = b % NJ, end_h = (endK % NK) >= NH, end_q = (endK % NK) % NH;
 
@@ -241,34 +234,18 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
       rowB[qq] = NEG;
     }
 
-    // records are indexed by the cube's slice (local slice + i0)
-    const int64_t recJ = (int64_t)(aT + 1) * G::RJ, recK = (int64_t)(aT + 1) * G::RK;
+    const int64_t recJ = (int64_t)(a + 1) * G::RJ, recK = (int64_t)(a + 1) * G::RK;
     int* const faces = p.faces;
-    const int* srcJ = faces + d.oj_off + (int64_t)(me - nK) * recJ + (int64_t)i0 * G::RJ;
-    const int* srcK = faces + d.ok_off + (int64_t)(me - 1) * recK + (int64_t)i0 * G::RK;
-    int* dstJ = faces + d.oj_off + (int64_t)me * recJ + (int64_t)i0 * G::RJ;
-    int* dstK = faces + d.ok_off + (int64_t)me * recK + (int64_t)i0 * G::RK;
+    const int* srcJ = faces + d.oj_off + (int64_t)(me - nK) * recJ;  // producer (J-1, K)
+    const int* srcK = faces + d.ok_off + (int64_t)(me - 1) * recK;   // producer (J, K-1)
+    int* dstJ = faces + d.oj_off + (int64_t)me * recJ;
+    int* dstK = faces + d.ok_off + (int64_t)me * recK;
     const bool has_out_j = (J + 1 < nJ), has_out_k = (K + 1 < nK);
-    const int mt = h * nJ * nK + me;  // this sub-task's progress counter
-    const int* progJ = p.progress + d.prog_base + (mt - nK);
-    const int* progK = p.progress + d.prog_base + (mt - 1);
-    int* progMe = p.progress + d.prog_base + mt;
-    // the column's plane (sub-tasks of more than one): block-local (jl, kl), absolute int32
-    int* plane = p.faces + d.plane_off + (int64_t)me * WJ * WK;
+    const int* progJ = p.progress + d.prog_base + (me - nK);
+    const int* progK = p.progress + d.prog_base + (me - 1);
+    int* progMe = p.progress + d.prog_base + me;
     int cachedJ = J > 0 ? 0 : 1 << 30, cachedK = K > 0 ? 0 : 1 << 30;  // warp-uniform
     bool ok = true;
-    if (h > 0) {  // the plane of slice i0 - 1: sub-task h - 1 of this column has finished
-      bool okl = true;
-      int seen = 0;
-      if (lane == 0)
-        okl = wait_flag(progMe - nJ * nK, d.isub + (kPR - 1) + (2 * kPC - 1), &seen, p.wait_ns);
-      ok = __shfl_sync(kFull, okl, 0);
-      __syncwarp();
-      if (!ok) {
-        if (lane == 0) atomicOr(p.err, 1);
-        return;
-      }
-    }
 
     // Face pieces (absolute int32 records, kNeg where absent): loaded two steps ahead, parked one
     // step ahead, read by the edge lanes and converted to the task's base there.
@@ -295,8 +272,7 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
 #pragma unroll
       for (int m = 0; m < G::NPL; ++m) {
         const int sl = u - cp_delta[m];
-        // local slice -1 of a sub-task h > 0 is the cube's slice i0 - 1, left by sub-task h - 1
-        const bool have = ok && cp_kind[m] != 0 && sl >= (h > 0 ? -1 : 0) && sl <= a &&
+        const bool have = ok && cp_kind[m] != 0 && sl >= 0 && sl <= a &&
                           (cp_kind[m] == 1 ? J > 0 : K > 0);
         const int* src = (cp_kind[m] == 1) ? srcJ + (int64_t)sl * G::RJ + cp_col[m]
                                            : srcK + (int64_t)sl * G::RK + cp_col[m];
@@ -316,7 +292,7 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
     // piece (record slots 0..3) carries only the corner in slot 3: slots 0..2 are never
     // written, so they stay out of the maximum.
     int Bt = 0;
-    if (h == 0) {
+    {
       int mx = kNeg;
 #pragma unroll
       for (int m = 0; m < G::NPL; ++m) {
@@ -326,55 +302,16 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) mx = max(mx, __shfl_xor_sync(kFull, mx, off));
       Bt = mx > kNeg / 2 ? mx : 0;
-    } else {
-      // Sub-task h > 0: the base is the block's first cell at slice i0 - 1, lane 0's reference
-      // for rebasing (M' only grows from there along every axis). Every lane's tile starts as
-      // the plane of slice i0 - 1 in both halves (the low half's previous slice, and the value
-      // the high half keeps for local slice -1).
-      Bt = __shfl_sync(kFull, plane[0], 0);
     }
     int nb = kVlBias - Bt;  // absolute M' -> biased half: max(v + nb, 0)
-    // the plane of slice i0 - 1 as this lane's halves (low: columns 0..NH-1 of the lane tile,
-    // high: NH..2NH-1), biased against the base
-    const auto plane_row = [&](int pp, int (&lo)[NH], int (&hi)[NH]) {
-      const int* row = plane + (r * NJ + pp) * WK + lc * NK;
-#pragma unroll
-      for (int q4 = 0; q4 < NH / 4; ++q4) {
-        const int4 u = reinterpret_cast<const int4*>(row)[q4];
-        const int4 v = reinterpret_cast<const int4*>(row + NH)[q4];
-        lo[4 * q4] = u.x; lo[4 * q4 + 1] = u.y; lo[4 * q4 + 2] = u.z; lo[4 * q4 + 3] = u.w;
-        hi[4 * q4] = v.x; hi[4 * q4 + 1] = v.y; hi[4 * q4 + 2] = v.z; hi[4 * q4 + 3] = v.w;
-      }
-    };
-    if (h > 0) {
-#pragma unroll
-      for (int pp = 0; pp < NJ; ++pp) {
-        int lo[NH], hi[NH];
-        plane_row(pp, lo, hi);
-#pragma unroll
-        for (int qq = 0; qq < NH; ++qq)
-          P[pp][qq] = (int)__byte_perm((unsigned)max(lo[qq] + nb, 0), (unsigned)max(hi[qq] + nb, 0),
-                                       0x5410);
-      }
-      // Lane (0,0) is active at step 0: its previous-slice halos are the records of slice
-      // i0 - 1 (the other lanes meet local slice -1 inside the loop, by shuffle and ring).
-      if (lane == 0) {
-        const int* rj = srcJ - G::RJ;  // producer (J-1, K), slice i0 - 1
-        const int* rk = srcK - G::RK;  // producer (J, K-1), slice i0 - 1
-#pragma unroll
-        for (int qq = 0; qq <= NH; ++qq) rowB[qq] = J > 0 ? max(rj[3 + qq] + nb, 0) : NEG;
-#pragma unroll
-        for (int pp = 0; pp < NJ; ++pp) colB[pp] = K > 0 ? max(rk[pp] + nb, 0) : NEG;
-      }
-    }
     // M'[-1][-1][-1] = 0 feeds the origin through the (1,1,1) move (low half of lane 0).
-    if (h == 0 && J == 0 && K == 0 && lane == 0) rowB[0] = kVlBias - Bt;
+    if (J == 0 && K == 0 && lane == 0) rowB[0] = kVlBias - Bt;
     park();
     fetch(1);
 
     auto xblock = [&](int base) -> int {
-      const int sl = base + lane, g = i0 + sl;  // local slice, cube slice
-      return (g >= 1 && sl <= a && g <= aT) ? (int)__ldg(S0 + g - 1) : VIRT;
+      const int sl = base + lane;
+      return (sl >= 1 && sl <= a) ? (int)__ldg(S0 + sl - 1) : VIRT;
     };
     int xprev = VIRT, xcur = xblock(0), xnext = xblock(32);
     int xlo_prev = VIRT;  // residue of slice s - 1: the high half's
@@ -523,7 +460,7 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
             if (qq >= 0 && qq < NH) pass2(pp, qq);
           }
         }
-        if (s == 0 && h == 0) {  // the high half was at slice -1: -infinity there, and in its halos
+        if (s == 0) {  // the high half was at slice -1: -infinity there, and in its halos
 #pragma unroll
           for (int pp = 0; pp < NJ; ++pp) {
 #pragma unroll
@@ -532,19 +469,6 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
           }
 #pragma unroll
           for (int qq = 0; qq <= NH; ++qq) rowCur[qq] &= 0xffff;
-        } else if (s == 0) {
-          // Sub-task h > 0: local slice -1 of the high half is the cube's slice i0 - 1, already
-          // computed by sub-task h - 1: it keeps the plane's values (its halos for that slice
-          // came from the plane too, through the ring and the shuffles).
-#pragma unroll
-          for (int pp = 0; pp < NJ; ++pp) {
-            int lo[NH], hi[NH];
-            plane_row(pp, lo, hi);
-#pragma unroll
-            for (int qq = 0; qq < NH; ++qq)
-              P[pp][qq] = (int)__byte_perm((unsigned)P[pp][qq], (unsigned)max(hi[qq] + nb, 0),
-                                           0x5410);
-          }
         }
       }
       if (--pub_in == 0) {
@@ -588,25 +512,6 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
             for (int e = 0; e < 4; ++e) v[e] = (int)((unsigned)P[4 * p4 + e][NH - 1] >> 16) + ub;
             st_global_if(reinterpret_cast<int4*>(dk) + p4, make_int4(v[0], v[1], v[2], v[3]),
                          out_k);
-          }
-        }
-        if (!last_sub && (s == a || s - 1 == a)) {
-          // the last slice of this sub-task becomes the plane the next one starts from: the low
-          // half at s = a, the high half one step later
-          const bool lo_last = s == a;
-#pragma unroll
-          for (int pp = 0; pp < NJ; ++pp) {
-            int* row = plane + (r * NJ + pp) * WK + lc * NK + (lo_last ? 0 : NH);
-#pragma unroll
-            for (int q4 = 0; q4 < NH / 4; ++q4) {
-              int v[4];
-#pragma unroll
-              for (int e = 0; e < 4; ++e) {
-                const unsigned w = (unsigned)P[pp][4 * q4 + e];
-                v[e] = (int)(lo_last ? (w & 0xffffu) : (w >> 16)) + ub;
-              }
-              reinterpret_cast<int4*>(row)[q4] = make_int4(v[0], v[1], v[2], v[3]);
-            }
           }
         }
         if (owns_end && (end_h ? s - 1 == a : s == a)) {

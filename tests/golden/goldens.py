@@ -22,6 +22,9 @@ CONFIG1 = os.path.join(HERE, "config1_alignment.tsv")
 CONFIG2 = os.path.join(HERE, "config2_scores.tsv")
 CONFIG3 = os.path.join(HERE, "config3_score.tsv")
 CONFIG4 = os.path.join(HERE, "config4_sample.tsv")
+CONFIG2_AFFINE = os.path.join(HERE, "config2_affine_first64.tsv")
+AFFINE_SAMPLE = 64    # the first triplets of the config-2 batch, affine model
+AFFINE_GAP_OPEN = -4  # gamma of the affine line (DNA scheme: alpha = -2 per residue)
 CONFIG4_SAMPLE = 200  # the first requests of the serving stream (seed 1004)
 
 
@@ -81,6 +84,13 @@ def load_config2():
     scores = np.array([int(r[1]) for r in rows], dtype=np.int64)
     assert [int(r[0]) for r in rows] == list(range(len(rows)))
     return _header(CONFIG2), scores
+
+
+def load_config2_affine():
+    """(meta, scores of the first AFFINE_SAMPLE config-2 triplets under affine gaps)."""
+    rows = _rows(CONFIG2_AFFINE)
+    assert [int(r[0]) for r in rows] == list(range(len(rows)))
+    return _header(CONFIG2_AFFINE), np.array([int(r[1]) for r in rows], dtype=np.int64)
 
 
 def load_config3():

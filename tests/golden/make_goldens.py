@@ -1,6 +1,6 @@
 """Write the full-size golden files from the oracle alone (test infrastructure).
 
-    python tests/golden/make_goldens.py [--only c0,c1,c2,c3,c4] [--threads N]
+    python tests/golden/make_goldens.py [--only c0,c1,c2,c2a,c3,c4] [--threads N]
 
 Every stored value is computed by ``oracle/`` (plain int64 Eq. 1 of Sec. II with the global
 initialisation and the first-maximal-move tie-break in Eq. 1's listing order) on the seeded
@@ -11,6 +11,8 @@ inputs of ``paper_2605_28400_gb300/synth.py``; nothing here touches the CUDA lib
   triplet (ancestor 1000, seed 1001).
 - config2_scores.tsv: all 4,096 scores of the batch of related DNA triplets (ancestor lengths
   uniform in [100, 300], seed 1002), independent triplets spread over host threads.
+- config2_affine_first64.tsv: the first 64 triplets of that batch under affine gaps (natural
+  gap costs, alpha = -2, gamma = -4; the build's reading of the paper's future work, Sec. VI).
 - config3_score.tsv: the score of the protein triplet with ancestor length 4000 (seed 1003),
   about 6.4e10 cells on one host core.
 - config4_sample.tsv: the first 200 requests of the serving stream (seed 1004: 70% DNA, 30%
@@ -91,6 +93,26 @@ def make_config2(threads):
     print(f"config2: {len(scores)} scores in {dt:.1f} s", flush=True)
 
 
+def make_config2_affine(threads):
+    w = synth.config2()
+    trips = w.triplets[:goldens.AFFINE_SAMPLE]
+    t0 = time.time()
+    with ThreadPoolExecutor(max_workers=threads) as ex:
+        scores = list(ex.map(lambda t: oracle.align_affine(*t, w.scoring.sub, w.scoring.gap,
+                                                           goldens.AFFINE_GAP_OPEN), trips))
+    dt = time.time() - t0
+    meta = {"workload": f"{w.name}, first {len(trips)}, affine", "seed": 1002,
+            "gap_open": goldens.AFFINE_GAP_OPEN, "triplets": len(trips),
+            "cells": sum(len(a) * len(b) * len(c) for a, b, c in trips),
+            "input_sha256": goldens.input_digest(trips),
+            "oracle_seconds": f"{dt:.1f} on {threads} threads"}
+    _write(goldens.CONFIG2_AFFINE, [f"{i}\t{int(v)}" for i, v in enumerate(scores)], meta,
+           "# Config 2 under affine gaps (natural gap costs: per pair, the induced alignment with its\n"
+           "# all-gap columns deleted; alpha = -2 per residue against a gap, gamma = -4 per maximal\n"
+           "# gap run): the first 64 triplets of the batch. Columns: index, score.\n")
+    print(f"config2 affine: {len(scores)} scores in {dt:.1f} s", flush=True)
+
+
 def make_config3():
     w = synth.config3()
     t0 = time.time()
@@ -147,7 +169,7 @@ def make_config4(threads):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--only", default="c0,c1,c2,c3,c4")
+    ap.add_argument("--only", default="c0,c1,c2,c2a,c3,c4")
     ap.add_argument("--threads", type=int, default=os.cpu_count() or 1)
     a = ap.parse_args()
     which = set(a.only.split(","))
@@ -161,6 +183,8 @@ def main():
                 make_alignment(c)
         if "c2" in which:
             make_config2(rest)
+        if "c2a" in which:
+            make_config2_affine(rest)
         if "c4" in which:
             make_config4(rest)
         if f3 is not None:

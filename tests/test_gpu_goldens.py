@@ -148,3 +148,18 @@ def test_config4_sample_through_the_server_equals_oracle():
         if w["traceback"]:
             assert len(rows[0]) == w["aln_len"], i
             assert goldens.rows_digest(rows) == w["rows_sha256"], i
+
+
+def test_config2_affine_first_triplets_equal_oracle():
+    """Affine gaps (natural gap costs) on the first 64 triplets of the config-2 batch, run in the
+    whole 4,096-triplet launch: the first 64 scores equal the stored oracle values."""
+    meta, want = goldens.load_config2_affine()
+    w = synth.config2()
+    assert meta["input_sha256"] == goldens.input_digest(w.triplets[:len(want)])
+    plan = B.trioseq_plan_affine(w.scoring.alphabet, w.scoring.sub, w.scoring.gap,
+                                 goldens.AFFINE_GAP_OPEN)
+    try:
+        got = B.trioseq_align_batch(plan, [_strs(t, w.scoring) for t in w.triplets])
+    finally:
+        B.trioseq_plan_destroy(plan)
+    assert [int(x) for x in got[:len(want)]] == [int(x) for x in want]

@@ -174,34 +174,3 @@ def test_vl_unavailable_cases_fall_back_to_int32():
         assert int(got[0]) == score
     finally:
         B.trioseq_plan_destroy(plan)
-
-
-@pytest.mark.parametrize("tile", VL_TILES)
-@pytest.mark.parametrize("nh", [2, 3, 7])
-def test_vl_sub_tasks_along_i(tile, nh):
-    """A one-triplet batch with each column's i axis cut into nh sub-tasks (TRIOSEQ_ISPLIT),
-    chained by the plane of the slice before each cut: exact against the oracle on a related DNA
-    triplet (n = 600, many rebases) and a protein one (n = 420), with the boundary records
-    poisoned so that a sub-task reading a record or plane slot before it is written fails."""
-    cases = [(DNA, synth.config1(seed=99, L=600).triplets[0]),
-             (synth.protein_scoring(97), synth.config3(seed=97, L=420).triplets[0])]
-    for sc, t in cases:
-        os.environ["TRIOSEQ_ISPLIT"] = str(nh)
-        os.environ["TRIOSEQ_TEST_POISON"] = "1"
-        try:
-            plan = _plan(sc, tile)
-        finally:
-            os.environ.pop("TRIOSEQ_ISPLIT", None)
-            os.environ.pop("TRIOSEQ_TEST_POISON", None)
-        try:
-            want = oracle.align(*t, sc.sub, sc.gap)
-            assert int(B.trioseq_align_batch(plan, [strs(t, sc)])[0]) == want
-            bt = B.trioseq_batch_create(plan, [strs(t, sc)])
-            try:
-                for _ in range(2):
-                    B.trioseq_batch_run(bt)
-                    assert int(B.trioseq_batch_scores(bt, 1)[0]) == want
-            finally:
-                B.trioseq_batch_destroy(bt)
-        finally:
-            B.trioseq_plan_destroy(plan)
