@@ -173,7 +173,7 @@ const void* wavefront_packed(int nj, int nk, int mode);
 // two cells of one triplet per register (wavefront_vl.cuh): nj x nk = 8 x 16 or 8 x 8 cells per
 // lane; cs = 1 or 2: the lane's sigma''(y,z) tile in shared memory (8 x 16 only; 2-warp or
 // 1-warp CTAs), 0: in registers
-const void* wavefront_vl(int nj, int nk, int cs);
+const void* wavefront_vl(int nj, int nk, int cs, int at);
 size_t wavefront_vl_smem_bytes(int nj, int nk, int KP, int cs);
 int wavefront_vl_warps(int cs);
 // Kernel entry of a slab-launch instantiation (kernels_slab.cu), or null.

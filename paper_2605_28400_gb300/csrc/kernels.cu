@@ -248,7 +248,7 @@ const void* kptr() {
 
 const void* pick(int nj, int nk, bool tb, int at, int pk, bool slab) {
   if (slab) return (pk || at != kGlobal) ? nullptr : wavefront_slab(nj, nk, tb);
-  if (pk >= 3) return (tb || at != kGlobal) ? nullptr : wavefront_vl(nj, nk, pk - 3);
+  if (pk >= 3) return tb ? nullptr : wavefront_vl(nj, nk, pk - 3, at);
   if (pk) return (tb || at != kGlobal) ? nullptr : wavefront_packed(nj, nk, pk);
   if (at != kGlobal) return wavefront_variant(nj, nk, at, tb);
   if (nj == 8 && nk == 8) return tb ? kptr<8, 8, true>() : kptr<8, 8, false>();

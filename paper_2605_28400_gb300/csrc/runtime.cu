@@ -399,12 +399,15 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
     }
   }
   // Two cells of one triplet per register (wavefront_vl.cuh), variants 8x16 and 8x8v: score-only
-  // global alignment with every sigma'' >= 0, max sigma'' <= 33 (the kernel's range argument),
+  // global or semi-global alignment with every sigma'' >= 0, max sigma'' <= 33 (the kernel's range
+  // argument),
   // and boundary records within the slab budget (it has no slab form). Outside the autotuner's
   // own candidate runs, work it cannot take runs on the int32 8x8 kernel instead.
   if (bt->var.vl) {
-    bool ok_vl = !tb && plan->atype == kGlobal && plan->sig2_nonneg && plan->max_abs_sig2 <= 33 &&
-                 wavefront_vl(bt->var.nj, bt->var.nk, bt->var.vl - 1) != nullptr;
+    // (semi-global too: its zero axes add steps of -2*alpha, so that must also stay <= 33)
+    bool ok_vl = !tb && plan->sig2_nonneg && plan->max_abs_sig2 <= 33 &&
+                 (plan->atype == kGlobal || (plan->atype == kSemiGlobal && -2 * plan->gap <= 33)) &&
+                 wavefront_vl(bt->var.nj, bt->var.nk, bt->var.vl - 1, plan->atype) != nullptr;
     if (ok_vl) {
       const int wj = kPR * bt->var.nj, wk = kPC * bt->var.nk;
       double rec = 0;  // int32 boundary records of all triplets: (a+1) x tasks x (WK+4 + WJ)

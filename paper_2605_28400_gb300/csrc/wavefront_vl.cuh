@@ -79,9 +79,13 @@ __host__ __device__ constexpr int vl_diag_index(int pp, int qq) {
   return e + (pp - lo);
 }
 
-template <int NJ, int NH, int CS>
+// AT: the alignment type of Sec. II, kGlobal or kSemiGlobal. Semi-global feeds its zero axes
+// through the halo cells at j = -1 / k = -1 (as wavefront_kernel does, in the relative halves)
+// and takes the best original-frame score over the last slices i = a, j = b, k = c.
+template <int NJ, int NH, int CS, int AT>
 __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
     __maxnreg__((VlLaunch<NH, CS>::max_regs)) wavefront_vl_kernel(const WaveParams p) {
+  static_assert(AT == kGlobal || (AT == kSemiGlobal && CS == 0), "global, or semi-global");
   using G = VlGeom<NJ, NH>;
   static_assert(NJ % 4 == 0 && NH % 4 == 0, "tile sides must be multiples of 4");
   constexpr int NK = G::NK, WJ = G::WJ, WK = G::WK;
@@ -218,6 +222,14 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
     const bool owns_end = (J == b / WJ) && (K == c / WK) && (r == (b % WJ) / NJ) &&
                           (lc == endK / NK);
     const int end_p = b % NJ, end_h = (endK % NK) >= NH, end_q = (endK % NK) % NH;
+    // Semi-global: -2*alpha per consumed residue (the frame shift), and this lane's share of the
+    // last row j = b and the last column k = c (low half: columns 0..NH-1 of the lane tile,
+    // high half: NH..2NH-1)
+    const int g2 = p.g2;
+    const int pb = b - j0, qlo = c - k0, qhi = c - k0 - NH;
+    const bool edgeJ = AT == kSemiGlobal && (unsigned)pb < (unsigned)NJ;
+    const bool edgeK = AT == kSemiGlobal && ((unsigned)qlo < (unsigned)NH || (unsigned)qhi < (unsigned)NH);
+    int best = kNeg;  // semi-global: best original-frame score of this lane's counted cells
 
     int P[NJ][NH];
     int rowA[NH + 1], colA[NJ], rowB[NH + 1], colB[NJ];
@@ -306,6 +318,20 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
     int nb = kVlBias - Bt;  // absolute M' -> biased half: max(v + nb, 0)
     // M'[-1][-1][-1] = 0 feeds the origin through the (1,1,1) move (low half of lane 0).
     if (J == 0 && K == 0 && lane == 0) rowB[0] = kVlBias - Bt;
+    // Semi-global zero axes in the shifted frame: M'[-1][-1][k] = g2*k feeds the k axis (move
+    // (1,1,0)), M'[-1][j][-1] = g2*j the j axis (move (1,0,1)), M'[i][-1][-1] = g2*i the i axis
+    // (move (0,1,1)); lane 0 starts from slice -1 (low halves; the high half's are reset).
+    const auto feed = [&](int v) { return max(v + nb, 0); };
+    if (AT == kSemiGlobal && lane == 0) {
+      if (J == 0) {
+#pragma unroll
+        for (int qq = 0; qq <= NH; ++qq) rowB[qq] = feed(g2 * max(k0 + qq - 1, 0));
+      }
+      if (K == 0) {
+#pragma unroll
+        for (int pp = 0; pp < NJ; ++pp) colB[pp] = feed(g2 * (j0 + pp));
+      }
+    }
     park();
     fetch(1);
 
@@ -362,6 +388,24 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
           const unsigned ring_lo = (unsigned)max(cs[pp] + nb, 0);
           colCur[pp] = (lc == 0) ? (int)__byte_perm(ring_lo, (unsigned)mine, 0x5410)
                                  : (int)__byte_perm((unsigned)v, (unsigned)mine, 0x5432);
+        }
+        if (AT == kSemiGlobal && (J == 0 || K == 0)) {  // axis feeds (warp-uniform branch)
+          if (J == 0 && r == 0) {
+#pragma unroll
+            for (int qq = 0; qq <= NH; ++qq) {
+              const int kl = k0 + qq - 1;  // low half: slice s (the high half's feed is at s == 0)
+              const unsigned w = (unsigned)rowCur[qq];
+              const unsigned lo = s == -1 ? (unsigned)feed(g2 * kl)
+                                          : ((s >= 0 && kl == -1) ? (unsigned)feed(g2 * s)
+                                                                  : (w & 0xffffu));
+              rowCur[qq] = (int)((w & 0xffff0000u) | lo);
+            }
+          }
+          if (K == 0 && lc == 0 && s == -1) {
+#pragma unroll
+            for (int pp = 0; pp < NJ; ++pp)
+              colCur[pp] = (int)(((unsigned)colCur[pp] & 0xffff0000u) | (unsigned)feed(g2 * (j0 + pp)));
+          }
         }
       }
 
@@ -469,6 +513,12 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
           }
 #pragma unroll
           for (int qq = 0; qq <= NH; ++qq) rowCur[qq] &= 0xffff;
+          if (AT == kSemiGlobal && J == 0 && r == 0) {
+            // the high half's halo row j = -1 at slice -1 is the k-axis feed M'[-1][-1][k]
+#pragma unroll
+            for (int qq = 0; qq <= NH; ++qq)
+              rowCur[qq] |= feed(g2 * (k0 + NH + qq - 1)) << 16;
+          }
         }
       }
       if (--pub_in == 0) {
@@ -514,7 +564,28 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
                          out_k);
           }
         }
-        if (owns_end && (end_h ? s - 1 == a : s == a)) {
+        if (AT == kSemiGlobal) {
+          // cells on a last slice: the row j = b and the column k = c of each half's slice, and
+          // the whole face i = a when a half reaches it; M = M' - g2*(i+j+k)
+          const bool lo_ok = s <= a, hi_ok = s >= 1;
+          const int base_lo = ub - g2 * (s + j0 + k0), base_hi = ub - g2 * (s - 1 + j0 + k0 + NH);
+          if (edgeJ || edgeK || s == a || s - 1 == a) {
+#pragma unroll
+            for (int pp = 0; pp < NJ; ++pp)
+#pragma unroll
+              for (int qq = 0; qq < NH; ++qq) {
+                const unsigned w = (unsigned)P[pp][qq];
+                const bool in_lo = pp <= pb && qq <= qlo, in_hi = pp <= pb && qq <= qhi;
+                const bool clo = lo_ok && in_lo &&
+                                 (s == a || (edgeJ && pp == pb) || (edgeK && qq == qlo));
+                const bool chi = hi_ok && in_hi &&
+                                 (s - 1 == a || (edgeJ && pp == pb) || (edgeK && qq == qhi));
+                if (clo) best = max(best, (int)(w & 0xffffu) + base_lo - g2 * (pp + qq));
+                if (chi) best = max(best, (int)(w >> 16) + base_hi - g2 * (pp + qq));
+              }
+          }
+        }
+        if (AT == kGlobal && owns_end && (end_h ? s - 1 == a : s == a)) {
           unsigned v = 0;
 #pragma unroll
           for (int pp = 0; pp < NJ; ++pp)
@@ -557,6 +628,11 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
     if (!ok) {
       if (lane == 0) atomicOr(p.err, 1);
       return;
+    }
+    if (AT == kSemiGlobal) {  // the triplet's score is the max over its tasks' lanes
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) best = max(best, __shfl_xor_sync(kFull, best, off));
+      if (lane == 0) atomicMax(p.scores + d.out_idx, best);
     }
   }
 }

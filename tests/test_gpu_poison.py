@@ -93,12 +93,14 @@ def test_traceback_kernels_poisoned(tile):
                                         (oracle.LOCAL, B.LOCAL)], ids=["semiglobal", "local"])
 def test_variant_types_poisoned(kind, flags):
     trips = _trips(63, PROT)
-    plan = _plan(PROT, flags)
-    try:
-        got = B.trioseq_align_batch(plan, _strs(trips, PROT)).tolist()
-        assert got == [oracle.align_type(*t, PROT.sub, PROT.gap, kind) for t in trips]
-    finally:
-        B.trioseq_plan_destroy(plan)
+    want = [oracle.align_type(*t, PROT.sub, PROT.gap, kind) for t in trips]
+    for tile in ("8x8", "8x16", "8x8v"):  # two cells per register where the type allows
+        plan = _plan(PROT, flags, TRIOSEQ_SCORE_TILE=tile)
+        try:
+            assert B.trioseq_align_batch(plan, _strs(trips, PROT)).tolist() == want
+            assert int(B.trioseq_align_batch(plan, _strs(trips[8:9], PROT))[0]) == want[8]
+        finally:
+            B.trioseq_plan_destroy(plan)
 
 
 @pytest.mark.parametrize("mode", [B.SCORE_ONLY, B.WITH_TRACEBACK], ids=["score", "traceback"])

@@ -174,3 +174,61 @@ def test_vl_unavailable_cases_fall_back_to_int32():
         assert int(got[0]) == score
     finally:
         B.trioseq_plan_destroy(plan)
+
+
+def _semi_plan(sc, tile):
+    old = os.environ.get("TRIOSEQ_SCORE_TILE")
+    os.environ["TRIOSEQ_SCORE_TILE"] = tile
+    try:
+        return B.trioseq_plan(sc.alphabet, sc.sub, sc.gap, B.SEMIGLOBAL)
+    finally:
+        if old is None:
+            os.environ.pop("TRIOSEQ_SCORE_TILE", None)
+        else:
+            os.environ["TRIOSEQ_SCORE_TILE"] = old
+
+
+@pytest.mark.parametrize("tile", ["8x16", "8x8v"])
+def test_vl_semiglobal_exact(tile):
+    """The semi-global type (Sec. II: zero axes, best cell on a last slice) on the two-cells-per-
+    register kernel: every shape up to 4^3, ragged multi-block DNA and protein shapes (empty
+    sequences included), related triplets whose values force rebases; exact against
+    oracle.align_type. The batch must run on the two-per-register kernel."""
+    rng = np.random.default_rng(81)
+    cases = [(DNA, [rand_trip(rng, s, 4) for s in itertools.product(range(5), repeat=3)]),
+             (DNA, [rand_trip(rng, s, 4) for s in ((37, 70, 130), (129, 33, 65), (0, 100, 100),
+                                                  (100, 0, 77), (64, 64, 0), (200, 1, 250),
+                                                  (33, 65, 129), (40, 135, 257))]),
+             (PROT, [rand_trip(rng, s, 20) for s in ((90, 140, 260), (31, 32, 63), (5, 260, 3))]),
+             (DNA, list(synth.config1(seed=82, L=600).triplets)),
+             (synth.protein_scoring(83), list(synth.config3(seed=83, L=420).triplets))]
+    for sc, trips in cases:
+        plan = _semi_plan(sc, tile)
+        try:
+            bt = B.trioseq_batch_create(plan, [strs(trips[0], sc)])
+            try:
+                info = B.trioseq_batch_info(bt)
+                assert info["kernel"].startswith("wavefront_vl_kernel"), info
+            finally:
+                B.trioseq_batch_destroy(bt)
+            got = B.trioseq_align_batch(plan, [strs(t, sc) for t in trips])
+            want = [oracle.align_type(*t, sc.sub, sc.gap, oracle.SEMIGLOBAL) for t in trips]
+            assert got.tolist() == want
+            for t, w in list(zip(trips, want))[:3]:  # alone as well as in the batch
+                assert int(B.trioseq_align_batch(plan, [strs(t, sc)])[0]) == w
+        finally:
+            B.trioseq_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("tile", ["8x16", "8x8v"])
+def test_vl_semiglobal_full_size_equals_int32(tile):
+    """The n=4000 protein triplet, semi-global: the two-per-register kernel equals the int32 kernel
+    (itself exact against the oracle on every smaller case)."""
+    w = synth.config3()
+    s = [strs(t, w.scoring) for t in w.triplets]
+    ref, vl = _semi_plan(w.scoring, "8x8"), _semi_plan(w.scoring, tile)
+    try:
+        assert B.trioseq_align_batch(vl, s).tolist() == B.trioseq_align_batch(ref, s).tolist()
+    finally:
+        B.trioseq_plan_destroy(vl)
+        B.trioseq_plan_destroy(ref)
