@@ -2,21 +2,23 @@
 // 8 rows x 2 x 8 columns per lane (column tasks of 32 x 128 cells, 2 CTAs per SM), 8 rows x
 // 2 x 4 columns per lane (tasks of 32 x 64 cells, 3 CTAs per SM), and the 32 x 128 tasks with
 // the lane's sigma''(y,z) tile and 16-bit profiles in shared memory (2-warp CTAs, 5 per SM, or
-// 1-warp CTAs, 9 per SM); the first two also for the semi-global type.
+// 1-warp CTAs, 9 per SM); the first two also for the semi-global and local types.
 #include "wavefront_vl.cuh"
 
 namespace trioseq {
 
 // cs: sigma''(y,z) tile in shared memory, 2-warp CTAs (1, tile label "8x16s") or 1-warp CTAs
 // (2, "8x16t"); 0: in registers
-// at: kGlobal, or kSemiGlobal (cs = 0 only)
+// at: kGlobal, or kSemiGlobal / kLocal (cs = 0 only)
 const void* wavefront_vl(int nj, int nk, int cs, int at) {
-  if (at == kSemiGlobal) {
+  if (at == kSemiGlobal || at == kLocal) {
     if (cs != 0) return nullptr;
     if (nj == 8 && nk == 16)
-      return reinterpret_cast<const void*>(&wavefront_vl_kernel<8, 8, 0, kSemiGlobal>);
+      return at == kLocal ? reinterpret_cast<const void*>(&wavefront_vl_kernel<8, 8, 0, kLocal>)
+                          : reinterpret_cast<const void*>(&wavefront_vl_kernel<8, 8, 0, kSemiGlobal>);
     if (nj == 8 && nk == 8)
-      return reinterpret_cast<const void*>(&wavefront_vl_kernel<8, 4, 0, kSemiGlobal>);
+      return at == kLocal ? reinterpret_cast<const void*>(&wavefront_vl_kernel<8, 4, 0, kLocal>)
+                          : reinterpret_cast<const void*>(&wavefront_vl_kernel<8, 4, 0, kSemiGlobal>);
     return nullptr;
   }
   if (at != kGlobal) return nullptr;

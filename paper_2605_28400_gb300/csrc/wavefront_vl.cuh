@@ -79,13 +79,17 @@ __host__ __device__ constexpr int vl_diag_index(int pp, int qq) {
   return e + (pp - lo);
 }
 
-// AT: the alignment type of Sec. II, kGlobal or kSemiGlobal. Semi-global feeds its zero axes
-// through the halo cells at j = -1 / k = -1 (as wavefront_kernel does, in the relative halves)
-// and takes the best original-frame score over the last slices i = a, j = b, k = c.
+// AT: the alignment type of Sec. II. Semi-global and local feed their zero axes through the halo
+// cells at j = -1 / k = -1 (as wavefront_kernel does, in the relative halves). Semi-global takes
+// the best original-frame score over the last slices i = a, j = b, k = c. Local adds v = 0 to
+// Eq. 1, i.e. M' >= -2*alpha*(i+j+k), as one more packed max in pass 1 (the floor is the same
+// along an anti-diagonal of a half), and takes the best original-frame score over every cell:
+// per step, each cell's M relative to a per-step reference is folded into a packed 16-bit
+// maximum by one add-max, and the step's maximum into a 32-bit best.
 template <int NJ, int NH, int CS, int AT>
 __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
     __maxnreg__((VlLaunch<NH, CS>::max_regs)) wavefront_vl_kernel(const WaveParams p) {
-  static_assert(AT == kGlobal || (AT == kSemiGlobal && CS == 0), "global, or semi-global");
+  static_assert(AT == kGlobal || CS == 0, "the variant types keep sigma'' in registers");
   using G = VlGeom<NJ, NH>;
   static_assert(NJ % 4 == 0 && NH % 4 == 0, "tile sides must be multiples of 4");
   constexpr int NK = G::NK, WJ = G::WJ, WK = G::WK;
@@ -322,7 +326,7 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
     // (1,1,0)), M'[-1][j][-1] = g2*j the j axis (move (1,0,1)), M'[i][-1][-1] = g2*i the i axis
     // (move (0,1,1)); lane 0 starts from slice -1 (low halves; the high half's are reset).
     const auto feed = [&](int v) { return max(v + nb, 0); };
-    if (AT == kSemiGlobal && lane == 0) {
+    if (AT != kGlobal && lane == 0) {
       if (J == 0) {
 #pragma unroll
         for (int qq = 0; qq <= NH; ++qq) rowB[qq] = feed(g2 * max(k0 + qq - 1, 0));
@@ -389,7 +393,7 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
           colCur[pp] = (lc == 0) ? (int)__byte_perm(ring_lo, (unsigned)mine, 0x5410)
                                  : (int)__byte_perm((unsigned)v, (unsigned)mine, 0x5432);
         }
-        if (AT == kSemiGlobal && (J == 0 || K == 0)) {  // axis feeds (warp-uniform branch)
+        if (AT != kGlobal && (J == 0 || K == 0)) {  // axis feeds (warp-uniform branch)
           if (J == 0 && r == 0) {
 #pragma unroll
             for (int qq = 0; qq <= NH; ++qq) {
@@ -471,6 +475,16 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
           }
         };
         // Two passes in place, as in the biased packed mode of wavefront_kernel.
+        // Local: the floor of each anti-diagonal e = pp + qq of the tile, both halves, relative
+        // and clamped at 0 (a floor below the representable range cannot win: every value of
+        // the working set lies above it): M' >= g2*(i+j+k) with i+j+k = s + j0 + k0 + e (low
+        // half) and s - 1 + j0 + k0 + NH + e (high half).
+        unsigned fl_base = 0, fl_step = 0, fl = 0;  // local: the current diagonal's floor
+        if constexpr (AT == kLocal) {
+          const int f0 = max(g2 * (s + j0 + k0) + nb, -30000);  // fits s16 with + g2*e below
+          fl_base = (unsigned)(f0 & 0xffff) | ((unsigned)((f0 + g2 * (NH - 1)) & 0xffff) << 16);
+          fl_step = (unsigned)g2 * 0x10001u;
+        }
         auto pass1 = [&](const int pp, const int qq) {
           const int Pd = (pp == 0) ? rowPrev[qq] : (qq == 0 ? colPrev[pp - 1] : P[pp - 1][qq - 1]);
           const int Pxy = (pp == 0) ? rowPrev[qq + 1] : P[pp - 1][qq];
@@ -478,6 +492,7 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
           const int Sx = P[pp][qq];
           const unsigned x2 = (unsigned)mad_lo(Bq[qq], p.one, mad_lo(A[pp], p.one, Pd));
           unsigned e = __viaddmax_u16x2((unsigned)Pxy, (unsigned)A[pp], (unsigned)Sx);
+          if constexpr (AT == kLocal) e = __vmaxu2(e, fl);  // v = 0
           e = __viaddmax_u16x2((unsigned)Pxz, (unsigned)Bq[qq], e);
           P[pp][qq] = (int)__viaddmax_u16x2(x2, cv(pp, qq), e);
         };
@@ -490,6 +505,7 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
         };
 #pragma unroll
         for (int dg = NJ + NH - 2; dg >= 0; --dg) {
+          if constexpr (AT == kLocal) fl = __viaddmax_s16x2(fl_base, (unsigned)dg * fl_step, 0u);
 #pragma unroll
           for (int pp = NJ - 1; pp >= 0; --pp) {
             const int qq = dg - pp;
@@ -513,7 +529,7 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
           }
 #pragma unroll
           for (int qq = 0; qq <= NH; ++qq) rowCur[qq] &= 0xffff;
-          if (AT == kSemiGlobal && J == 0 && r == 0) {
+          if (AT != kGlobal && J == 0 && r == 0) {
             // the high half's halo row j = -1 at slice -1 is the k-axis feed M'[-1][-1][k]
 #pragma unroll
             for (int qq = 0; qq <= NH; ++qq)
@@ -563,6 +579,24 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
             st_global_if(reinterpret_cast<int4*>(dk) + p4, make_int4(v[0], v[1], v[2], v[3]),
                          out_k);
           }
+        }
+        if constexpr (AT == kLocal) {
+          // Every cell counts. D = P + 2^14 - g2*d per half, d the cell's offset of i+j+k from the
+          // lane corner's at the low half's slice (e, or e + NH - 1 for the high half), equals
+          // M - mbase with mbase = Bt - g2*(s + j0 + k0) - 2^15; by the range argument it lies in
+          // (0, 2^16), so one unsigned add-max per register folds it into the step's maximum.
+          const unsigned g2x2 = (unsigned)g2 * 0x10001u;
+          const unsigned add0 = 0x40004000u - ((unsigned)(g2 * (NH - 1)) << 16);
+          unsigned acc = 0;
+#pragma unroll
+          for (int pp = 0; pp < NJ; ++pp)
+#pragma unroll
+            for (int qq = 0; qq < NH; ++qq)
+              acc = __viaddmax_u16x2((unsigned)P[pp][qq], add0 - (unsigned)(pp + qq) * g2x2, acc);
+          // the low half's extra slice a + 1 and the high half's slice -1 do not count (a masked
+          // half contributes 0, below any counted cell's D)
+          const int dlo = s <= a ? (int)(acc & 0xffffu) : 0, dhi = s >= 1 ? (int)(acc >> 16) : 0;
+          best = max(best, max(dlo, dhi) + Bt - g2 * (s + j0 + k0) - 32768);
         }
         if (AT == kSemiGlobal) {
           // cells on a last slice: the row j = b and the column k = c of each half's slice, and
@@ -629,7 +663,7 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
       if (lane == 0) atomicOr(p.err, 1);
       return;
     }
-    if (AT == kSemiGlobal) {  // the triplet's score is the max over its tasks' lanes
+    if (AT != kGlobal) {  // the triplet's score is the max over its tasks' lanes
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) best = max(best, __shfl_xor_sync(kFull, best, off));
       if (lane == 0) atomicMax(p.scores + d.out_idx, best);

@@ -176,11 +176,12 @@ def test_vl_unavailable_cases_fall_back_to_int32():
         B.trioseq_plan_destroy(plan)
 
 
-def _semi_plan(sc, tile):
+def _semi_plan(sc, tile, flags=None):
     old = os.environ.get("TRIOSEQ_SCORE_TILE")
     os.environ["TRIOSEQ_SCORE_TILE"] = tile
     try:
-        return B.trioseq_plan(sc.alphabet, sc.sub, sc.gap, B.SEMIGLOBAL)
+        return B.trioseq_plan(sc.alphabet, sc.sub, sc.gap,
+                              B.SEMIGLOBAL if flags is None else flags)
     finally:
         if old is None:
             os.environ.pop("TRIOSEQ_SCORE_TILE", None)
@@ -189,11 +190,14 @@ def _semi_plan(sc, tile):
 
 
 @pytest.mark.parametrize("tile", ["8x16", "8x8v"])
-def test_vl_semiglobal_exact(tile):
-    """The semi-global type (Sec. II: zero axes, best cell on a last slice) on the two-cells-per-
-    register kernel: every shape up to 4^3, ragged multi-block DNA and protein shapes (empty
-    sequences included), related triplets whose values force rebases; exact against
-    oracle.align_type. The batch must run on the two-per-register kernel."""
+@pytest.mark.parametrize("kind,flags", [(oracle.SEMIGLOBAL, B.SEMIGLOBAL), (oracle.LOCAL, B.LOCAL)],
+                         ids=["semiglobal", "local"])
+def test_vl_variant_types_exact(tile, kind, flags):
+    """The semi-global type (Sec. II: zero axes, best cell on a last slice) and the local type
+    (zero axes, v = 0, best cell of the cube) on the two-cells-per-register kernel: every shape up
+    to 4^3, ragged multi-block DNA and protein shapes (empty sequences included), related
+    triplets whose values force rebases; exact against oracle.align_type. The batch must run on
+    the two-per-register kernel."""
     rng = np.random.default_rng(81)
     cases = [(DNA, [rand_trip(rng, s, 4) for s in itertools.product(range(5), repeat=3)]),
              (DNA, [rand_trip(rng, s, 4) for s in ((37, 70, 130), (129, 33, 65), (0, 100, 100),
@@ -203,7 +207,7 @@ def test_vl_semiglobal_exact(tile):
              (DNA, list(synth.config1(seed=82, L=600).triplets)),
              (synth.protein_scoring(83), list(synth.config3(seed=83, L=420).triplets))]
     for sc, trips in cases:
-        plan = _semi_plan(sc, tile)
+        plan = _semi_plan(sc, tile, flags)
         try:
             bt = B.trioseq_batch_create(plan, [strs(trips[0], sc)])
             try:
@@ -212,7 +216,7 @@ def test_vl_semiglobal_exact(tile):
             finally:
                 B.trioseq_batch_destroy(bt)
             got = B.trioseq_align_batch(plan, [strs(t, sc) for t in trips])
-            want = [oracle.align_type(*t, sc.sub, sc.gap, oracle.SEMIGLOBAL) for t in trips]
+            want = [oracle.align_type(*t, sc.sub, sc.gap, kind) for t in trips]
             assert got.tolist() == want
             for t, w in list(zip(trips, want))[:3]:  # alone as well as in the batch
                 assert int(B.trioseq_align_batch(plan, [strs(t, sc)])[0]) == w
@@ -221,12 +225,13 @@ def test_vl_semiglobal_exact(tile):
 
 
 @pytest.mark.parametrize("tile", ["8x16", "8x8v"])
-def test_vl_semiglobal_full_size_equals_int32(tile):
-    """The n=4000 protein triplet, semi-global: the two-per-register kernel equals the int32 kernel
-    (itself exact against the oracle on every smaller case)."""
+@pytest.mark.parametrize("flags", [B.SEMIGLOBAL, B.LOCAL], ids=["semiglobal", "local"])
+def test_vl_variant_types_full_size_equal_int32(tile, flags):
+    """The n=4000 protein triplet, semi-global and local: the two-per-register kernel equals the
+    int32 kernel (itself exact against the oracle on every smaller case)."""
     w = synth.config3()
     s = [strs(t, w.scoring) for t in w.triplets]
-    ref, vl = _semi_plan(w.scoring, "8x8"), _semi_plan(w.scoring, tile)
+    ref, vl = _semi_plan(w.scoring, "8x8", flags), _semi_plan(w.scoring, tile, flags)
     try:
         assert B.trioseq_align_batch(vl, s).tolist() == B.trioseq_align_batch(ref, s).tolist()
     finally:
