@@ -147,7 +147,7 @@ struct AffineParams {
   const int8_t* seq;
   const int32_t* sub;     // KP x KP table of sigma (the virtual row and column unused)
   int32_t gap, gap_open;  // alpha (per residue against a gap), gamma (per maximal gap run)
-  int32_t* planes;        // per CTA: 4 plane buffers of plane_cells * kAffineStates int32
+  int32_t* planes;        // per CTA: 4 plane buffers of plane_cells * 16 int32 (13 used)
   int64_t plane_cells;    // (max b + 1) * (max c + 1) over the batch
   int32_t* queue;         // zeroed before launch
   int32_t* scores;

@@ -367,7 +367,7 @@ trioseq_status build_affine(trioseq_plan_s* plan, trioseq_batch_s* bt) {
   if (affine_occupancy(&bpm) != 0 || bpm <= 0) return TRIOSEQ_ECUDA;
   bt->grid = (int)std::max<size_t>(1, std::min<size_t>((size_t)plan->sms * bpm, n));
   bt->affine_cells = maxcells;
-  bt->face_ints = (size_t)bt->grid * 4 * (size_t)maxcells * kAffineStates;
+  bt->face_ints = (size_t)bt->grid * 4 * (size_t)maxcells * 16;  // 16 int32 per cell (13 used)
   bt->seq_bytes = bt->seq.size();
   layout_inputs(bt);
   return TRIOSEQ_OK;
