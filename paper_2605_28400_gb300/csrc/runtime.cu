@@ -222,7 +222,6 @@ struct trioseq_plan_s {
   int64_t wait_ns = 2000000000LL;  // 2 s without progress = give up
   bool test_wait_unset = false;    // test switch: first-wave warps wait on a flag nothing sets
   bool test_poison = false;        // test switch: boundary records start as a large garbage value
-  int grid_ctas = 0;               // TRIOSEQ_GRID: at most this many CTAs per launch (0: all fit)
   bool graphs = true;              // trioseq_batch_run replays a captured CUDA graph
   bool packed16 = true;            // pair score-only global triplets in int16 halves if they fit
   bool sig2_nonneg = false;        // every sigma'' >= 0: the biased packed mode applies
@@ -709,7 +708,6 @@ trioseq_status build_batch(trioseq_plan_s* plan, const trioseq_triplet* trip, si
     return TRIOSEQ_ECUDA;
   const int want = env_int("TRIOSEQ_CTAS_PER_SM", bpm);
   bt->grid = plan->sms * std::max(1, std::min(bpm, want));
-  if (plan->grid_ctas > 0) bt->grid = std::min(bt->grid, plan->grid_ctas);
   return TRIOSEQ_OK;
 }
 
@@ -1137,7 +1135,6 @@ trioseq_status trioseq_plan(const trioseq_scoring* sc, uint32_t max_len_hint, ui
     plan->wait_ns = (int64_t)std::max(1, env_int("TRIOSEQ_WAIT_MS", 2000)) * 1000000LL;
     plan->test_wait_unset = env_int("TRIOSEQ_TEST_WAIT_UNSET", 0) != 0;
     plan->test_poison = env_int("TRIOSEQ_TEST_POISON", 0) != 0;
-    plan->grid_ctas = std::max(0, env_int("TRIOSEQ_GRID", 0));
     g_alloc_calls.store(0);
     g_alloc_fail_at.store(std::max(0, env_int("TRIOSEQ_TEST_FAIL_ALLOC", 0)));
     {

@@ -599,24 +599,50 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
           best = max(best, max(dlo, dhi) + Bt - g2 * (s + j0 + k0) - 32768);
         }
         if (AT == kSemiGlobal) {
-          // cells on a last slice: the row j = b and the column k = c of each half's slice, and
-          // the whole face i = a when a half reaches it; M = M' - g2*(i+j+k)
-          const bool lo_ok = s <= a, hi_ok = s >= 1;
+          // Cells on a last slice, M = M' - g2*(i+j+k): the face i = a when each half reaches
+          // it, and the row j = b / column k = c of each half's slice. Edge lanes all share one
+          // row (pb) or column, so only its block runs.
           const int base_lo = ub - g2 * (s + j0 + k0), base_hi = ub - g2 * (s - 1 + j0 + k0 + NH);
-          if (edgeJ || edgeK || s == a || s - 1 == a) {
+          const auto m_lo = [&](int pp, int qq) {
+            return (int)((unsigned)P[pp][qq] & 0xffffu) + base_lo - g2 * (pp + qq);
+          };
+          const auto m_hi = [&](int pp, int qq) {
+            return (int)((unsigned)P[pp][qq] >> 16) + base_hi - g2 * (pp + qq);
+          };
+          if (s == a || s - 1 == a) {
 #pragma unroll
             for (int pp = 0; pp < NJ; ++pp)
 #pragma unroll
               for (int qq = 0; qq < NH; ++qq) {
-                const unsigned w = (unsigned)P[pp][qq];
-                const bool in_lo = pp <= pb && qq <= qlo, in_hi = pp <= pb && qq <= qhi;
-                const bool clo = lo_ok && in_lo &&
-                                 (s == a || (edgeJ && pp == pb) || (edgeK && qq == qlo));
-                const bool chi = hi_ok && in_hi &&
-                                 (s - 1 == a || (edgeJ && pp == pb) || (edgeK && qq == qhi));
-                if (clo) best = max(best, (int)(w & 0xffffu) + base_lo - g2 * (pp + qq));
-                if (chi) best = max(best, (int)(w >> 16) + base_hi - g2 * (pp + qq));
+                if (s == a && pp <= pb && qq <= qlo) best = max(best, m_lo(pp, qq));
+                if (s - 1 == a && pp <= pb && qq <= qhi) best = max(best, m_hi(pp, qq));
               }
+          }
+          if (edgeJ) {
+#pragma unroll
+            for (int pp = 0; pp < NJ; ++pp)
+              if (pp == pb) {
+#pragma unroll
+                for (int qq = 0; qq < NH; ++qq) {
+                  if (s <= a && qq <= qlo) best = max(best, m_lo(pp, qq));
+                  if (s >= 1 && qq <= qhi) best = max(best, m_hi(pp, qq));
+                }
+              }
+          }
+          if (edgeK) {
+#pragma unroll
+            for (int qq = 0; qq < NH; ++qq) {
+              if (qq == qlo && s <= a) {
+#pragma unroll
+                for (int pp = 0; pp < NJ; ++pp)
+                  if (pp <= pb) best = max(best, m_lo(pp, qq));
+              }
+              if (qq == qhi && s >= 1) {
+#pragma unroll
+                for (int pp = 0; pp < NJ; ++pp)
+                  if (pp <= pb) best = max(best, m_hi(pp, qq));
+              }
+            }
           }
         }
         if (AT == kGlobal && owns_end && (end_h ? s - 1 == a : s == a)) {
