@@ -715,15 +715,19 @@ def aux_measurements(B, torch, stream, flush, sms, clock_mhz, skip: str, cpu_leg
         plan = B.trioseq_plan(w.scoring.alphabet, w.scoring.sub, w.scoring.gap, flags)
         tuned = B.trioseq_plan_autotune(plan, triplet_strings(w), B.SCORE_ONLY)
         bt = B.trioseq_batch_create(plan, triplet_strings(w), B.SCORE_ONLY)
+        binfo = B.trioseq_batch_info(bt)
+        packing = binfo.get("packing", 1)
         sm, km, _, sc = time_batch(B, torch, bt, 5, 3, stream, flush, 1)
         kmean = statistics.mean(km)
         ach = ops * w.cells / (kmean / 1e3) / 1e12
-        peak = sms * lanes * clock_mhz * 1e6 / 1e12
+        peak = packing * sms * lanes * clock_mhz * 1e6 / 1e12
         out[f"protein4000_{name}"] = {
             "workload": f"{w.name}: alignment type {name} (Sec. II), score only",
             "gcups": w.cells / (statistics.mean(sm) / 1e3) / 1e9, "kernel_ms": kmean,
             "score": int(sc[0]), "tuned": tuned, "ops_per_cell": ops,
-            "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TOPS (int32)",
+            "tile": binfo["tile_label"], "kernel": binfo["kernel"],
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak,
+                         "unit": "TOPS (int32)" if packing == 1 else "TOPS (int16x2 lanes)",
                          "frac": ach / peak}}
         if extra:
             out[f"protein4000_{name}"]["roofline"]["frac_counting_type_ops"] = {

@@ -394,17 +394,18 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
                                  : (int)__byte_perm((unsigned)v, (unsigned)mine, 0x5432);
         }
         if (AT != kGlobal && (J == 0 || K == 0)) {  // axis feeds (warp-uniform branch)
-          if (J == 0 && r == 0) {
+          // Only two kinds of halo cells are finite: those of slice -1 (each lane meets slice -1
+          // once, the step before its first) and the i-axis feed M'[s][-1][-1] of lane (0,0)
+          // of task (0,0); every other halo cell of the first row or column stays -infinity, as
+          // staged. So the per-step cost is one value on one lane.
+          if (J == 0 && r == 0 && s == -1) {
 #pragma unroll
-            for (int qq = 0; qq <= NH; ++qq) {
-              const int kl = k0 + qq - 1;  // low half: slice s (the high half's feed is at s == 0)
-              const unsigned w = (unsigned)rowCur[qq];
-              const unsigned lo = s == -1 ? (unsigned)feed(g2 * kl)
-                                          : ((s >= 0 && kl == -1) ? (unsigned)feed(g2 * s)
-                                                                  : (w & 0xffffu));
-              rowCur[qq] = (int)((w & 0xffff0000u) | lo);
-            }
+            for (int qq = 0; qq <= NH; ++qq)
+              rowCur[qq] = (int)(((unsigned)rowCur[qq] & 0xffff0000u) |
+                                 (unsigned)feed(g2 * (k0 + qq - 1)));
           }
+          if (J == 0 && K == 0 && lane == 0 && s >= 0)
+            rowCur[0] = (int)(((unsigned)rowCur[0] & 0xffff0000u) | (unsigned)feed(g2 * s));
           if (K == 0 && lc == 0 && s == -1) {
 #pragma unroll
             for (int pp = 0; pp < NJ; ++pp)
