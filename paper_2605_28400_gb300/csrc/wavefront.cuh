@@ -527,18 +527,17 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
           colCur[pp] = (lc == 0) ? ec[pp] : v;
         }
         if (AT == kSemiGlobal && (J == 0 || K == 0)) {  // axis feeds (warp-uniform branch)
-          if (J == 0 && r == 0) {
+          // Finite only at slice -1 (once per lane) and for the i-axis feed M'[s][-1][-1] of
+          // lane 0 of task (0,0): the first row and column of tasks pace every task after them,
+          // so their per-step cost stays at one value on one lane.
+          if (J == 0 && r == 0 && s == -1) {
 #pragma unroll
-            for (int qq = 0; qq <= NK; ++qq) {
-              const int k = k0 + qq - 1;
-              rowCur[qq] = (s == -1) ? axis_feed(g2 * k)
-                                     : ((s >= 0 && k == -1) ? axis_feed(g2 * s) : rowCur[qq]);
-            }
+            for (int qq = 0; qq <= NK; ++qq) rowCur[qq] = axis_feed(g2 * (k0 + qq - 1));
           }
-          if (K == 0 && lc == 0) {
+          if (J == 0 && K == 0 && lane == 0 && s >= 0) rowCur[0] = axis_feed(g2 * s);
+          if (K == 0 && lc == 0 && s == -1) {
 #pragma unroll
-            for (int pp = 0; pp < NJ; ++pp)
-              colCur[pp] = (s == -1) ? axis_feed(g2 * (j0 + pp)) : colCur[pp];
+            for (int pp = 0; pp < NJ; ++pp) colCur[pp] = axis_feed(g2 * (j0 + pp));
           }
         }
       }

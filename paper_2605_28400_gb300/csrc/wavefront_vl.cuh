@@ -79,11 +79,12 @@ __host__ __device__ constexpr int vl_diag_index(int pp, int qq) {
   return e + (pp - lo);
 }
 
-// AT: the alignment type of Sec. II. Semi-global and local feed their zero axes through the halo
-// cells at j = -1 / k = -1 (as wavefront_kernel does, in the relative halves). Semi-global takes
-// the best original-frame score over the last slices i = a, j = b, k = c. Local adds v = 0 to
-// Eq. 1, i.e. M' >= -2*alpha*(i+j+k), as one more packed max in pass 1 (the floor is the same
-// along an anti-diagonal of a half), and takes the best original-frame score over every cell:
+// AT: the alignment type of Sec. II. Semi-global feeds its zero axes through the halo cells at
+// j = -1 / k = -1 (as wavefront_kernel does, in the relative halves) and takes the best
+// original-frame score over the last slices i = a, j = b, k = c. Local adds v = 0 to Eq. 1, i.e.
+// M' >= -2*alpha*(i+j+k), which also gives its zero axes, as one more packed max in pass 1 (the
+// floor is the same along an anti-diagonal of a half), and takes the best original-frame score
+// over every cell:
 // per step, each cell's M relative to a per-step reference is folded into a packed 16-bit
 // maximum by one add-max, and the step's maximum into a 32-bit best.
 template <int NJ, int NH, int CS, int AT>
@@ -326,7 +327,7 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
     // (1,1,0)), M'[-1][j][-1] = g2*j the j axis (move (1,0,1)), M'[i][-1][-1] = g2*i the i axis
     // (move (0,1,1)); lane 0 starts from slice -1 (low halves; the high half's are reset).
     const auto feed = [&](int v) { return max(v + nb, 0); };
-    if (AT != kGlobal && lane == 0) {
+    if (AT == kSemiGlobal && lane == 0) {
       if (J == 0) {
 #pragma unroll
         for (int qq = 0; qq <= NH; ++qq) rowB[qq] = feed(g2 * max(k0 + qq - 1, 0));
@@ -393,7 +394,7 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
           colCur[pp] = (lc == 0) ? (int)__byte_perm(ring_lo, (unsigned)mine, 0x5410)
                                  : (int)__byte_perm((unsigned)v, (unsigned)mine, 0x5432);
         }
-        if (AT != kGlobal && (J == 0 || K == 0)) {  // axis feeds (warp-uniform branch)
+        if (AT == kSemiGlobal && (J == 0 || K == 0)) {  // axis feeds (warp-uniform branch)
           // Only two kinds of halo cells are finite: those of slice -1 (each lane meets slice -1
           // once, the step before its first) and the i-axis feed M'[s][-1][-1] of lane (0,0)
           // of task (0,0); every other halo cell of the first row or column stays -infinity, as
@@ -530,7 +531,7 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
           }
 #pragma unroll
           for (int qq = 0; qq <= NH; ++qq) rowCur[qq] &= 0xffff;
-          if (AT != kGlobal && J == 0 && r == 0) {
+          if (AT == kSemiGlobal && J == 0 && r == 0) {
             // the high half's halo row j = -1 at slice -1 is the k-axis feed M'[-1][-1][k]
 #pragma unroll
             for (int qq = 0; qq <= NH; ++qq)
