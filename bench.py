@@ -606,6 +606,18 @@ def serving_measurement(B, n_req: int = 10000, load: float = 0.7, n_cal: int = 6
     ts, td, _, _ = _serve(B, srv, reqs[:n_cal], strs[:n_cal], None, cap)
     B.trioseq_server_destroy(srv)
     capacity = sum(cells[:n_cal]) / (max(td.values()) - min(ts.values())) / 1e9
+    # The same n_cal requests as four plain batches, one per (scheme, mode) group, back to back
+    # (host strings in, results out, one trioseq_align_batch each): what the server's burst is
+    # compared with, so that the gap splits into the mix's own cost and serving's overhead.
+    groups = {}
+    for i, r in enumerate(reqs[:n_cal]):
+        groups.setdefault((r["protein"], r["traceback"]), []).append(i)
+    for rep in range(2):  # the first pass sizes the plans' workspaces, the second is timed
+        t0 = time.perf_counter()
+        for (prot_, tb_), idx in groups.items():
+            B.trioseq_align_batch(plans[1 if prot_ else 0], [strs[i] for i in idx],
+                                  B.WITH_TRACEBACK if tb_ else B.SCORE_ONLY)
+        batched_mix = sum(cells[:n_cal]) / (time.perf_counter() - t0) / 1e9
     rate = load * capacity * 1e9 / mean_cells  # requests per second
     srv = B.trioseq_server_create(plans)
     t_sub, t_done, results, tickets = _serve(B, srv, reqs, strs, rate, cap)
@@ -628,6 +640,7 @@ def serving_measurement(B, n_req: int = 10000, load: float = 0.7, n_cal: int = 6
     return {"requests": len(reqs), "arrival_rate_per_s": rate,
             "equals_oracle_on_stored_prefix": golden,
             "server_capacity_gcups": capacity, "capacity_burst_requests": n_cal,
+            "same_mix_as_four_batches_gcups": batched_mix,
             "load_vs_server_capacity": load,
             "mean_cells_per_request": mean_cells, "p50_ms": lat[len(lat) // 2],
             "p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))], "max_ms": lat[-1],
@@ -896,6 +909,10 @@ def main():
     ap.add_argument("--workload", choices=sorted(workloads()), default="protein4000")
     ap.add_argument("--no-aux", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--tile", default=None,
+                    help="force the wavefront tile (e.g. 8x16, 8x8v, 8x8, 8x4) instead of autotuning")
+    ap.add_argument("--ti", type=int, default=None,
+                    help="progress interval with --tile (default: the plan's, 8)")
     ap.add_argument("--alu-rate", action="store_true",
                     help="print the measured int32 instruction-form rates (trioseq_alu_rate) and exit")
     args = ap.parse_args()
@@ -942,8 +959,18 @@ def main():
     uuid = str(getattr(props, "uuid", "") or "")
     uuid = uuid if uuid.startswith("GPU-") else (f"GPU-{uuid}" if uuid else None)
 
+    if args.tile:  # a forced tile (profiling one kernel): no autotuner launches before it
+        os.environ["TRIOSEQ_TB_TILE" if tb else "TRIOSEQ_SCORE_TILE"] = args.tile
+        if args.ti:
+            os.environ["TRIOSEQ_TI"] = str(args.ti)
     plan = B.trioseq_plan(w.scoring.alphabet, w.scoring.sub, w.scoring.gap)
-    tuned = B.trioseq_plan_autotune(plan, strs, mode)  # untimed: picks tile and interval
+    for k in ("TRIOSEQ_TB_TILE", "TRIOSEQ_SCORE_TILE", "TRIOSEQ_TI"):
+        if args.tile:
+            os.environ.pop(k, None)
+    if args.tile:
+        tuned = {"tile": None, "ti": args.ti or 8, "forced": args.tile}
+    else:
+        tuned = B.trioseq_plan_autotune(plan, strs, mode)  # untimed: picks tile and interval
     bt = B.trioseq_batch_create(plan, strs, mode)
     info = B.trioseq_batch_info(bt)
     stream = torch.cuda.current_stream()
@@ -1024,7 +1051,7 @@ def main():
                        "mode": "score+traceback" if tb else "score",
                        "column_tasks": info["tasks"],
                        "tile": tile,
-                       "progress_interval": tuned["ti"], "autotuned": True,
+                       "progress_interval": tuned["ti"], "autotuned": not args.tile,
                        "l2": "256 MiB flush between timed steps (outside the events)",
                        "parallelism": parallelism},
             "roofline": roof,
