@@ -19,6 +19,9 @@
 namespace trioseq {
 
 constexpr int kNeg = -(1 << 30);   // -infinity sentinel (never accumulates: see the kernel)
+// A boundary-record slot not yet written (the byte 0x80 repeated): below -infinity and below any
+// key, so no stored value can equal it.
+constexpr int kRecordSentinel = (int)0x80808080u;
 constexpr int kPR = 4;             // lanes of a warp along j
 constexpr int kPC = 8;             // lanes of a warp along k
 constexpr int kMaxAlphabet = 32;
@@ -111,6 +114,9 @@ struct WaveParams {
   int32_t pace_n, pace_T;
   const int32_t* pace_flag;
   int32_t one;         // 1, as a launch argument (multiply-adds by it stay on the FMA pipe)
+  // Traceback launches: the boundary records start as kRecordSentinel (set before the launch)
+  // and a consumer waits on the record slots themselves instead of the producers' progress.
+  int32_t data_flags;
 };
 
 struct WalkParams {

@@ -222,6 +222,7 @@ struct trioseq_plan_s {
   int64_t wait_ns = 2000000000LL;  // 2 s without progress = give up
   bool test_wait_unset = false;    // test switch: first-wave warps wait on a flag nothing sets
   bool test_poison = false;        // test switch: boundary records start as a large garbage value
+  int data_flags = -1;             // TRIOSEQ_DATA_FLAGS: records as readiness flags (-1: chosen)
   bool graphs = true;              // trioseq_batch_run replays a captured CUDA graph
   bool packed16 = true;            // pair score-only global triplets in int16 halves if they fit
   bool sig2_nonneg = false;        // every sigma'' >= 0: the biased packed mode applies
@@ -833,6 +834,17 @@ trioseq_status run(trioseq_batch_s* bt, cudaStream_t st) {
   p.wait_ns = plan->wait_ns;
   p.g2 = -2 * plan->gap;
   p.one = 1;
+  // One-triplet traceback launches, whose time is the wavefront ramp: records carry their own
+  // readiness (sentinel-filled here, in the launch's stream order), so each producer-consumer
+  // level lags by its skew alone instead of also by a publication interval and a flag round
+  // trip; progress is then published only at the end of a task. TRIOSEQ_DATA_FLAGS at plan
+  // creation forces it on (1) or off (0) for every traceback launch.
+  p.data_flags = tb && !bt->slab && (plan->data_flags >= 0 ? plan->data_flags : bt->n == 1);
+  if (p.data_flags) {
+    if ((e = cudaMemsetAsync(p.faces, 0x80, bt->face_ints * sizeof(int32_t), st)) != cudaSuccess)
+      return cuda_status(e);
+    p.TI = 1 << 30;
+  }
   const int warps_per_cta = wavefront_block_threads(bt->packed) / 32;  // resident warps per CTA
   if (plan->test_wait_unset && !bt->slab) {
     // Test of the bounded waits: every first-wave task but queue task 0 waits on a word of the
@@ -841,7 +853,8 @@ trioseq_status run(trioseq_batch_s* bt, cudaStream_t st) {
     p.pace_n = bt->grid * warps_per_cta;
     p.pace_T = 1 << 20;
     p.pace_flag = prog + bt->tasks.size() + 48;
-  } else if (!bt->slab && plan->pace && bt->tasks.size() >= 2 * (size_t)bt->grid * warps_per_cta) {
+  } else if (!bt->slab && plan->pace && !p.data_flags &&
+             bt->tasks.size() >= 2 * (size_t)bt->grid * warps_per_cta) {
     // pace the first wave against the progress of queue task 0, the (0,0) block of its triplet
     const TripDesc& d0 = bt->desc[bt->tasks[0].trip];
     p.pace_n = bt->grid * warps_per_cta;
@@ -1135,6 +1148,7 @@ trioseq_status trioseq_plan(const trioseq_scoring* sc, uint32_t max_len_hint, ui
     plan->wait_ns = (int64_t)std::max(1, env_int("TRIOSEQ_WAIT_MS", 2000)) * 1000000LL;
     plan->test_wait_unset = env_int("TRIOSEQ_TEST_WAIT_UNSET", 0) != 0;
     plan->test_poison = env_int("TRIOSEQ_TEST_POISON", 0) != 0;
+    plan->data_flags = env_int("TRIOSEQ_DATA_FLAGS", -1);
     g_alloc_calls.store(0);
     g_alloc_fail_at.store(std::max(0, env_int("TRIOSEQ_TEST_FAIL_ALLOC", 0)));
     {

@@ -105,6 +105,28 @@ __device__ __forceinline__ int4 ld_cg_if(const int4* p, bool pr, int neg) {
       : "l"(p), "r"((int)pr), "r"(neg));
   return v;
 }
+// gpu-scope relaxed 16-byte accesses of the traceback kernels' boundary records. Each 32-bit
+// element is single-copy atomic, so a reader sees either the sentinel a record slot starts as or
+// its final value, never a mix (records are written once).
+__device__ __forceinline__ int4 ld_relaxed_if(const int4* p, bool pr, int neg) {
+  int4 v;
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.b32 q, %5, 0;\n mov.b32 %0, %6;\n mov.b32 %1, %6;\n"
+      " mov.b32 %2, %6;\n mov.b32 %3, %6;\n @q ld.relaxed.gpu.global.v4.s32 {%0,%1,%2,%3}, [%4];\n}"
+      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+      : "l"(p), "r"((int)pr), "r"(neg));
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_if(int4* p, int4 v, bool pr) {
+  asm volatile(
+      "{\n .reg .pred q;\n setp.ne.b32 q, %5, 0;\n @q st.relaxed.gpu.global.v4.s32 [%0], {%1,%2,%3,%4};\n}"
+      ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w), "r"((int)pr));
+}
+__device__ __forceinline__ void st_relaxed_if(int* p, int v, bool pr) {
+  asm volatile("{\n .reg .pred q;\n setp.ne.b32 q, %2, 0;\n @q st.relaxed.gpu.global.s32 [%0], %1;\n}"
+               ::"l"(p), "r"(v), "r"((int)pr));
+}
+
 __device__ __forceinline__ void st_shared_if(int4* p, int4 v, bool pr) {
   asm volatile(
       "{\n .reg .pred q;\n setp.ne.b32 q, %5, 0;\n @q st.shared.v4.s32 [%0], {%1,%2,%3,%4};\n}"
@@ -409,6 +431,14 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
     // on at step u, so the edge lanes take the ring value as is.
     int4 pf = make_int4(NEG, NEG, NEG, NEG);
     int pf_u = -1;
+    // Records as their own readiness flags (traceback launches with WaveParams::data_flags): the
+    // records start as kRecordSentinel, and a staged piece is reloaded until none of its written
+    // slots holds it, so no progress flag is polled and none is published while the task runs.
+    const bool df = TB && !SLAB && p.data_flags != 0;
+    const int* pf_src = nullptr;
+    bool pf_have = false;
+    // slots 0..2 of the first j-record piece are never written (only the corner, slot 3, is)
+    const bool pf_corner_only = cp_kind == 1 && cp_col == 0;
     // Lead of a piece's load over its use, in steps. Traceback keys serve single triplets whose
     // time is the wavefront ramp, where each producer-consumer level lags by the lead: 1 step
     // (the load then has the rest of one step to land). Score mode runs many levels at once
@@ -416,7 +446,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
     constexpr int kAh = TB ? 1 : 2;
     auto fetch = [&](int u) {
       const int needJ = min(u + kPR, T), needK = min(u + kPC, T);
-      if (cachedJ < needJ || cachedK < needK) {  // warp-uniform
+      if (!df && (cachedJ < needJ || cachedK < needK)) {  // warp-uniform
         bool okl = true;
         int cj = cachedJ, ck = cachedK;
         if (lane == 0) {
@@ -434,7 +464,13 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
         const bool have = ok && cp_kind != 0 && sl >= 0 && sl <= a && (cp_kind == 1 ? J > 0 : K > 0);
         const int* src = (cp_kind == 1) ? srcJ + (int64_t)sl * G::RJ + cp_col
                                         : srcK + (int64_t)sl * G::RK + cp_col;
-        pf = ld_cg_if(reinterpret_cast<const int4*>(src), have, NEG);  // src is read only if have
+        if constexpr (TB) {
+          pf = ld_relaxed_if(reinterpret_cast<const int4*>(src), have, NEG);
+          pf_src = src;
+          pf_have = have;
+        } else {
+          pf = ld_cg_if(reinterpret_cast<const int4*>(src), have, NEG);  // src read only if have
+        }
       }
       if (SLAB && p.plane_in && sl == -1 && cp_kind != 0 && (cp_kind == 1 ? J > 0 : K > 0)) {
         // Slab launch, local slice -1: the producer's record of that slice is plane i0 - 1.
@@ -450,6 +486,31 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
       }
     };
     auto park = [&]() {
+      if (TB && df) {
+        const auto missing = [&](const int4& v) {
+          return pf_have && (v.w == kRecordSentinel ||
+                             (!pf_corner_only && (v.x == kRecordSentinel || v.y == kRecordSentinel ||
+                                                  v.z == kRecordSentinel)));
+        };
+        bool miss = missing(pf);
+        if (__any_sync(kFull, miss)) {  // bounded wait for the producer's stores
+          const uint64_t t0 = global_ns();
+          unsigned ns = 32;
+          for (;;) {
+            __nanosleep(ns);
+            if (ns < 256) ns <<= 1;
+            if (miss) {
+              pf = ld_relaxed_if(reinterpret_cast<const int4*>(pf_src), true, NEG);
+              miss = missing(pf);
+            }
+            if (!__any_sync(kFull, miss)) break;
+            if (__shfl_sync(kFull, (int64_t)(global_ns() - t0) > p.wait_ns ? 1 : 0, 0)) {
+              ok = false;
+              break;
+            }
+          }
+        }
+      }
       st_shared_if(reinterpret_cast<int4*>(ring + (pf_u & (kRing - 1)) * G::SLOT + cp_dst), pf,
                    cp_kind != 0);
     };
@@ -787,24 +848,33 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
         {  // j-record: the last lane row's bottom tile rows (predicated, no branch)
           const bool out_j = r == kPR - 1 && has_out_j;
           int* dst = dstJ + (int64_t)s * G::RJ;
-          st_global_if(dst + 3, colCur[NJ - 1], out_j && lc == 0);  // corner for lane (0,0)
+          if constexpr (TB)
+            st_relaxed_if(dst + 3, colCur[NJ - 1], out_j && lc == 0);  // corner for lane (0,0)
+          else
+            st_global_if(dst + 3, colCur[NJ - 1], out_j && lc == 0);
           int4* d4 = reinterpret_cast<int4*>(dst + 4 + lc * NK);
 #pragma unroll
-          for (int q4 = 0; q4 < NK / 4; ++q4)
-            st_global_if(d4 + q4,
-                         make_int4(P[NJ - 1][4 * q4], P[NJ - 1][4 * q4 + 1],
-                                   P[NJ - 1][4 * q4 + 2], P[NJ - 1][4 * q4 + 3]),
-                         out_j);
+          for (int q4 = 0; q4 < NK / 4; ++q4) {
+            const int4 v = make_int4(P[NJ - 1][4 * q4], P[NJ - 1][4 * q4 + 1],
+                                     P[NJ - 1][4 * q4 + 2], P[NJ - 1][4 * q4 + 3]);
+            if constexpr (TB)
+              st_relaxed_if(d4 + q4, v, out_j);
+            else
+              st_global_if(d4 + q4, v, out_j);
+          }
         }
         {  // k-record: the last lane column's right tile columns
           const bool out_k = lc == kPC - 1 && has_out_k;
           int4* d4 = reinterpret_cast<int4*>(dstK + (int64_t)s * G::RK + r * NJ);
 #pragma unroll
-          for (int p4 = 0; p4 < NJ / 4; ++p4)
-            st_global_if(d4 + p4,
-                         make_int4(P[4 * p4][NK - 1], P[4 * p4 + 1][NK - 1],
-                                   P[4 * p4 + 2][NK - 1], P[4 * p4 + 3][NK - 1]),
-                         out_k);
+          for (int p4 = 0; p4 < NJ / 4; ++p4) {
+            const int4 v = make_int4(P[4 * p4][NK - 1], P[4 * p4 + 1][NK - 1],
+                                     P[4 * p4 + 2][NK - 1], P[4 * p4 + 3][NK - 1]);
+            if constexpr (TB)
+              st_relaxed_if(d4 + p4, v, out_k);
+            else
+              st_global_if(d4 + p4, v, out_k);
+          }
         }
         if (AT == kSemiGlobal && (edgeJ || edgeK)) {
           // Cells of this slice on the last row j = b or the last column k = c, in the original
