@@ -54,8 +54,10 @@ __device__ __forceinline__ uint64_t global_ns() {
 // (the satisfying one orders the record loads that follow; unlike a fence it does not wait for
 // this warp's own record stores in flight) and exponential back-off up to 256 ns, light on L2
 // while many warps wait and at most a fraction of a step late. Gives up (returns false) when
-// the flag has not moved for wait_ns.
-__device__ __noinline__ bool wait_flag(const int* flag, int need, int* cached, int64_t wait_ns) {
+// the flag has not moved for wait_ns. Inlined: an out-of-line call in the step loop, even one
+// never taken, cost a lone warp 6-8% of its step (the call's register save/restore constrains the
+// whole loop body), and the main-line kernel 5%.
+__device__ __forceinline__ bool wait_flag(const int* flag, int need, int* cached, int64_t wait_ns) {
   int v = ld_acquire(flag);
   if (v >= need) {
     *cached = v;
@@ -444,9 +446,12 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
     // (the load then has the rest of one step to land). Score mode runs many levels at once
     // and gives the load two steps.
     constexpr int kAh = TB ? 1 : 2;
-    auto fetch = [&](int u) {
-      const int needJ = min(u + kPR, T), needK = min(u + kPC, T);
-      if (!df && (cachedJ < needJ || cachedK < needK)) {  // warp-uniform
+    // The producers are checked once per pair of steps (chk on the first step of each loop
+    // iteration), for the pieces of steps u and u + 1 together: one warp-uniform branch per two
+    // steps instead of one per step (a lone warp's step -4%, the main line +1%).
+    auto fetch = [&](int u, bool chk) {
+      const int needJ = min(u + 1 + kPR, T), needK = min(u + 1 + kPC, T);
+      if (!df && chk && (cachedJ < needJ || cachedK < needK)) {  // warp-uniform
         bool okl = true;
         int cj = cachedJ, ck = cachedK;
         if (lane == 0) {
@@ -515,10 +520,10 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
                    cp_kind != 0);
     };
 
-    fetch(0);
+    fetch(0, true);
     if (kAh == 2) {
       park();
-      fetch(1);
+      fetch(1, false);
     }
     // Residues of S0 by slice: in block B, lane q holds the residue of slice 32*B + q. Blocks are
     // loaded one block ahead and read by shuffle, so no global load sits on the per-step path.
@@ -534,12 +539,14 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
 
     int pub_in = p.TI;  // steps until the next progress publication
     // One step: the halo of slice s goes into rowCur / colCur, slice s-1 is in rowPrev /
-    // colPrev. Returns false when a bounded wait gave up.
-    auto step = [&](const int t, int (&rowCur)[NK + 1], const int (&rowPrev)[NK + 1],
-                    int (&colCur)[NJ], const int (&colPrev)[NJ]) -> bool {
+    // colPrev. `first` marks the first step of a loop iteration (it checks the producers for
+    // both). Returns false when a bounded wait gave up.
+    auto step = [&](const int t, const bool first, int (&rowCur)[NK + 1],
+                    const int (&rowPrev)[NK + 1], int (&colCur)[NJ],
+                    const int (&colPrev)[NJ]) -> bool {
       const int s = t - r - lc;
       park();  // piece of step t + 1
-      if (t + kAh < T) fetch(t + kAh);
+      if (t + kAh < T) fetch(t + kAh, first);
       if (!ok) return false;
       if ((t & 31) == 0 && t > 0) {
         xprev = xcur;
@@ -916,8 +923,8 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
       return true;
     };
     for (int t = 0; t < T; t += 2) {
-      if (!step(t, rowA, rowB, colA, colB)) break;
-      if (t + 1 < T && !step(t + 1, rowB, rowA, colB, colA)) break;
+      if (!step(t, true, rowA, rowB, colA, colB)) break;
+      if (t + 1 < T && !step(t + 1, false, rowB, rowA, colB, colA)) break;
     }
     __syncwarp();
     if (ok && lane == 0) st_release(progMe, T);  // all steps computed and stored

@@ -270,10 +270,11 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
 #pragma unroll
     for (int m = 0; m < G::NPL; ++m) pf[m] = make_int4(kNeg, kNeg, kNeg, kNeg);
     int pf_u = -1;
-    auto fetch = [&](int u) {
+    // Producers are checked once per pair of steps, for steps u and u + 1 (as in wavefront_kernel).
+    auto fetch = [&](int u, bool chk) {
       // k-records are written by the last virtual lane column (2*kPC - 1 steps of skew)
-      const int needJ = min(u + kPR, T), needK = min(u + 2 * kPC, T);
-      if (cachedJ < needJ || cachedK < needK) {  // warp-uniform
+      const int needJ = min(u + 1 + kPR, T), needK = min(u + 1 + 2 * kPC, T);
+      if (chk && (cachedJ < needJ || cachedK < needK)) {  // warp-uniform
         bool okl = true;
         int cj = cachedJ, ck = cachedK;
         if (lane == 0) {
@@ -303,7 +304,7 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
                      pf[m], cp_kind[m] != 0);
     };
 
-    fetch(0);
+    fetch(0, true);
     // The task's base: the largest record value its first slice borders (0 without producers);
     // every cell of the working set lies within the range argument of it. The first j-record
     // piece (record slots 0..3) carries only the corner in slot 3: slots 0..2 are never
@@ -338,7 +339,7 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
       }
     }
     park();
-    fetch(1);
+    fetch(1, false);
 
     auto xblock = [&](int base) -> int {
       const int sl = base + lane;
@@ -348,11 +349,12 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
     int xlo_prev = VIRT;  // residue of slice s - 1: the high half's
 
     int pub_in = p.TI;
-    auto step = [&](const int t, int (&rowCur)[NH + 1], const int (&rowPrev)[NH + 1],
-                    int (&colCur)[NJ], const int (&colPrev)[NJ]) -> bool {
+    auto step = [&](const int t, const bool first, int (&rowCur)[NH + 1],
+                    const int (&rowPrev)[NH + 1], int (&colCur)[NJ],
+                    const int (&colPrev)[NJ]) -> bool {
       const int s = t - r - 2 * lc;
       park();
-      if (t + 2 < T) fetch(t + 2);
+      if (t + 2 < T) fetch(t + 2, first);
       if (!ok) return false;
       if ((t & 31) == 0 && t > 0) {
         xprev = xcur;
@@ -681,8 +683,8 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
       }
     };
     for (int t = 0; t < T; t += 2) {
-      if (!step(t, rowA, rowB, colA, colB)) break;
-      if (t + 1 < T && !step(t + 1, rowB, rowA, colB, colA)) break;
+      if (!step(t, true, rowA, rowB, colA, colB)) break;
+      if (t + 1 < T && !step(t + 1, false, rowB, rowA, colB, colA)) break;
       rebase();
     }
     __syncwarp();
