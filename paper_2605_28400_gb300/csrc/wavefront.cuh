@@ -676,11 +676,12 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
             const int Pxz = (qq == 0) ? colPrev[pp] : P[pp][qq - 1];
             const int Sx = P[pp][qq];
             if constexpr (PACK == 2) {
-              // Biased halves: the 32-bit multiply-adds are the two 16-bit adds (no carry out of
-              // the low half, engine.h), then unsigned per-half max(a + b, c).
+              // Biased halves: the 32-bit multiply-adds are the 16-bit adds (no carry out of the
+              // low half, engine.h), then unsigned per-half maxima (3-input, then add-max).
               const unsigned x2 = (unsigned)mad_lo(B[qq], p.one, mad_lo(A[pp], p.one, Pd));
-              unsigned e = __viaddmax_u16x2((unsigned)Pxy, (unsigned)A[pp], (unsigned)Sx);
-              e = __viaddmax_u16x2((unsigned)Pxz, (unsigned)B[qq], e);
+              const unsigned ea = (unsigned)mad_lo(A[pp], p.one, Pxy);
+              const unsigned eb = (unsigned)mad_lo(B[qq], p.one, Pxz);
+              const unsigned e = __vimax3_u16x2(ea, eb, (unsigned)Sx);
               P[pp][qq] = (int)__viaddmax_u16x2(x2, (unsigned)Cv[pp][qq], e);
             } else if constexpr (PACK == 1) {
               // Per 16-bit half: max(a + b, c). Sums from a -infinity operand are clamped at
@@ -692,13 +693,15 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
               e = __viaddmax_s16x2((unsigned)Pxz, (unsigned)B[qq], e);
               P[pp][qq] = (int)__viaddmax_s16x2(dd, (unsigned)Cv[pp][qq], e);
             } else {
-              // The diagonal sum Pd + A + B as two multiply-adds by a runtime 1 (p.one): they
-              // issue to the FMA pipe, so the ALU pipe, which bounds the step, carries 5 of the
-              // cell's 7 operations instead of 6.
-              const int x1 = max(Pxy + A[pp], Sx);
+              // The sums Pd + A + B, Pxy + A and Pxz + B as multiply-adds by a runtime 1 (p.one):
+              // they issue to the FMA pipe, so the ALU pipe, which bounds the step, carries only a
+              // 3-input max and one fused add-max in pass 1 (n=4000: 30.1 -> 28.1 ms against
+              // moving only the diagonal sum). The inner Pd + A is the left cell's Pxy + A.
               const int x2 = mad_lo(B[qq], p.one, mad_lo(A[pp], p.one, Pd));
-              const int x3 = max(x2 + Cv[pp][qq], x1);
-              P[pp][qq] = max(Pxz + B[qq], x3);
+              const int ea = mad_lo(A[pp], p.one, Pxy);
+              const int eb = mad_lo(B[qq], p.one, Pxz);
+              const int e = __vimax3_s32(ea, eb, Sx);
+              P[pp][qq] = __viaddmax_s32(x2, Cv[pp][qq], e);
             }
           };
           auto pass2 = [&](const int pp, const int qq) {
