@@ -167,9 +167,10 @@ class ClockSampler:
 
 def kernel_source_hash(tile: str) -> str:
     """Hash of the sources a tile's wavefront kernel is compiled from: the two-cells-per-register
-    kernel (tile label ending in 'v') or the int32 / two-triplets kernel family."""
+    kernel (tile 8x16, or a label ending in 'v', 's' or 't') or the int32 / two-triplets kernel
+    family."""
     common = ("wavefront.cuh", "engine.h")
-    own = (("wavefront_vl.cuh", "kernels_vl.cu") if tile.endswith(("v", "s")) or tile == "8x16"
+    own = (("wavefront_vl.cuh", "kernels_vl.cu") if tile.endswith(("v", "s", "t")) or tile == "8x16"
            else ("kernels.cu", "kernels_packed.cu", "kernels_slab.cu", "kernels_variants.cu"))
     h = hashlib.sha256()
     for f in common + own:
@@ -221,7 +222,7 @@ def measured_traffic(key: str, tile: str):
     try:
         with open(path) as fh:
             d = json.load(fh)
-        e = d.get(key)
+        e = d.get(f"{key}/{tile}") or d.get(key)  # per tile where several are measured
         if e and e.get("kernel_hash") == kernel_source_hash(tile) and e.get("tile") == tile:
             return e.get("dram_bytes_per_launch")
     except (OSError, ValueError):

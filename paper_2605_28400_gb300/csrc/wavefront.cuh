@@ -541,7 +541,9 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
     // One step: the halo of slice s goes into rowCur / colCur, slice s-1 is in rowPrev /
     // colPrev. `first` marks the first step of a loop iteration (it checks the producers for
     // both). Returns false when a bounded wait gave up.
-    auto step = [&](const int t, const bool first, int (&rowCur)[NK + 1],
+    // `tail` enables the end-cell work (scores, the slab's last plane, semi-global edge maxima):
+    // false on steps before any lane reaches an end slice, which then carry no branches for it.
+    auto step = [&](const int t, const bool first, const bool tail, int (&rowCur)[NK + 1],
                     const int (&rowPrev)[NK + 1], int (&colCur)[NJ],
                     const int (&colPrev)[NJ]) -> bool {
       const int s = t - r - lc;
@@ -845,7 +847,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
               reinterpret_cast<uint2*>(dst)[w2] = make_uint2(cw[2 * w2], cw[2 * w2 + 1]);
           }
         }
-        if (SLAB && p.plane_out && s == a) {
+        if (SLAB && tail && p.plane_out && s == a) {
           // Slab launch: the last slice becomes the next slab's input plane.
 #pragma unroll
           for (int pp = 0; pp < NJ; ++pp)
@@ -886,7 +888,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
               st_global_if(d4 + p4, v, out_k);
           }
         }
-        if (AT == kSemiGlobal && (edgeJ || edgeK)) {
+        if (AT == kSemiGlobal && tail && (edgeJ || edgeK)) {
           // Cells of this slice on the last row j = b or the last column k = c, in the original
           // frame M = M' - g2*(i+j+k). The last slice i = a is taken after the sweep.
           const int base = g2 * (s + j0 + k0);
@@ -901,7 +903,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
                   best = max(best, P[pp][qq] - base - g2 * (pp + qq));
               }
         }
-        if (AT == kGlobal && owns_end && s == a0 && (!SLAB || d.out_idx >= 0)) {
+        if (AT == kGlobal && tail && owns_end && s == a0 && (!SLAB || d.out_idx >= 0)) {
           int v = 0;
 #pragma unroll
           for (int pp = 0; pp < NJ; ++pp)
@@ -912,7 +914,7 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
           if (PACK == 2) v = (v & 0xffff) - (1 << 14);   // low half, unbiased
           p.scores[d.out_idx] = (TB ? (v >> 3) : v) + d.score_base;
         }
-        if (PACK && owns_end1 && s == a1) {
+        if (PACK && tail && owns_end1 && s == a1) {
           int v = 0;
 #pragma unroll
           for (int pp = 0; pp < NJ; ++pp)
@@ -925,9 +927,26 @@ __global__ void __launch_bounds__(kWarpsPerCta * 32, MinBlocks<NJ, NK, TB>::valu
       }
       return true;
     };
-    for (int t = 0; t < T; t += 2) {
-      if (!step(t, true, rowA, rowB, colA, colB)) break;
-      if (t + 1 < T && !step(t + 1, false, rowB, rowA, colB, colA)) break;
+    // Steps before t_end have every lane below every end slice (a, a0, a1): they run without the
+    // end-cell work, except in semi-global tasks of the last task row or column, whose edge lanes
+    // hold the row j = b or the column k = c of every slice. The second copy of the step pays in
+    // the traceback kernels (n~1000: 1.49 -> 1.47 ms); the score kernels were 2-3% slower with it.
+    constexpr bool kSplit = TB && AT != kLocal;
+    const int t_end = min(a, PACK ? min(a0, a1) : a0);
+    int t = 0;
+    bool running = true;
+    if (kSplit && !(AT == kSemiGlobal && (J == nJ - 1 || K == nK - 1))) {
+      for (; t + 1 < T && t + 1 < t_end; t += 2) {
+        if (!step(t, true, false, rowA, rowB, colA, colB) ||
+            !step(t + 1, false, false, rowB, rowA, colB, colA)) {
+          running = false;
+          break;
+        }
+      }
+    }
+    for (; running && t < T; t += 2) {
+      if (!step(t, true, true, rowA, rowB, colA, colB)) break;
+      if (t + 1 < T && !step(t + 1, false, true, rowB, rowA, colB, colA)) break;
     }
     __syncwarp();
     if (ok && lane == 0) st_release(progMe, T);  // all steps computed and stored

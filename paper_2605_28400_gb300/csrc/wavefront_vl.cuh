@@ -349,7 +349,10 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
     int xlo_prev = VIRT;  // residue of slice s - 1: the high half's
 
     int pub_in = p.TI;
-    auto step = [&](const int t, const bool first, int (&rowCur)[NH + 1],
+    // `tail` enables the end-cell work (the global score, the semi-global last-slice maxima):
+    // false on the steps before any lane can reach slice a, so those steps carry no per-step
+    // branches for it.
+    auto step = [&](const int t, const bool first, const bool tail, int (&rowCur)[NH + 1],
                     const int (&rowPrev)[NH + 1], int (&colCur)[NJ],
                     const int (&colPrev)[NJ]) -> bool {
       const int s = t - r - 2 * lc;
@@ -502,8 +505,14 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
           const unsigned ea = (unsigned)mad_lo(A[pp], p.one, Pxy);
           const unsigned eb = (unsigned)mad_lo(Bq[qq], p.one, Pxz);
           unsigned e = __vimax3_u16x2(ea, eb, (unsigned)Sx);
-          if constexpr (AT == kLocal) e = __vmaxu2(e, fl);  // v = 0
-          P[pp][qq] = (int)__viaddmax_u16x2(x2, cv(pp, qq), e);
+          if constexpr (AT == kLocal) {
+            // v = 0: the floor as the third input of one max, with x2 + C on the FMA pipe
+            // (one ALU-pipe instruction less per register: 27.4 -> 26.6 ms at n=4000)
+            const unsigned x2c = (unsigned)mad_lo((int)cv(pp, qq), p.one, (int)x2);
+            P[pp][qq] = (int)__vimax3_u16x2(x2c, e, fl);
+          } else {
+            P[pp][qq] = (int)__viaddmax_u16x2(x2, cv(pp, qq), e);
+          }
         };
         auto pass2 = [&](const int pp, const int qq) {
           const int Myz = (pp == 0) ? rowCur[qq] : (qq == 0 ? colCur[pp - 1] : P[pp - 1][qq - 1]);
@@ -596,18 +605,34 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
           // (0, 2^16), so one unsigned add-max per register folds it into the step's maximum.
           const unsigned g2x2 = (unsigned)g2 * 0x10001u;
           const unsigned add0 = 0x40004000u - ((unsigned)(g2 * (NH - 1)) << 16);
+          // Cells of one anti-diagonal share d, so they meet in 3-input maxima first and take
+          // the offset once per group of up to three.
           unsigned acc = 0;
 #pragma unroll
-          for (int pp = 0; pp < NJ; ++pp)
+          for (int dg = 0; dg < NJ + NH - 1; ++dg) {
+            const unsigned off = add0 - (unsigned)dg * g2x2;
+            unsigned g[3] = {0u, 0u, 0u};
+            int k = 0;
 #pragma unroll
-            for (int qq = 0; qq < NH; ++qq)
-              acc = __viaddmax_u16x2((unsigned)P[pp][qq], add0 - (unsigned)(pp + qq) * g2x2, acc);
+            for (int pp = 0; pp < NJ; ++pp) {
+              const int qq = dg - pp;
+              if (qq >= 0 && qq < NH) {
+                g[k++] = (unsigned)P[pp][qq];
+                if (k == 3) {
+                  acc = __viaddmax_u16x2(__vimax3_u16x2(g[0], g[1], g[2]), off, acc);
+                  k = 0;
+                }
+              }
+            }
+            if (k == 2) acc = __viaddmax_u16x2(__vmaxu2(g[0], g[1]), off, acc);
+            if (k == 1) acc = __viaddmax_u16x2(g[0], off, acc);
+          }
           // the low half's extra slice a + 1 and the high half's slice -1 do not count (a masked
           // half contributes 0, below any counted cell's D)
           const int dlo = s <= a ? (int)(acc & 0xffffu) : 0, dhi = s >= 1 ? (int)(acc >> 16) : 0;
           best = max(best, max(dlo, dhi) + Bt - g2 * (s + j0 + k0) - 32768);
         }
-        if (AT == kSemiGlobal) {
+        if (AT == kSemiGlobal && tail) {
           // Cells on a last slice, M = M' - g2*(i+j+k): the face i = a when each half reaches
           // it, and the row j = b / column k = c of each half's slice. Edge lanes all share one
           // row (pb) or column, so only its block runs.
@@ -654,7 +679,7 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
             }
           }
         }
-        if (AT == kGlobal && owns_end && (end_h ? s - 1 == a : s == a)) {
+        if (AT == kGlobal && tail && owns_end && (end_h ? s - 1 == a : s == a)) {
           unsigned v = 0;
 #pragma unroll
           for (int pp = 0; pp < NJ; ++pp)
@@ -687,9 +712,28 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
         nb = kVlBias - Bt;
       }
     };
-    for (int t = 0; t < T; t += 2) {
-      if (!step(t, true, rowA, rowB, colA, colB)) break;
-      if (t + 1 < T && !step(t + 1, false, rowB, rowA, colB, colA)) break;
+    // Steps t < a have every lane at a slice s <= t < a, so no end cell: they run without the
+    // end-cell work, except in semi-global tasks of the last task row or column, whose edge lanes
+    // hold the row j = b or the column k = c of every slice. The second copy of the step that
+    // this takes pays only where that work is per-step branches: the global type (8x16 tile
+    // 24.2 -> 23.0 ms at n=4000) and semi-global on 8x8v (30.2 -> 28.2 ms); semi-global 8x16 (255
+    // registers) was 14% slower with it, and local has no such work.
+    constexpr bool kSplit = AT == kGlobal || (AT == kSemiGlobal && NH < 8);
+    int t = 0;
+    bool running = true;
+    if (kSplit && !(AT == kSemiGlobal && (J == nJ - 1 || K == nK - 1))) {
+      for (; t + 1 < T && t + 1 < a; t += 2) {
+        if (!step(t, true, false, rowA, rowB, colA, colB) ||
+            !step(t + 1, false, false, rowB, rowA, colB, colA)) {
+          running = false;
+          break;
+        }
+        rebase();
+      }
+    }
+    for (; running && t < T; t += 2) {
+      if (!step(t, true, true, rowA, rowB, colA, colB)) break;
+      if (t + 1 < T && !step(t + 1, false, true, rowB, rowA, colB, colA)) break;
       rebase();
     }
     __syncwarp();

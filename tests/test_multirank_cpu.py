@@ -102,6 +102,8 @@ def test_kernel_label_and_tile_checked_traffic(tmp_path, monkeypatch):
         ("8x16s", "wavefront_vl_kernel<8,8,1>")
     # which sources a tile's traffic figure is tied to
     assert bench.kernel_source_hash("8x8v") == bench.kernel_source_hash("8x16s")
+    assert bench.kernel_source_hash("8x8v") == bench.kernel_source_hash("8x16t")
+    assert bench.kernel_source_hash("8x8v") == bench.kernel_source_hash("8x16")
     assert bench.kernel_source_hash("8x8v") != bench.kernel_source_hash("8x4")
     # traffic is reported only for the measured tile and the current kernel source
     prof = tmp_path / "profiles"
@@ -113,6 +115,13 @@ def test_kernel_label_and_tile_checked_traffic(tmp_path, monkeypatch):
     assert bench.measured_traffic("w", "8x8v") == 123
     assert bench.measured_traffic("w", "8x16v") is None
     assert bench.measured_traffic("other", "8x8v") is None
+    # a per-tile entry ("key/tile") where a workload's tiles are measured separately
+    (prof / "wavefront_traffic.json").write_text(json.dumps({
+        "w/8x8v": {"kernel_hash": "h0", "tile": "8x8v", "dram_bytes_per_launch": 5},
+        "w/8x16": {"kernel_hash": "h0", "tile": "8x16", "dram_bytes_per_launch": 7}}))
+    assert bench.measured_traffic("w", "8x8v") == 5
+    assert bench.measured_traffic("w", "8x16") == 7
+    assert bench.measured_traffic("w", "8x8") is None
     monkeypatch.setattr(bench, "kernel_source_hash", lambda tile: "h1")  # source changed since
     assert bench.measured_traffic("w", "8x8v") is None
 
