@@ -498,6 +498,7 @@ def _serve(B, srv, reqs, strs, rate, cap):
     """Submit `reqs` to the server with Poisson gaps at `rate` requests/s (None: all at once) and
     poll until every result is back. Returns submit times, completion times, results, tickets."""
     t_sub, t_done, tickets, results = {}, {}, [None] * len(reqs), {}
+    fresh = []  # tickets submitted since the poller last took them (O(1) per poll pass)
     lock = threading.Lock()
 
     def submitter():
@@ -517,6 +518,7 @@ def _serve(B, srv, reqs, strs, rate, cap):
             with lock:
                 t_sub[tk] = time.perf_counter()
                 tickets[i] = tk
+                fresh.append(tk)
 
     th = threading.Thread(target=submitter)
     th.start()
@@ -524,7 +526,8 @@ def _serve(B, srv, reqs, strs, rate, cap):
     n_done = 0
     while n_done < len(reqs):
         with lock:
-            pending |= {tk for tk in tickets if tk is not None and tk not in t_done}
+            pending.update(fresh)
+            fresh.clear()
         for tk in list(pending):
             st, score, rows = B.trioseq_poll(srv, tk, cap)
             if st == B.OK:
