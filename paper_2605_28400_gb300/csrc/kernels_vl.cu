@@ -41,7 +41,8 @@ template <int NJ, int NH, int CS>
 size_t vl_smem(int KP) {
   using G = VlGeom<NJ, NH>;
   const size_t sigN = (size_t)((KP * KP + 3) & ~3);
-  const size_t prof = CS ? (size_t)KP * (G::PJ16 + G::PK16) / 2 : (size_t)KP * (G::PJ + G::PK);
+  const bool p16 = CS || NH >= 8;  // 16-bit profiles, as the kernel keeps them
+  const size_t prof = p16 ? (size_t)KP * (G::PJ16 + G::PK16) / 2 : (size_t)KP * (G::PJ + G::PK);
   const size_t cv = CS ? (size_t)32 * 4 * G::CVG : 0;
   return (sigN + (size_t)VlLaunch<NH, CS>::warps * (prof + kRing * G::SLOT + cv)) * sizeof(int);
 }
