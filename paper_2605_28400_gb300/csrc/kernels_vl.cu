@@ -42,7 +42,10 @@ size_t vl_smem(int KP) {
   using G = VlGeom<NJ, NH>;
   const size_t sigN = (size_t)((KP * KP + 3) & ~3);
   const bool p16 = CS || NH >= 8;  // 16-bit profiles, as the kernel keeps them
-  const size_t prof = p16 ? (size_t)KP * (G::PJ16 + G::PK16) / 2 : (size_t)KP * (G::PJ + G::PK);
+  const bool pt = !CS && NH >= 8;  // the 8x16 tile's bank-conflict-free profile layout
+  const size_t prof = pt    ? (size_t)KP * (kPR * kPC * NJ / 2 + kPC * NH)
+                     : p16 ? (size_t)KP * (G::PJ16 + G::PK16) / 2
+                           : (size_t)KP * (G::PJ + G::PK);
   const size_t cv = CS ? (size_t)32 * 4 * G::CVG : 0;
   return (sigN + (size_t)VlLaunch<NH, CS>::warps * (prof + kRing * G::SLOT + cv)) * sizeof(int);
 }

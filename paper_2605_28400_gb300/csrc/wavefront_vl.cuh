@@ -108,10 +108,17 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
   // without it too: half the profile loads per step there (n=4000: 23.2 -> 22.3 ms). The 8x8v
   // tile's lane rows of 4 columns have no 8-value groups in k.
   constexpr bool kP16 = CS || NH >= 8;
-  const int prof_ints = kP16 ? KP * (G::PJ16 + G::PK16) / 2 : KP * (G::PJ + G::PK);
+  // 8x16 without CS: profile entries laid out [x][lane row][lane column] (J, 8 halves each) and
+  // [half][x][lane column] (K), so the 8 lanes of a 16-byte load phase (one lane row, lane
+  // columns 0..7) read 8 distinct bank groups whatever their residues: the row-major rows left
+  // 36% of the shared-load wavefronts to bank conflicts. The J rows repeat per lane column
+  // (16 KB of profiles per warp). n=4000: 22.1 -> 21.6 ms.
+  constexpr bool kPT = !CS && NH >= 8;
+  const int prof_ints = kPT ? KP * (kPR * kPC * NJ / 2 + kPC * NH)
+                             : (kP16 ? KP * (G::PJ16 + G::PK16) / 2 : KP * (G::PJ + G::PK));
   const int warp_ints = prof_ints + kRing * G::SLOT + (CS ? 32 * 4 * G::CVG : 0);
   int* profJ = smem + sigN + warp * warp_ints;
-  int* profK = profJ + (kP16 ? KP * G::PJ16 / 2 : KP * G::PJ);
+  int* profK = profJ + (kPT ? KP * kPR * kPC * NJ / 2 : (kP16 ? KP * G::PJ16 / 2 : KP * G::PJ));
   int* ring = profJ + prof_ints;
   int4* cvs = reinterpret_cast<int4*>(ring + kRing * G::SLOT);  // CS only
   unsigned short* profJ16 = reinterpret_cast<unsigned short*>(profJ);
@@ -184,7 +191,11 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
     for (int e = lane; e < KP * WJ; e += 32) {
       const int x = e / WJ, jl = e - x * WJ, j = J * WJ + jl;
       const int y = (j >= 1 && j <= b) ? (int)S1[j - 1] : VIRT;
-      if (kP16)
+      if (kPT) {
+        const int rr = jl / NJ, pq = jl - rr * NJ;
+        const unsigned short v16 = (unsigned short)sig[x * KP + y];
+        for (int l = 0; l < kPC; ++l) profJ16[((x * kPR + rr) * kPC + l) * NJ + pq] = v16;
+      } else if (kP16)
         profJ16[x * G::PJ16 + jl] = (unsigned short)sig[x * KP + y];
       else
         profJ[x * G::PJ + jl] = sig[x * KP + y];
@@ -192,7 +203,10 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
     for (int e = lane; e < KP * WK; e += 32) {
       const int x = e / WK, kl = e - x * WK, k = K * WK + kl;
       const int z = (k >= 1 && k <= c) ? (int)S2[k - 1] : VIRT;
-      if (kP16)
+      if (kPT) {
+        const int l = kl / NK, rem = kl - l * NK, h = rem / NH, q = rem - h * NH;
+        profK16[((h * KP + x) * kPC + l) * NH + q] = (unsigned short)sig[x * KP + z];
+      } else if (kP16)
         profK16[x * G::PK16 + kl] = (unsigned short)sig[x * KP + z];
       else
         profK[x * G::PK + kl] = sig[x * KP + z];
@@ -430,8 +444,10 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
         if constexpr (kP16) {
           // 16-bit profiles: one 16-byte load holds 8 values of a half; a PRMT pairs the low
           // half's value with the high half's
-          const int4* pl = reinterpret_cast<const int4*>(profJ16 + xl * G::PJ16 + r * NJ);
-          const int4* ph = reinterpret_cast<const int4*>(profJ16 + xh * G::PJ16 + r * NJ);
+          const int4* pl = reinterpret_cast<const int4*>(
+              kPT ? profJ16 + ((xl * kPR + r) * kPC + lc) * NJ : profJ16 + xl * G::PJ16 + r * NJ);
+          const int4* ph = reinterpret_cast<const int4*>(
+              kPT ? profJ16 + ((xh * kPR + r) * kPC + lc) * NJ : profJ16 + xh * G::PJ16 + r * NJ);
 #pragma unroll
           for (int p8 = 0; p8 < NJ / 8; ++p8) {
             const int4 u = pl[p8], v = ph[p8];
@@ -442,8 +458,10 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
               A[8 * p8 + 2 * w + 1] = (int)__byte_perm(uu[w], vv[w], 0x7632);
             }
           }
-          const int4* ql = reinterpret_cast<const int4*>(profK16 + xl * G::PK16 + lc * NK);
-          const int4* qh = reinterpret_cast<const int4*>(profK16 + xh * G::PK16 + lc * NK + NH);
+          const int4* ql = reinterpret_cast<const int4*>(
+              kPT ? profK16 + (xl * kPC + lc) * NH : profK16 + xl * G::PK16 + lc * NK);
+          const int4* qh = reinterpret_cast<const int4*>(
+              kPT ? profK16 + ((KP + xh) * kPC + lc) * NH : profK16 + xh * G::PK16 + lc * NK + NH);
 #pragma unroll
           for (int q8 = 0; q8 < NH / 8; ++q8) {
             const int4 u = ql[q8], v = qh[q8];
