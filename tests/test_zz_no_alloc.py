@@ -2,8 +2,9 @@
 
 It serves callers that may not allocate device memory when they align (their device memory is
 already reserved by another allocator, or their host forbids cudaMalloc in callbacks): its
-workspace is a fixed array in the library. Its score must equal the regular entry point's
-(trioseq_align_batch, score only) exactly, on consecutive calls that reuse the same array.
+workspace is a fixed array in the library. Its score must equal the oracle's and the regular
+entry point's (trioseq_align_batch, score only) exactly, on consecutive calls that reuse the same
+array.
 This file is collected last so that a run stopping at the first failure has run every other
 test first.
 """
@@ -70,3 +71,26 @@ def test_noalloc_edge_cases_and_limits():
     assert st == B.ESCRATCH
     st, got = _noalloc(torch, sc, ["AC", "AC", "AC"])  # usable again after the rejections
     assert st == B.OK and got == 3 * 2 * 2
+
+
+def test_noalloc_equals_the_oracle():
+    """Scores straight against oracle.align (Eq. 1, Sec. II): every shape up to 3^3 with random
+    DNA residues, ragged shapes that span several column tasks, and a protein case."""
+    torch = pytest.importorskip("torch")
+    import itertools
+
+    import oracle
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(511)
+    dna, prot = synth.dna_scoring(), synth.protein_scoring(512)
+    cases = [(dna, s) for s in itertools.product(range(4), repeat=3)]
+    cases += [(dna, s) for s in ((37, 70, 55), (90, 12, 64), (0, 60, 61), (130, 97, 41))]
+    cases += [(prot, (80, 75, 90))]
+    bad = []
+    for sc, shape in cases:
+        trip = [rng.integers(0, len(sc.alphabet), n).astype(np.uint8) for n in shape]
+        st, got = _noalloc(torch, sc, [synth.to_str(s, sc.alphabet) for s in trip])
+        want = oracle.align(*trip, sc.sub, sc.gap)
+        if st != B.OK or got != want:
+            bad.append((shape, st, got, want))
+    assert not bad, bad[:5]
