@@ -100,6 +100,16 @@ typedef struct trioseq_plan_s* trioseq_plan_t;
  * autotuner cache for the current CUDA device. `max_len_hint` pre-sizes nothing mandatory
  * (0 = no hint). `flags` is the alignment type: TRIOSEQ_GLOBAL (0), TRIOSEQ_SEMIGLOBAL or
  * TRIOSEQ_LOCAL; every call on the plan (batches, autotuner, server) uses that type.
+ * Tuning read from the environment when the plan is created (none changes a result):
+ * TRIOSEQ_SCORE_TILE forces the score tile ("8x8", "4x8", "4x4", or the two-cells-per-register
+ * "8x16", "8x8v", "8x16s", "8x16t"; work those cannot take runs on the int32 8x8 kernel) and
+ * TRIOSEQ_TB_TILE the traceback tile ("8x8", "4x8", "4x4", "8x4"); TRIOSEQ_TI the progress
+ * interval (steps between published progress counts, default 8); TRIOSEQ_DATA_FLAGS=1/0 forces
+ * the boundary records to act as their own readiness flags in traceback launches, or not (by
+ * default they do for one-triplet traceback batches); TRIOSEQ_PACKED=0 disables two triplets per
+ * register; TRIOSEQ_GRAPHS=0 graph replay; TRIOSEQ_PACE=0 first-wave pacing; TRIOSEQ_WAIT_MS the
+ * bounded waits' limit (default 2000). TRIOSEQ_CTAS_PER_SM (read per batch) caps the resident
+ * CTAs per SM.
  * Errors: EINVAL (null, bad alphabet, asymmetric sub, gap > 0, unknown flags), ECUDA. */
 trioseq_status trioseq_plan(const trioseq_scoring* scoring, uint32_t max_len_hint, uint32_t flags,
                             trioseq_plan_t* out);
