@@ -41,11 +41,10 @@ template <int NJ, int NH, int CS>
 size_t vl_smem(int KP) {
   using G = VlGeom<NJ, NH>;
   const size_t sigN = (size_t)((KP * KP + 3) & ~3);
-  const bool p16 = CS || NH >= 8;  // 16-bit profiles, as the kernel keeps them
-  const bool pt = !CS && NH >= 8;  // the 8x16 tile's bank-conflict-free profile layout
-  const size_t prof = pt    ? (size_t)KP * (kPR * kPC * NJ / 2 + kPC * NH)
-                     : p16 ? (size_t)KP * (G::PJ16 + G::PK16) / 2
-                           : (size_t)KP * (G::PJ + G::PK);
+  // Without CS: the bank-conflict-free 16-bit layout (the local 8x8v kernel's 32-bit row-major
+  // profiles take less); with CS: 16-bit row-major profiles.
+  const size_t prof = !CS ? (size_t)KP * (kPR * kPC * NJ / 2 + kPC * NH)
+                          : (size_t)KP * (G::PJ16 + G::PK16) / 2;
   const size_t cv = CS ? (size_t)32 * 4 * G::CVG : 0;
   return (sigN + (size_t)VlLaunch<NH, CS>::warps * (prof + kRing * G::SLOT + cv)) * sizeof(int);
 }

@@ -104,16 +104,18 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // per warp: profiles (32-bit, or 16-bit with kP16), the staging ring, and with CS the sigma''
   // tiles of the warp's lanes ([group][lane][4] ints, conflict-free 16-byte loads)
-  // 16-bit profiles (one 16-byte load per 8 values of a half) with CS, and on the 8x16 tile
-  // without it too: half the profile loads per step there (n=4000: 23.2 -> 22.3 ms). The 8x8v
-  // tile's lane rows of 4 columns have no 8-value groups in k.
-  constexpr bool kP16 = CS || NH >= 8;
-  // 8x16 without CS: profile entries laid out [x][lane row][lane column] (J, 8 halves each) and
-  // [half][x][lane column] (K), so the 8 lanes of a 16-byte load phase (one lane row, lane
-  // columns 0..7) read 8 distinct bank groups whatever their residues: the row-major rows left
-  // 36% of the shared-load wavefronts to bank conflicts. The J rows repeat per lane column
-  // (16 KB of profiles per warp). n=4000: 22.1 -> 21.6 ms.
-  constexpr bool kPT = !CS && NH >= 8;
+  // 16-bit profiles (one 16-byte load per 8 values of a half) with CS, on the 8x16 tile without
+  // it too (half the profile loads per step there: n=4000 23.2 -> 22.3 ms), and on 8x8v with the
+  // layout below (its K entries are 4 values, 8-byte loads).
+  constexpr bool kP16 = CS || NH >= 8 || AT != kLocal;
+  // Without CS: 16-bit profile entries laid out [x][lane row][lane column] (J, 8 halves each) and
+  // [half][x][lane column] (K, NH halves), so the 8 lanes of a 16-byte load phase (one lane row,
+  // lane columns 0..7) read 8 distinct bank groups whatever their residues: the row-major rows
+  // left 36% (8x16) and 46% (8x8v) of the shared-load wavefronts to bank conflicts. The J rows
+  // repeat per lane column (16 KB of profiles per warp on 8x16, 13 KB on 8x8v). n=4000: 8x16
+  // 22.1 -> 21.6 ms, 8x8v 22.7 -> 21.9 ms, semi-global 8x8v -2.6%; the local 8x8v kernel was
+  // 1.4% slower with it and keeps 32-bit row-major profiles.
+  constexpr bool kPT = !CS && (NH >= 8 || AT != kLocal);
   const int prof_ints = kPT ? KP * (kPR * kPC * NJ / 2 + kPC * NH)
                              : (kP16 ? KP * (G::PJ16 + G::PK16) / 2 : KP * (G::PJ + G::PK));
   const int warp_ints = prof_ints + kRing * G::SLOT + (CS ? 32 * 4 * G::CVG : 0);
@@ -462,6 +464,14 @@ __global__ void __launch_bounds__(VlLaunch<NH, CS>::warps * 32)
               kPT ? profK16 + (xl * kPC + lc) * NH : profK16 + xl * G::PK16 + lc * NK);
           const int4* qh = reinterpret_cast<const int4*>(
               kPT ? profK16 + ((KP + xh) * kPC + lc) * NH : profK16 + xh * G::PK16 + lc * NK + NH);
+          if constexpr (kPT && NH == 4) {
+            const uint2 u = *reinterpret_cast<const uint2*>(profK16 + (xl * kPC + lc) * NH);
+            const uint2 v = *reinterpret_cast<const uint2*>(profK16 + ((KP + xh) * kPC + lc) * NH);
+            Bq[0] = (int)__byte_perm(u.x, v.x, 0x5410);
+            Bq[1] = (int)__byte_perm(u.x, v.x, 0x7632);
+            Bq[2] = (int)__byte_perm(u.y, v.y, 0x5410);
+            Bq[3] = (int)__byte_perm(u.y, v.y, 0x7632);
+          }
 #pragma unroll
           for (int q8 = 0; q8 < NH / 8; ++q8) {
             const int4 u = ql[q8], v = qh[q8];
